@@ -1,0 +1,222 @@
+"""ctypes front end of the FP64 CPU oracle.
+
+TEST INFRASTRUCTURE ONLY: the slow reference that the CUDA library is checked
+against.  Only tests/, __graft_entry__.smoke() and bench.py (its cpu_baseline
+leg and its ``--impl reference`` arm) may import this module.  It imports
+nothing from the CUDA package.
+
+Array conventions follow the library: pos [3][n], U [8][n] float64, fields
+(rho, Vx, Vy, Vz, Bx, By, Bz, sigma).  Neighbour lists are CSR over a query
+list of particle indices, with neighbour indices in increasing order.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+
+
+class Box(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("len", C.c_double * 3), ("periodic", C.c_int32 * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("rf_factor", C.c_double), ("weight_kind", C.c_int32),
+                ("pad", C.c_int32), ("zeta", C.c_void_p), ("eta", C.c_void_p)]
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load(_build.build())
+    return _LIB
+
+
+def load(path: str):
+    """Open an oracle shared library at ``path`` and declare its signatures."""
+    L = C.CDLL(path)
+    L.orc_neighbors.argtypes = [C.POINTER(Box), C.c_int64, _f64p, _f64p, C.c_double, C.c_double,
+                                C.c_int64, _i64p, _i64p, C.c_void_p, C.c_int64]
+    L.orc_mls_derivs.argtypes = [C.POINTER(Box), C.c_int64, _f64p, _f64p, _f64p, C.POINTER(Params),
+                                 C.c_int64, _i64p, _i64p, _i64p, _f64p, C.c_void_p, _i32p]
+    L.orc_mhd_rhs.argtypes = [C.POINTER(Box), C.c_int64, _f64p, _f64p, _f64p, C.POINTER(Params),
+                              C.c_int64, _i64p, _i64p, _i64p, _f64p, _i32p]
+    L.orc_rhs_jvp.argtypes = [C.POINTER(Box), C.c_int64, _f64p, _f64p, _f64p, C.c_void_p,
+                              C.c_void_p, C.POINTER(Params), C.c_int64, _i64p, _i64p, _i64p,
+                              _f64p, _f64p]
+    L.orc_pc_step.argtypes = [C.POINTER(Box), C.c_int64, _f64p, _f64p, _f64p, C.c_double,
+                              C.POINTER(Params)]
+    for f in ("orc_neighbors", "orc_mls_derivs", "orc_mhd_rhs", "orc_rhs_jvp", "orc_pc_step"):
+        getattr(L, f).restype = C.c_int
+    return L
+
+
+class using:
+    """Context manager: route every oracle call through another build of it
+    (the mutation tests plant mistakes in a copy of the source)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _LIB
+        self.prev = _LIB
+        _LIB = load(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _LIB
+        _LIB = self.prev
+        return False
+
+
+def make_box(lo, ln, periodic) -> Box:
+    b = Box()
+    for a in range(3):
+        b.lo[a] = float(lo[a])
+        b.len[a] = float(ln[a])
+        b.periodic[a] = int(periodic[a])
+    return b
+
+
+def box_of(w) -> Box:
+    return make_box(w.box_lo, w.box_len, w.periodic)
+
+
+class _P:
+    """Params plus the numpy arrays its pointers refer to (kept alive)."""
+
+    def __init__(self, gamma, rf_factor=2.3, weight_kind=0, zeta=None, eta=None):
+        self.keep = []
+        self.p = Params()
+        self.p.gamma = float(gamma)
+        self.p.rf_factor = float(rf_factor)
+        self.p.weight_kind = int(weight_kind)
+        self.p.zeta = self._ptr(zeta)
+        self.p.eta = self._ptr(eta)
+
+    def _ptr(self, a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, np.float64)
+        self.keep.append(a)
+        return a.ctypes.data
+
+
+def _c(a, dt=np.float64):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _query(n, query):
+    return np.arange(n, dtype=np.int64) if query is None else _c(query, np.int64)
+
+
+def neighbors(box: Box, pos, lam, query=None, rf_factor=2.3, skin=0.0):
+    """Brute-force neighbour sets of the query particles: (off[nq+1], idx)."""
+    pos, lam = _c(pos), _c(lam)
+    n = lam.shape[0]
+    q = _query(n, query)
+    off = np.zeros(q.shape[0] + 1, np.int64)
+    L = lib()
+    L.orc_neighbors(C.byref(box), n, pos, lam, rf_factor, skin, q.shape[0], q, off, None, 0)
+    idx = np.zeros(max(int(off[-1]), 1), np.int64)
+    rc = L.orc_neighbors(C.byref(box), n, pos, lam, rf_factor, skin, q.shape[0], q, off,
+                         idx.ctypes.data, idx.shape[0])
+    assert rc == 0
+    return off, idx[: off[-1]]
+
+
+def mls_derivs(box: Box, pos, lam, U, nbrs, query=None, gamma=5.0 / 3.0, rf_factor=2.3,
+               weight_kind=0):
+    """grad [8][3][nq], hess [8][6][nq], status [nq] for the query particles."""
+    pos, lam, U = _c(pos), _c(lam), _c(U)
+    n = lam.shape[0]
+    q = _query(n, query)
+    off, idx = nbrs
+    nq = q.shape[0]
+    grad = np.zeros((8, 3, nq))
+    hess = np.zeros((8, 6, nq))
+    st = np.zeros(nq, np.int32)
+    P = _P(gamma, rf_factor, weight_kind)
+    lib().orc_mls_derivs(C.byref(box), n, pos, lam, U, C.byref(P.p), nq, q, _c(off, np.int64),
+                         _c(idx, np.int64) if len(idx) else np.zeros(1, np.int64), grad,
+                         hess.ctypes.data, st)
+    return grad, hess, st
+
+
+def mhd_rhs(box: Box, pos, lam, U, nbrs, query=None, gamma=5.0 / 3.0, rf_factor=2.3,
+            weight_kind=0, zeta=None, eta=None):
+    """dU/dt [8][nq] and status [nq] for the query particles."""
+    pos, lam, U = _c(pos), _c(lam), _c(U)
+    n = lam.shape[0]
+    q = _query(n, query)
+    off, idx = nbrs
+    nq = q.shape[0]
+    out = np.zeros((8, nq))
+    st = np.zeros(nq, np.int32)
+    P = _P(gamma, rf_factor, weight_kind, zeta, eta)
+    lib().orc_mhd_rhs(C.byref(box), n, pos, lam, U, C.byref(P.p), nq, q, _c(off, np.int64),
+                      _c(idx, np.int64) if len(idx) else np.zeros(1, np.int64), out, st)
+    return out, st
+
+
+def rhs_jvp(box: Box, pos, lam, U, dpos, dU, nbrs, query=None, gamma=5.0 / 3.0, rf_factor=2.3,
+            weight_kind=0, zeta=None, eta=None):
+    """(dU/dt, its derivative along (dpos, dU)) for the query particles, sets frozen."""
+    pos, lam, U = _c(pos), _c(lam), _c(U)
+    n = lam.shape[0]
+    q = _query(n, query)
+    off, idx = nbrs
+    nq = q.shape[0]
+    out = np.zeros((8, nq))
+    dout = np.zeros((8, nq))
+    dpos = None if dpos is None else _c(dpos)
+    dU = None if dU is None else _c(dU)
+    P = _P(gamma, rf_factor, weight_kind, zeta, eta)
+    lib().orc_rhs_jvp(C.byref(box), n, pos, lam, U,
+                      None if dpos is None else dpos.ctypes.data,
+                      None if dU is None else dU.ctypes.data, C.byref(P.p), nq, q,
+                      _c(off, np.int64), _c(idx, np.int64) if len(idx) else np.zeros(1, np.int64),
+                      out, dout)
+    return out, dout
+
+
+def pc_step(box: Box, pos, lam, U, dt, gamma=5.0 / 3.0, rf_factor=2.3, weight_kind=0, zeta=None,
+            eta=None):
+    """One Heun step of all particles (O(n^2) brute force): returns new (pos, U)."""
+    pos, lam, U = _c(pos).copy(), _c(lam), _c(U).copy()
+    P = _P(gamma, rf_factor, weight_kind, zeta, eta)
+    nsing = lib().orc_pc_step(C.byref(box), lam.shape[0], pos, lam, U, float(dt), C.byref(P.p))
+    return pos, U, nsing
+
+
+def workload_rhs(w, query=None, **kw):
+    """Convenience: brute-force neighbours plus dU/dt for a workloads.Workload."""
+    box = box_of(w)
+    nb = neighbors(box, w.pos, w.lam, query, kw.get("rf_factor", 2.3))
+    return mhd_rhs(box, w.pos, w.lam, w.U, nb, query, gamma=w.gamma, **kw)
+
+
+def available() -> bool:
+    try:
+        lib()
+        return True
+    except Exception:  # pragma: no cover - no compiler
+        return False
+
+
+__all__ = ["Box", "Params", "lib", "load", "using", "make_box", "box_of", "neighbors", "mls_derivs", "mhd_rhs",
+           "rhs_jvp", "pc_step", "workload_rhs", "available"]
+
+if os.environ.get("PHB_ORACLE_EAGER"):
+    lib()

@@ -1,0 +1,79 @@
+"""The oracle pins must fail when a plausible mistake is planted in the oracle.
+
+Each case compiles a copy of oracle/phb_oracle.cpp with one textual mistake
+(on the CPU, in a temporary directory) and runs the pins that should catch it
+against that copy.  A mutation that no pin catches fails this test.
+"""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+from oracle import build as obuild
+
+import test_oracle_fit as tfit
+import test_oracle_neighbors as tnb
+import test_oracle_rhs as trhs
+import test_oracle_step as tstep
+
+MUTATIONS = {
+    "hessian_diag_factor": ("hess[f][0] = T(2.0) * C[3 * NF + f] * il2;",
+                            "hess[f][0] = C[3 * NF + f] * il2;"),
+    "weight_power": ("(T(1.0) - s2);  // sqrt of", "(T(1.0) - s2) * (T(1.0) - s2);  // sqrt of"),
+    "not_centred": ("sw * (U[f * n + j] - U[f * n + i])", "sw * (U[f * n + j])"),
+    "lorentz_sign": ("J[1] * B[2] - J[2] * B[1]", "J[2] * B[1] - J[1] * B[2]"),
+    "curl_sign": ("g[6][1] - g[5][2]", "g[6][1] + g[5][2]"),
+    "no_pressure": ("T(-(gamma - 1.0)) * g[7][a]", "T(0.0) * g[7][a]"),
+    "zeta_sign": ("/ rho + T(zeta) * gdivV[a]", "/ rho - T(zeta) * gdivV[a]"),
+    "no_heating": ("+ rho * T(zeta) * divV * divV", "+ T(0.0) * divV"),
+    "eta_dropped": ("+ T(eta) * gdivB[a]", "+ T(0.0) * gdivB[a]"),
+    "induction_compression": ("- B[a] * divV", "+ B[a] * divV"),
+    "not_strict": ("return d2 < r * r;", "return d2 <= r * r;"),
+    "no_min_image": ("if (periodic) d = d - len", "if (periodic < 0) d = d - len"),
+    "euler_corrector": ("U[k] += 0.5 * dt * (F0[k] + F1[k]);", "U[k] += dt * F0[k];"),
+    "basis_xyz_missing": ("p[13] = x * y * z;", "p[13] = x * y;"),
+    "lambda_scale": ("grad[f][0] = C[0 * NF + f] * il;", "grad[f][0] = C[0 * NF + f] * il * il;"),
+}
+
+PINS = [
+    lambda: tnb.test_golden_ties_strict_periodic_nonmutual(oracle),
+    lambda: tnb.test_exact_rational_bruteforce_tiny(oracle),
+    lambda: tfit.test_cubic_reproduction(oracle, 0),
+    lambda: tfit.test_matches_library_lstsq(oracle),
+    lambda: tfit.test_rotation_equivariance(oracle),
+    lambda: trhs.test_uniform_state_is_exactly_steady(oracle),
+    lambda: trhs.test_circular_alfven_exact_solution_third_order(oracle),
+    lambda: trhs.test_linear_wave_eigenmode_third_order(oracle, "fast"),
+    lambda: trhs.test_damped_sound_wave_bulk_viscosity(oracle),
+    lambda: trhs.test_divb_diffusion(oracle),
+    lambda: trhs.test_viscous_heating_linear_flow(oracle),
+    lambda: tstep.test_heun_is_second_order_in_time(oracle),
+]
+
+
+def _compile(src_text, out):
+    with open(out + ".cpp", "w") as f:
+        f.write(src_text)
+    subprocess.run([os.environ.get("CXX", "g++"), *obuild.FLAGS, out + ".cpp", "-o", out],
+                   check=True)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_mutation_is_caught(name, tmp_path):
+    src = open(obuild.SRC).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, f"mutation anchor not unique/found: {old!r}"
+    lib = str(tmp_path / f"mut_{name}.so")
+    _compile(src.replace(old, new), lib)
+    caught = []
+    with oracle.using(lib):
+        for i, pin in enumerate(PINS):
+            try:
+                pin()
+            except AssertionError:
+                caught.append(i)
+                break
+    assert caught, f"no pin caught mutation {name}"

@@ -1,0 +1,139 @@
+"""Pins of the oracle's MHD time derivatives against exact solutions
+(Paper II Sec. 2, Sec. 3.1-3.2, App. A)."""
+import numpy as np
+import pytest
+
+import workloads
+from _analytic import (circular_alfven_dudt, circular_alfven_state, damped_sound_wave,
+                       linear_wave_dudt, rel_err)
+
+
+def _sample(n, k=1500, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n, min(n, k), replace=False)).astype(np.int64)
+
+
+def test_uniform_state_is_exactly_steady(orc):
+    w = workloads.linear_wave(10, amplitude=0.0)
+    out, st = orc.workload_rhs(w)
+    assert not st.any()
+    assert not out.any()          # centred fit: every right-hand side is exactly zero
+
+
+def test_galilean_shift(orc):
+    """Adding a uniform velocity leaves every Lagrangian time derivative unchanged."""
+    w = workloads.random_modes(12, seed=12, amp=0.05)
+    box = orc.box_of(w)
+    nb = orc.neighbors(box, w.pos, w.lam)
+    o1, _ = orc.mhd_rhs(box, w.pos, w.lam, w.U, nb, gamma=w.gamma)
+    U2 = w.U.copy()
+    U2[1:4] += np.array([[3.0], [-1.5], [0.75]])
+    o2, _ = orc.mhd_rhs(box, w.pos, w.lam, U2, nb, gamma=w.gamma)
+    assert rel_err(o2, o1).max() < 1e-12
+
+
+def _alfven_err(ns):
+    pos, h = workloads.lattice_positions(ns, 7)
+    U = circular_alfven_state(pos)
+    lam = np.full(pos.shape[1], h)
+    import oracle
+    box = oracle.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    q = _sample(pos.shape[1])
+    out, st = oracle.mhd_rhs(box, pos, lam, U, oracle.neighbors(box, pos, lam, q), q)
+    assert not st.any()
+    return np.abs(out - circular_alfven_dudt(pos[:, q])).max() / (0.2 * np.pi)
+
+
+def test_circular_alfven_exact_solution_third_order(orc):
+    """Sec. 3.2 state is an exact travelling solution: DV/Dt = DB/Dt =
+    0.2 pi (0, cos 2 pi x, -sin 2 pi x), Drho/Dt = Dsigma/Dt = 0.  The MLS
+    truncation error falls at third order as lambda halves."""
+    e16, e32 = _alfven_err(16), _alfven_err(32)
+    assert e16 < 2e-2 and e32 < 3e-3
+    assert e16 / e32 > 6.0
+
+
+@pytest.mark.parametrize("mode", ["fast", "slow", "alfven"])
+def test_linear_wave_eigenmode_third_order(orc, mode):
+    """App. A eigen-relations: the RHS of a 1e-6 eigenmode is -omega times the
+    mode in quadrature, exact to O(A^2); error converges at third order."""
+    errs = []
+    for ns in (16, 32):
+        w = workloads.linear_wave(ns, mode=mode)
+        q = _sample(w.n)
+        out, st = orc.workload_rhs(w, q)
+        assert not st.any()
+        exp = linear_wave_dudt(w)[:, q]
+        errs.append(np.abs(out - exp).max() / (w.meta["amplitude"] * w.meta["omega"]))
+    assert errs[0] < 2e-2, errs
+    assert errs[0] / errs[1] > 6.0, errs
+
+
+def test_damped_sound_wave_bulk_viscosity(orc):
+    """App. A with zeta > 0, B = 0: the damped eigenmode's RHS is -i omega times
+    the mode with omega = sqrt(c_s^2 k^2 - zeta^2 k^4/4) - i zeta k^2 / 2."""
+    pos, h = workloads.lattice_positions(32, 21)
+    n = pos.shape[1]
+    zeta = 0.08
+    U, exp = damped_sound_wave(pos, zeta)
+    lam = np.full(n, h)
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    q = _sample(n)
+    nb = orc.neighbors(box, pos, lam, q)
+    out, st = orc.mhd_rhs(box, pos, lam, U, nb, q, zeta=np.full(n, zeta))
+    scale = np.abs(exp[1]).max()
+    assert np.abs(out[1] - exp[1, q]).max() < 5e-3 * scale
+    assert np.abs(out[0] - exp[0, q]).max() < 5e-3 * np.abs(exp[0]).max()
+    assert np.abs(out[7] - exp[7, q]).max() < 5e-3 * np.abs(exp[7]).max()
+    # the viscous term is what damps: without zeta the velocity RHS misses
+    # -zeta k^2 V, which is much larger than the tolerance above
+    out0, _ = orc.mhd_rhs(box, pos, lam, U, nb, q)
+    assert np.abs(out0[1] - exp[1, q]).max() > 5e-2 * scale
+
+
+def test_divb_diffusion(orc):
+    """Sec. 2 'diffusive correction ... diffuses nonzero div B away': for
+    B = (1 + a sin kx, 0, 0), V = 0 the only non-zero RHS is
+    dBx/dt = eta d^2 Bx/dx^2 = -eta k^2 a sin kx."""
+    pos, h = workloads.lattice_positions(32, 22)
+    n = pos.shape[1]
+    k = 2 * np.pi
+    a = 1e-3
+    U = workloads.background(n, B0=(1.0, 0.0, 0.0))
+    U[4] += a * np.sin(k * pos[0])
+    eta = 0.05
+    lam = np.full(n, h)
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    q = _sample(n)
+    out, st = orc.mhd_rhs(box, pos, lam, U, orc.neighbors(box, pos, lam, q), q,
+                          eta=np.full(n, eta))
+    exp = -eta * k * k * a * np.sin(k * pos[0, q])
+    # a second derivative from a cubic fit carries an O(lambda^2) truncation error
+    assert np.abs(out[4] - exp).max() < 1.5e-2 * np.abs(exp).max()
+    # V = 0 so rho and sigma stay exactly steady; the Lorentz force and the
+    # cross terms eta d_y d_x B_x, eta d_z d_x B_x are small truncation residues
+    assert not out[[0, 7]].any()
+    assert np.abs(out[[1, 2, 3, 5, 6]]).max() < 1e-2 * np.abs(exp).max()
+
+
+def test_viscous_heating_linear_flow(orc):
+    """Linear velocity V = G (x - c), uniform rho, sigma, B = 0 (reproduced
+    exactly by the cubic fit): DV/Dt = 0 and
+    Dsigma/Dt = -gamma sigma tr G + rho zeta (tr G)^2, the heating that makes
+    the viscous force conserve total energy."""
+    pos, h = workloads.lattice_positions(10, 23)
+    n = pos.shape[1]
+    G = np.array([[0.3, 0.1, -0.2], [0.05, -0.1, 0.2], [0.1, 0.0, 0.25]])
+    U = workloads.background(n, B0=(0.0, 0.0, 0.0), rho0=1.3, P0=0.9)
+    U[1:4] = G @ (pos - 0.5)
+    zeta = 0.7
+    gamma = 5.0 / 3.0
+    lam = np.full(n, h)
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (0, 0, 0))
+    nb = orc.neighbors(box, pos, lam)
+    out, st = orc.mhd_rhs(box, pos, lam, U, nb, gamma=gamma, zeta=np.full(n, zeta))
+    ok = st == 0
+    tr = np.trace(G)
+    np.testing.assert_allclose(out[7, ok], -gamma * U[7, 0] * tr + 1.3 * zeta * tr * tr, rtol=1e-10)
+    np.testing.assert_allclose(out[0, ok], -1.3 * tr, rtol=1e-10)
+    assert np.abs(out[1:4, ok]).max() < 1e-10

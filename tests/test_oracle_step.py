@@ -1,0 +1,59 @@
+"""Pins of the oracle's predictor-corrector step and its forward-mode derivative
+(Paper II Sec. 2 'second order predictor-corrector', Sec. 4.2)."""
+import numpy as np
+
+import workloads
+from _analytic import rel_err
+
+
+def test_uniform_flow_advects_exactly(orc):
+    w = workloads.linear_wave(8, amplitude=0.0)
+    w.U[1:4] = np.array([[0.3], [-0.2], [0.1]])
+    box = orc.box_of(w)
+    dt = 0.0625
+    pos, U, ns = orc.pc_step(box, w.pos, w.lam, w.U, dt, gamma=w.gamma)
+    assert ns == 0
+    np.testing.assert_array_equal(U, w.U)
+    np.testing.assert_array_equal(pos, w.pos + dt * w.U[1:4])
+
+
+def test_heun_is_second_order_in_time(orc):
+    """One step against the semi-discrete solution (64 small steps): the local
+    error scales as dt^3 (Euler would give dt^2)."""
+    w = workloads.linear_wave(8, amplitude=1e-3)
+    box = orc.box_of(w)
+
+    def run(dt, steps):
+        p, u = w.pos, w.U
+        for _ in range(steps):
+            p, u, _ = orc.pc_step(box, p, w.lam, u, dt, gamma=w.gamma)
+        return u
+
+    errs = []
+    for dt in (0.04, 0.02):
+        ref = run(dt / 64, 64)
+        errs.append(np.abs(run(dt, 1) - ref).max())
+    assert errs[0] / errs[1] > 6.5, errs
+
+
+def test_jvp_matches_central_differences(orc):
+    w = workloads.random_modes(10, seed=31, amp=0.05)
+    box = orc.box_of(w)
+    rng = np.random.default_rng(4)
+    q = np.sort(rng.choice(w.n, 120, replace=False)).astype(np.int64)
+    nb = orc.neighbors(box, w.pos, w.lam, q)
+    dpos = rng.uniform(-1, 1, size=(3, w.n)) * w.lam
+    dU = rng.uniform(-1, 1, size=(8, w.n))
+    zeta = np.full(w.n, 0.02)
+    eta = np.full(w.n, 0.01)
+    out, dout = orc.rhs_jvp(box, w.pos, w.lam, w.U, dpos, dU, nb, q, gamma=w.gamma, zeta=zeta,
+                            eta=eta)
+    base, _ = orc.mhd_rhs(box, w.pos, w.lam, w.U, nb, q, gamma=w.gamma, zeta=zeta, eta=eta)
+    np.testing.assert_array_equal(out, base)
+    h = 1e-6
+    op, _ = orc.mhd_rhs(box, w.pos + h * dpos, w.lam, w.U + h * dU, nb, q, gamma=w.gamma,
+                        zeta=zeta, eta=eta)
+    om, _ = orc.mhd_rhs(box, w.pos - h * dpos, w.lam, w.U - h * dU, nb, q, gamma=w.gamma,
+                        zeta=zeta, eta=eta)
+    fd = (op - om) / (2 * h)
+    assert rel_err(dout, fd).max() < 1e-6
