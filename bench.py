@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the Phurbas particle right-hand-side hot path on one GB300.
+
+One step = one second-order predictor-corrector step (Paper II Sec. 2) of the
+whole particle set: cell binning, neighbour lists with a skin, two fused MLS
+fit + MHD right-hand-side evaluations and the Heun update.  The metric counts
+particle-RHS evaluations (two per particle per step).  Workload: the 64^3
+jittered lattice with random Fourier modes (262,144 particles, constant
+lambda), inputs resident in HBM; the L2 is flushed (256 MiB write) before
+every timed step and the state is reset so every step does the same work.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent replica (weak scaling; the path
+needs no collective between replicas) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-RHS evals/s (MLS fit + MHD RHS), FP32-mixed vs FP64 on 1 GB300, err vs oracle"
+UNIT = "particle-RHS/s"
+WORKLOAD = "C2"
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# algorithmic flops of the fused RHS fit:
+#   per neighbour inside r_f: 80 moment FMAs + 7 fields x 19 RHS FMAs = 213 FMA
+#   per particle: Cholesky 1140 FMA + 7 forward solves 7x171 + 7 partial back
+#   solves 7x36 FMA, and ~100 flop of right-hand side
+FLOP_PER_NEIGHBOUR = 2 * (80 + 7 * 19)
+FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--sample", type=int, default=2048, help="oracle sample size")
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def aggregate_max(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.remove(self.path)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cfl_dt(w, cfl=0.1):
+    rho = w.U[0]
+    P = (w.gamma - 1.0) * w.U[7]
+    b2 = (w.U[4:7] ** 2).sum(0)
+    cf = np.sqrt(w.gamma * P / rho + b2 / rho)
+    return cfl * float(w.lam.min()) / float(cf.max())
+
+
+def kind_err(a, o, floor_frac=1e-2):
+    num = np.abs(a - o).max(axis=1)
+    den = np.abs(o).max(axis=1)
+    den = np.maximum(den, floor_frac * den.max())
+    return num / den
+
+
+def oracle_leg(w, sample: int, seed: int = 0):
+    """Time the FP64 CPU oracle (fit + RHS with brute-force neighbour lists
+    precomputed, untimed) on a sample of particles; return (rate, info, q, dudt)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    q = np.sort(rng.choice(w.n, min(sample, w.n), replace=False)).astype(np.int64)
+    box = oracle.box_of(w)
+    nb = oracle.neighbors(box, w.pos, w.lam, q)
+    oracle.mhd_rhs(box, w.pos, w.lam, w.U, nb, q[:64], gamma=w.gamma)  # warm
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        out, st = oracle.mhd_rhs(box, w.pos, w.lam, w.U, nb, q, gamma=w.gamma)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > 10.0 or reps >= 50:
+            break
+    rate = reps * len(q) / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    info = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(q)} particles of {w.name} x {reps} repetitions ({el:.1f} s): FP64 "
+                      "Householder-QR fit + RHS, OpenMP over particles, brute-force neighbour "
+                      "lists precomputed outside the timing"}
+    return rate, info, q, out
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import workloads
+    w = workloads.config(args.workload)
+    import oracle
+    rng = np.random.default_rng(1)
+    q = np.sort(rng.choice(w.n, min(args.sample, w.n), replace=False)).astype(np.int64)
+    box = oracle.box_of(w)
+    nb = oracle.neighbors(box, w.pos, w.lam, q)
+    for _ in range(args.warmup):
+        oracle.mhd_rhs(box, w.pos, w.lam, w.U, nb, q, gamma=w.gamma)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.mhd_rhs(box, w.pos, w.lam, w.U, nb, q, gamma=w.gamma)
+    el = time.perf_counter() - t0
+    rate = args.steps * len(q) / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{w.name}: 64^3 jittered lattice, constant lambda, 8 random "
+                                   "Fourier modes", "particles": w.n, "sample_per_step": int(len(q))},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{len(q)} particles per step, FP64 QR fit + RHS, "
+                                       "neighbour lists precomputed"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import workloads
+    import paper_1110_0836_gb300 as phb
+    from paper_1110_0836_gb300 import _lib
+    phb.build()
+    L = _lib.lib()
+
+    w = workloads.config(args.workload)
+    n = w.n
+    dt = cfl_dt(w)
+    vmax = float(np.sqrt((w.U[1:4] ** 2).sum(0)).max())
+    rf_min = 2.3 * float(w.lam.min())
+    skin = max(4.0 * dt * vmax, 0.02 * rf_min)
+    pos0, lam, U0 = phb.tensors_of(w, dev)
+    pos, U = pos0.clone(), U0.clone()
+
+    # exact neighbour count inside r_f (for the algorithmic flop count)
+    plan0 = phb.Plan.for_workload(w, device=dev)
+    phb.build_neighbors(plan0, pos0, lam)
+    nbr_inside = plan0.neighbor_total()
+    del plan0
+
+    plan = phb.Plan.for_workload(w, skin=skin, device=dev)
+    phb.build_neighbors(plan, pos0, lam)
+    mixed = phb.Params(gamma=w.gamma, precision="fp32_mixed")
+    fp64 = phb.Params(gamma=w.gamma, precision="fp64")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def reset():
+        pos.copy_(pos0)
+        U.copy_(U0)
+        flush.zero_()
+
+    def timed_steps(params, k, trace=False):
+        ms = []
+        for _ in range(k):
+            reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            phb.pc_step(plan, params, pos, lam, U, dt)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    plan.reset_status()
+    for _ in range(args.warmup):
+        reset()
+        phb.pc_step(plan, mixed, pos, lam, U, dt)
+    torch.cuda.synchronize()
+    status = plan.read_status()
+    if status & ~_lib.FLAG_FIT_SINGULAR:
+        raise RuntimeError(f"warm-up status word {status:#x}")
+
+    # ---------------- timed region (FP32-mixed)
+    cap = 4 * args.steps + 16
+    L.phb_trace_start(cap)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = int(L.phb_launch_count())
+    with Clocks(local) as clk:
+        ms = timed_steps(mixed, args.steps)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = int(L.phb_launch_count()) - launches0
+    import ctypes as C
+    tr_ms = (C.c_float * cap)()
+    tr_id = (C.c_int32 * cap)()
+    ntr = L.phb_trace_stop(tr_ms, tr_id, cap)
+    clocks = clk.summary()
+    status = plan.read_status()
+    if status & ~_lib.FLAG_FIT_SINGULAR:
+        raise RuntimeError(f"timed-region status word {status:#x} ({_lib.status_string(L.phb_check(status))})")
+    # launches inside the timed region also include the reset/flush (torch kernels, not ours)
+    step_ms = float(np.mean(ms))
+    step_ms_max = aggregate_max(step_ms, world, dev)
+    value = world * 2 * n / (step_ms_max * 1e-3)
+
+    fit_ms = [tr_ms[k] for k in range(max(ntr, 0)) if tr_id[k] == 1]
+    fit_avg = float(np.mean(fit_ms)) if fit_ms else float("nan")
+    flops = FLOP_PER_NEIGHBOUR * nbr_inside + FLOP_PER_PARTICLE * n
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / (fit_avg * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_fit_mixed<kRHS> (fused FP32 MLS fit + MHD RHS)",
+                "launch_ms": fit_avg, "launches": len(fit_ms),
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)"}
+
+    # ---------------- FP64 path, same step (fewer steps: ~35x slower)
+    ms64 = timed_steps(fp64, max(1, min(3, args.steps)))
+    value64 = 2 * n / (float(np.mean(ms64)) * 1e-3)
+
+    # ---------------- single RHS evaluation (lists prebuilt) in both precisions
+    def rhs_ms(params, reps):
+        out = torch.empty((8, n), dtype=torch.float64, device=dev)
+        phb.mhd_rhs(plan, params, pos0, lam, U0, out=out)
+        t = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            phb.mhd_rhs(plan, params, pos0, lam, U0, out=out)
+            e1.record()
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return float(np.mean(t)), out
+
+    phb.build_neighbors(plan, pos0, lam)
+    rhs32_ms, d32 = rhs_ms(mixed, 10)
+    rhs64_ms, d64 = rhs_ms(fp64, 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    phb.build_neighbors(plan, pos0, lam, check_capacity=False)
+    e1.record()
+    e1.synchronize()
+    build_ms = e0.elapsed_time(e1)
+
+    # ---------------- end to end through the API with host buffers
+    hpos = pos0.cpu().pin_memory()
+    hlam = lam.cpu().pin_memory()
+    hU = U0.cpu().pin_memory()
+    opos = torch.empty_like(hpos).pin_memory()
+    oU = torch.empty_like(hU).pin_memory()
+    dpos, dlam, dU = torch.empty_like(pos0), torch.empty_like(lam), torch.empty_like(U0)
+    k_e2e = max(3, min(args.steps, 10))
+    te = []
+    for _ in range(k_e2e):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dpos.copy_(hpos, non_blocking=True)
+        dlam.copy_(hlam, non_blocking=True)
+        dU.copy_(hU, non_blocking=True)
+        phb.pc_step(plan, mixed, dpos, dlam, dU, dt)
+        opos.copy_(dpos, non_blocking=True)
+        oU.copy_(dU, non_blocking=True)
+        torch.cuda.synchronize()
+        te.append(time.perf_counter() - t0)
+    e2e_s = aggregate_max(float(np.mean(te)), world, dev)
+    e2e = {"value": world * 2 * n / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(hpos.numel() + hlam.numel() + hU.numel()) * 8,
+           "d2h_bytes_per_step": int(opos.numel() + oU.numel()) * 8}
+
+    # ---------------- CPU oracle and accuracy (rank 0, one GPU)
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_oracle:
+        rate, cpu, q, o = oracle_leg(w, args.sample)
+        err = {"fp32_mixed": float(kind_err(d32.cpu().numpy()[:, q], o).max()),
+               "fp64": float(kind_err(d64.cpu().numpy()[:, q], o).max()),
+               "metric": "max over fields of max_i|a-o| / max_i|o| on the oracle sample"}
+
+    fst = torch.empty(n, dtype=torch.int32, device=dev)
+    phb.mhd_rhs(plan, mixed, pos0, lam, U0, fit_status=fst)
+    routed = float((fst == 2).float().mean().item())
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 storage, FP32 fit, FP64 routing)",
+        "data": "synthetic",
+        "config": {"workload": f"{w.name}: 64^3 = 262,144 jittered-lattice particles in the periodic "
+                               "unit box, constant lambda = 1/64, fields = background + 8 random "
+                               "Fourier modes (k <= 4, amplitude 1e-2)",
+                   "step": "one predictor-corrector step: binning + neighbour lists (skin) + 2 fused "
+                           "FP32-mixed fit/RHS evaluations + Heun update; 2 particle-RHS per particle",
+                   "dt": dt, "skin": skin, "neighbours_per_particle": nbr_inside / n,
+                   "l2": "flushed (256 MiB write) before every timed step; state reset per step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": float(np.mean(ms64)),
+                 "speedup_fp32_mixed_over_fp64": value / value64},
+        "rhs_only": {"fp32_mixed_ms": rhs32_ms, "fp64_ms": rhs64_ms,
+                     "fp32_mixed_value": n / (rhs32_ms * 1e-3), "fp64_value": n / (rhs64_ms * 1e-3),
+                     "neighbour_build_ms": build_ms},
+        "err_vs_oracle": err,
+        "routed_to_fp64": routed,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * phurbas.h - C ABI of the GB300 (sm_103a) particle right-hand-side library.
+ *
+ * The library evaluates the data-parallel hot path of the Phurbas meshless
+ * Lagrangian MHD method (McNally, Maron & Mac Low, Paper II, arXiv:1110.0836):
+ *   - strict fixed-radius neighbour sets, r_f,i = 2.3 lambda_i (Sec. 2, Sec. 2.1);
+ *   - the local third-order interpolating moving-least-squares fit of rho, V,
+ *     B and sigma (Sec. 2; Acknowledgements: interpolating fits), its
+ *     derivatives, and the ideal-MHD Lagrangian time derivatives with bulk
+ *     viscosity and diffusive div B correction (Sec. 2; App. A);
+ *   - the second-order predictor-corrector step (Sec. 2, Sec. 4.2);
+ *   - a hand-written adjoint of the fit + right-hand side (not in the paper).
+ *
+ * Conventions for every entry point:
+ *   - Array arguments named pos, lambda, U, dudt, grad, hess, gbar, Ubar, xbar,
+ *     zeta, eta, ws, status_word are DEVICE pointers owned by the caller.
+ *     Layout is structure-of-arrays float64: pos [3][n], U [8][n] with field
+ *     order (rho, Vx, Vy, Vz, Bx, By, Bz, sigma), sigma the internal energy
+ *     density with P = (gamma - 1) sigma (reading of Sec. 2: the paper names
+ *     sigma but defers the equation of state to Paper I).
+ *   - Particle index i is the caller's index; internally particles are
+ *     re-ordered by cell, and results are returned in the caller's order.
+ *   - The library allocates no device memory: all scratch lives in the
+ *     caller-provided workspace `ws` of `ws_bytes` bytes, whose size is given
+ *     by phb_workspace_size.  Neighbour lists live in the workspace between
+ *     calls; a workspace belongs to one plan.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and performs no host synchronisation, so call sequences
+ *     can be captured into CUDA graphs.
+ *   - Errors found on the host are returned as phb_status.  Errors found on
+ *     the device are OR-ed as PHB_FLAG_* bits into *status_word (an int32 in
+ *     device memory that the caller zeroes); read it after synchronising and
+ *     map it with phb_check.  No call throws, traps or spins without bound.
+ */
+#ifndef PHURBAS_H
+#define PHURBAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* phb_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  PHB_OK = 0,
+  PHB_ERR_INVALID_ARG = 1, /* null pointer, n <= 0, bad box/lambda range, r_f >= len/2 */
+  PHB_ERR_WORKSPACE = 2,   /* ws_bytes smaller than phb_workspace_size */
+  PHB_ERR_CUDA = 3,        /* a CUDA launch or memset failed */
+  PHB_ERR_CAPACITY = 4,    /* neighbour list larger than plan.nbr_capacity */
+  PHB_ERR_SKIN = 5,        /* predictor moved a particle by more than skin/2 */
+  PHB_WARN_FIT = 6,        /* at least one fit was singular (its derivatives are 0) */
+  PHB_ERR_TIMEOUT = 7,     /* a bounded device wait gave up */
+  PHB_ERR_NONFINITE = 8    /* a non-finite input or result was seen */
+} phb_status;
+
+/* Device status-word bits (OR-ed by kernels). */
+#define PHB_FLAG_CAPACITY 0x01
+#define PHB_FLAG_SKIN 0x02
+#define PHB_FLAG_FIT_SINGULAR 0x04
+#define PHB_FLAG_NONFINITE 0x08
+#define PHB_FLAG_TIMEOUT 0x10
+#define PHB_FLAG_LAMBDA_RANGE 0x20 /* a lambda outside the plan's [lambda_min, lambda_max] */
+
+/* Periodic or open box [lo, lo + len) per axis.  On a periodic axis offsets
+ * use the minimum image d - len * nearbyint(d / len).  Particles on an open
+ * axis may lie anywhere; cells clamp them to the box. */
+typedef struct {
+  double lo[3];
+  double len[3];
+  int32_t periodic[3];
+  int32_t pad_;
+} phb_box;
+
+typedef enum { PHB_FP64 = 0, PHB_FP32_MIXED = 1 } phb_precision;
+
+/* Method parameters. */
+typedef struct {
+  double gamma;          /* adiabatic index, P = (gamma - 1) sigma */
+  int32_t weight_kind;   /* MLS weight: 0 = (1 - s^2)^2 with s = |d| / r_f,i; 1 = unweighted */
+  int32_t precision;     /* phb_precision */
+  double cond_threshold; /* FP32_MIXED: fits whose conditioning estimate
+                            (max L_kk / min L_kk)^2 of the Jacobi-scaled
+                            Cholesky factor exceeds this are redone in FP64 */
+  const double* zeta;    /* bulk viscosity per particle [n], or NULL for 0 */
+  const double* eta;     /* div B diffusivity per particle [n], or NULL for 0 */
+} phb_params;
+
+/* A plan fixes the particle count, box, radius law and the cell grid.  The
+ * caller fills the input fields and calls phb_plan_init, which fills the rest.
+ * Every lambda passed later must lie in [lambda_min, lambda_max]. */
+typedef struct {
+  /* inputs */
+  phb_box box;
+  int64_t n;             /* number of particles */
+  double rf_factor;      /* r_f,i = rf_factor * lambda_i (2.3 in the paper, Sec. 2) */
+  double skin;           /* list radius = r_f,i + skin (0: exact lists) */
+  double lambda_min;
+  double lambda_max;
+  int64_t nbr_capacity;  /* entries reserved for neighbour lists (sum of |N(i)|) */
+  double cell_frac;      /* cell edge / (rf_factor*lambda_min + skin); 0 = default 0.5 */
+  /* filled by phb_plan_init */
+  double cell[3];        /* cell edge per axis */
+  int32_t ncell[3];      /* cells per axis */
+  int32_t nbrick[3];     /* 4x4x4-cell bricks per axis */
+  int64_t nkeys;         /* cell-key space: bricks * 64 */
+  double screen_margin;  /* absolute distance margin of the FP32 neighbour screen */
+  size_t ws_bytes;       /* workspace bytes needed for every operation */
+  size_t ws_off[32];     /* byte offsets of the workspace regions (internal) */
+} phb_plan;
+
+/* Operations for phb_workspace_size. */
+#define PHB_OP_ALL 0
+
+/* Fill the derived fields of *plan.  Host only.  Returns PHB_ERR_INVALID_ARG
+ * for n <= 0, non-positive lengths or lambda range, rf_factor <= 0, skin < 0,
+ * or when the list radius of lambda_max reaches half a periodic box length. */
+phb_status phb_plan_init(phb_plan* plan);
+
+/* Workspace bytes needed by `op` under `plan` (0 for an invalid plan). */
+size_t phb_workspace_size(const phb_plan* plan, int32_t op);
+
+/* Text for a phb_status code (static storage). */
+const char* phb_status_string(int32_t status);
+
+/* Map a device status word (already copied to the host) to the most severe
+ * phb_status it encodes. */
+phb_status phb_check(int32_t status_word);
+
+/* Build the neighbour sets of all particles (Sec. 2; Sec. 2.1: strict,
+ * fixed radius, not mutual, no iteration):
+ *   N(i) = { j != i : ((dx*dx + dy*dy) + dz*dz) < r*r },  r = rf_factor*lambda_i + skin,
+ * with d = pos_j - pos_i (minimum image on periodic axes), evaluated in FP64
+ * in exactly this order without fused multiply-adds, so the sets are
+ * bit-exact.  Bins particles into the plan's cell grid with a counting sort
+ * (stable by caller index) and stores the lists in the workspace.  Device
+ * errors: PHB_FLAG_CAPACITY when the lists exceed plan->nbr_capacity (lists
+ * are then incomplete), PHB_FLAG_LAMBDA_RANGE.  pos [3][n], lambda [n]. */
+phb_status phb_build_neighbors(const phb_plan* plan, const double* pos, const double* lambda,
+                               void* ws, size_t ws_bytes, int32_t* status_word,
+                               phb_stream_t stream);
+
+/* Copy the lists of the last phb_build_neighbors out in the caller's
+ * numbering: off [n+1] (int64, device), idx [capacity] (int32, device) with
+ * the neighbours of i at idx[off[i] .. off[i+1]) in increasing index order.
+ * Returns PHB_ERR_CAPACITY (and writes nothing) when idx_capacity is too
+ * small for the total, which is read from the device (synchronising). */
+phb_status phb_export_neighbors(const phb_plan* plan, const void* ws, int64_t* off, int32_t* idx,
+                                int64_t idx_capacity, phb_stream_t stream);
+
+/* Total neighbour-list entries of the last build (synchronises). */
+int64_t phb_neighbor_total(const phb_plan* plan, const void* ws, phb_stream_t stream);
+
+/* MLS fit derivatives of all 8 fields (Sec. 2: local, third-order polynomial
+ * moving least squares over N(i); interpolating: the constant term is U_i):
+ * minimise sum_j w_j (p(q_j).c - (U_j - U_i))^2 with q_j = d_ij / lambda_i,
+ * p = the 19 monomials of degree 1..3, w_j = (1 - |d_ij|^2 / r_f,i^2)^2.
+ * grad [8][3][n]: dU/dx_a = c_a / lambda_i;  hess [8][6][n] (xx,xy,xz,yy,yz,zz,
+ * may be NULL): c_ab / lambda_i^2, doubled on the diagonal.  fit_status [n]
+ * (may be NULL): 0 ok, 1 singular (fewer than 19 neighbours or a failed
+ * factorisation: derivatives 0), 2 solved in FP64 after FP32 routing.
+ * Uses the lists of the last phb_build_neighbors; entries farther than r_f,i
+ * (skin) are skipped. */
+phb_status phb_mls_derivs(const phb_plan* plan, const phb_params* params, const double* pos,
+                          const double* lambda, const double* U, void* ws, size_t ws_bytes,
+                          double* grad, double* hess, int32_t* fit_status, int32_t* status_word,
+                          phb_stream_t stream);
+
+/* Ideal-MHD Lagrangian time derivatives (Sec. 2; App. A), mu_0 = 1:
+ *   Drho/Dt   = -rho div V
+ *   DV/Dt     = [-(gamma-1) grad sigma + (curl B) x B] / rho + zeta_i grad(div V)
+ *   DB/Dt     = (B.grad) V - B div V + eta_i grad(div B)
+ *   Dsigma/Dt = -gamma sigma div V + rho zeta_i (div V)^2
+ * from the fused fit (as phb_mls_derivs) at every particle.  dudt [8][n].
+ * dx/dt = V needs no call.  fit_status as in phb_mls_derivs. */
+phb_status phb_mhd_rhs(const phb_plan* plan, const phb_params* params, const double* pos,
+                       const double* lambda, const double* U, void* ws, size_t ws_bytes,
+                       double* dudt, int32_t* fit_status, int32_t* status_word,
+                       phb_stream_t stream);
+
+/* One second-order predictor-corrector step in place (Sec. 2; read as Heun):
+ *   Y^p = Y^n + dt F(Y^n);  Y^{n+1} = Y^n + dt/2 (F(Y^n) + F(Y^p)),
+ * Y = (x, U), dx/dt = V, lambda unchanged.  Builds the neighbour lists once
+ * at x^n with radius r_f + plan->skin and filters them at r_f for both
+ * evaluations; if the predictor moves any particle by more than skin/2 it
+ * sets PHB_FLAG_SKIN (the step used incomplete sets; rebuild with a larger
+ * skin).  pos [3][n] and U [8][n] are updated in place. */
+phb_status phb_pc_step(const phb_plan* plan, const phb_params* params, double* pos,
+                       const double* lambda, double* U, double dt, void* ws, size_t ws_bytes,
+                       int32_t* status_word, phb_stream_t stream);
+
+/* Reverse-mode derivative of the fused fit + right-hand side (not in the
+ * paper): given gbar = dL/d(dudt) [8][n], returns Ubar = dL/dU [8][n] and
+ * xbar = dL/dpos [3][n] with the neighbour sets of the last build held fixed
+ * and lambda treated as a constant.  Recomputes each factorisation (no stored
+ * factors); contributions to neighbours are gathered through a reverse
+ * neighbour list, so the result is deterministic.  FP64. */
+phb_status phb_rhs_adjoint(const phb_plan* plan, const phb_params* params, const double* pos,
+                           const double* lambda, const double* U, const double* gbar,
+                           void* ws, size_t ws_bytes, double* Ubar, double* xbar,
+                           int32_t* status_word, phb_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHURBAS_H */

@@ -1,0 +1,46 @@
+/*
+ * phurbas_bench.h - measurement helper of libphurbas (not part of the method).
+ *
+ * phb_fma_peak runs a fixed, dependency-light chain of fused multiply-adds on
+ * every SM so that the benchmark can measure the ALU peak that the fused fit
+ * kernels are bounded by (the MLS accumulation is plain FP32 / FP64 FMA work,
+ * not a tensor-core contraction).  precision: 0 = FP64, 1 = FP32.  Each of
+ * blocks x 256 threads performs iters x 16 FMAs; `sink` (device, >= blocks*256
+ * elements of the chosen type) receives the results so nothing is optimised
+ * away.  Asynchronous on `stream`; returns 0, or 1 for invalid arguments, 3 on
+ * a launch error.
+ */
+#ifndef PHURBAS_BENCH_H
+#define PHURBAS_BENCH_H
+
+#include <stdint.h>
+
+#include "phurbas.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+int phb_fma_peak(int32_t precision, int32_t blocks, int32_t iters, void* sink, phb_stream_t stream);
+
+/* Number of kernels this library has launched since load (host-side count,
+ * incremented at every launch site). */
+int64_t phb_launch_count(void);
+
+/* Event trace of the fused fit kernel.  phb_trace_start(capacity) creates
+ * `capacity` CUDA event pairs (timing enabled) on the current device and arms
+ * the trace; every later launch of the fused FP32-mixed or FP64 fit kernel
+ * records one pair around itself on its own stream, until the pairs run out.
+ * phb_trace_stop(ms, kernel_ids, capacity) synchronises on the last recorded
+ * event, writes each launch's duration in milliseconds and kernel id (1 =
+ * FP32-mixed fused fit, 2 = FP64 fused fit over all particles, 3 = FP64 fit of
+ * the routed queue), destroys the events and returns the number of launches
+ * recorded (or -1 on a CUDA error).  Not thread-safe; one trace at a time. */
+int phb_trace_start(int32_t capacity);
+int phb_trace_stop(float* ms, int32_t* kernel_ids, int32_t capacity);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,16 @@
+"""GB300 (sm_103a) library for the Phurbas particle right-hand side.
+
+Hot path (all in libphurbas, C ABI in include/phurbas.h): cell binning and the
+strict fixed-radius neighbour search, the fused third-order interpolating MLS
+fit + ideal-MHD Lagrangian right-hand side (FP32-mixed with FP64 routing, or
+FP64), the Heun predictor-corrector step, and the hand-written adjoint.
+"""
+from ._lib import PhbError  # noqa: F401
+from .api import (FIELDS, Params, Plan, build_neighbors, export_neighbors, mhd_rhs,  # noqa: F401
+                  mls_derivs, pc_step, rhs, rhs_adjoint, tensors_of)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libphurbas.so in-tree for sm_103a."""
+    from ._build import build as _b
+    return _b(force=force, verbose=verbose)

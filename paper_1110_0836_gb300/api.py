@@ -1,0 +1,238 @@
+"""Torch-facing wrappers of the C ABI (include/phurbas.h).
+
+PyTorch provides device memory and the current CUDA stream; every step of the
+computation runs in libphurbas.  Arrays are float64 CUDA tensors in
+structure-of-arrays layout: pos [3, n], lam [n], U [8, n] with fields
+(rho, Vx, Vy, Vz, Bx, By, Bz, sigma).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import PHB_FP32_MIXED, PHB_FP64, PhbError, check
+
+FIELDS = ("rho", "Vx", "Vy", "Vz", "Bx", "By", "Bz", "sigma")
+
+
+def _stream() -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _need(t: torch.Tensor, shape, name: str, dtype=torch.float64) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name}: expected contiguous {dtype} {tuple(shape)}, got {t.dtype} "
+                         f"{tuple(t.shape)} (contiguous={t.is_contiguous()})")
+    return t
+
+
+@dataclass
+class Params:
+    """Method parameters (phb_params)."""
+    gamma: float = 5.0 / 3.0
+    precision: str = "fp32_mixed"     # or "fp64"
+    weight_kind: int = 0              # 0: (1 - s^2)^2, 1: unweighted
+    cond_threshold: float = 300.0     # FP32-mixed: route fits above this estimate to FP64
+    zeta: torch.Tensor | None = None  # bulk viscosity [n] (caller order) or None
+    eta: torch.Tensor | None = None   # div B diffusivity [n] or None
+
+    def c(self) -> _lib.Params:
+        p = _lib.Params()
+        p.gamma = float(self.gamma)
+        p.weight_kind = int(self.weight_kind)
+        p.precision = PHB_FP64 if self.precision == "fp64" else PHB_FP32_MIXED
+        if self.precision not in ("fp64", "fp32_mixed"):
+            raise ValueError(f"precision must be 'fp64' or 'fp32_mixed', not {self.precision!r}")
+        p.cond_threshold = float(self.cond_threshold)
+        p.zeta = None if self.zeta is None else self.zeta.data_ptr()
+        p.eta = None if self.eta is None else self.eta.data_ptr()
+        return p
+
+
+class Plan:
+    """A phb_plan plus its device workspace and status word."""
+
+    def __init__(self, box_lo, box_len, periodic, n: int, lambda_min: float, lambda_max: float,
+                 rf_factor: float = 2.3, skin: float = 0.0, nbr_capacity: int | None = None,
+                 cell_frac: float = 0.0, device="cuda"):
+        self.device = torch.device(device)
+        self.args = dict(box_lo=tuple(map(float, box_lo)), box_len=tuple(map(float, box_len)),
+                         periodic=tuple(int(bool(p)) for p in periodic), n=int(n),
+                         lambda_min=float(lambda_min), lambda_max=float(lambda_max),
+                         rf_factor=float(rf_factor), skin=float(skin), cell_frac=float(cell_frac))
+        if nbr_capacity is None:
+            # ~51 neighbours at r_f = 2.3 lambda and uniform density; margin for
+            # density contrast and the skin shell
+            grow = ((rf_factor * lambda_min + skin) / (rf_factor * lambda_min)) ** 3
+            nbr_capacity = int(n * 72 * grow) + 1024
+        self._init(int(nbr_capacity))
+        self.status_word = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def _init(self, capacity: int):
+        a = self.args
+        p = _lib.Plan()
+        for k in range(3):
+            p.box.lo[k] = a["box_lo"][k]
+            p.box.len[k] = a["box_len"][k]
+            p.box.periodic[k] = a["periodic"][k]
+        p.n = a["n"]
+        p.rf_factor = a["rf_factor"]
+        p.skin = a["skin"]
+        p.lambda_min = a["lambda_min"]
+        p.lambda_max = a["lambda_max"]
+        p.nbr_capacity = capacity
+        p.cell_frac = a["cell_frac"]
+        check(_lib.lib().phb_plan_init(C.byref(p)), "phb_plan_init")
+        self.c = p
+        self.ws = torch.empty(int(p.ws_bytes), dtype=torch.uint8, device=self.device)
+
+    @classmethod
+    def for_workload(cls, w, skin: float = 0.0, nbr_capacity: int | None = None, device="cuda",
+                     **kw):
+        return cls(w.box_lo, w.box_len, w.periodic, w.n, float(w.lam.min()), float(w.lam.max()),
+                   skin=skin, nbr_capacity=nbr_capacity, device=device, **kw)
+
+    @property
+    def n(self) -> int:
+        return int(self.c.n)
+
+    @property
+    def capacity(self) -> int:
+        return int(self.c.nbr_capacity)
+
+    def reset_status(self):
+        self.status_word.zero_()
+
+    def read_status(self) -> int:
+        """Synchronise and return the device status word."""
+        return int(self.status_word.item())
+
+    def raise_status(self, what: str = "", allow=(_lib.FLAG_FIT_SINGULAR,)) -> int:
+        w = self.read_status()
+        bad = w & ~sum(allow)
+        if bad:
+            raise PhbError(int(_lib.lib().phb_check(bad)), what or "device status")
+        return w
+
+    def neighbor_total(self) -> int:
+        return int(_lib.lib().phb_neighbor_total(C.byref(self.c), _ptr(self.ws), _stream()))
+
+
+def build_neighbors(plan: Plan, pos: torch.Tensor, lam: torch.Tensor, check_capacity: bool = True):
+    """Neighbour lists of all particles (phb_build_neighbors).  With
+    check_capacity, synchronises and grows the plan's list capacity if needed."""
+    n = plan.n
+    _need(pos, (3, n), "pos")
+    _need(lam, (n,), "lam")
+    L = _lib.lib()
+    check(L.phb_build_neighbors(C.byref(plan.c), _ptr(pos), _ptr(lam), _ptr(plan.ws),
+                                plan.ws.numel(), _ptr(plan.status_word), _stream()),
+          "phb_build_neighbors")
+    if check_capacity:
+        w = plan.read_status()
+        if w & _lib.FLAG_CAPACITY:
+            total = plan.neighbor_total()
+            plan._init(int(total * 1.05) + 1024)
+            plan.reset_status()
+            check(L.phb_build_neighbors(C.byref(plan.c), _ptr(pos), _ptr(lam), _ptr(plan.ws),
+                                        plan.ws.numel(), _ptr(plan.status_word), _stream()),
+                  "phb_build_neighbors")
+            w = plan.read_status()
+        if w & ~_lib.FLAG_FIT_SINGULAR:
+            raise PhbError(int(L.phb_check(w)), "phb_build_neighbors")
+
+
+def export_neighbors(plan: Plan):
+    """(off int64 [n+1], idx int32 [total]) in caller numbering, ascending per list."""
+    total = plan.neighbor_total()
+    off = torch.empty(plan.n + 1, dtype=torch.int64, device=plan.device)
+    idx = torch.empty(max(total, 1), dtype=torch.int32, device=plan.device)
+    check(_lib.lib().phb_export_neighbors(C.byref(plan.c), _ptr(plan.ws), _ptr(off), _ptr(idx),
+                                          idx.numel(), _stream()), "phb_export_neighbors")
+    return off, idx[:total]
+
+
+def mls_derivs(plan: Plan, params: Params, pos, lam, U, hess: bool = True, out=None):
+    """MLS derivatives: grad [8,3,n], hess [8,6,n] (or None), fit_status [n] int32."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    if out is None:
+        g = torch.empty((8, 3, n), dtype=torch.float64, device=plan.device)
+        h = torch.empty((8, 6, n), dtype=torch.float64, device=plan.device) if hess else None
+        st = torch.empty(n, dtype=torch.int32, device=plan.device)
+    else:
+        g, h, st = out
+    pc = params.c()
+    check(_lib.lib().phb_mls_derivs(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                                    _ptr(plan.ws), plan.ws.numel(), _ptr(g), _ptr(h), _ptr(st),
+                                    _ptr(plan.status_word), _stream()), "phb_mls_derivs")
+    return g, h, st
+
+
+def mhd_rhs(plan: Plan, params: Params, pos, lam, U, out=None, fit_status=None):
+    """Lagrangian time derivatives dU/dt [8, n] (phb_mhd_rhs); returns (dudt, fit_status)."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    if out is None:
+        out = torch.empty((8, n), dtype=torch.float64, device=plan.device)
+    pc = params.c()
+    check(_lib.lib().phb_mhd_rhs(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                                 _ptr(plan.ws), plan.ws.numel(), _ptr(out), _ptr(fit_status),
+                                 _ptr(plan.status_word), _stream()), "phb_mhd_rhs")
+    return out, fit_status
+
+
+def pc_step(plan: Plan, params: Params, pos, lam, U, dt: float):
+    """One predictor-corrector step in place (phb_pc_step).  Needs plan.skin > 2 dt max|V|."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    pc = params.c()
+    check(_lib.lib().phb_pc_step(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                                 float(dt), _ptr(plan.ws), plan.ws.numel(), _ptr(plan.status_word),
+                                 _stream()), "phb_pc_step")
+
+
+def rhs_adjoint(plan: Plan, params: Params, pos, lam, U, gbar, Ubar=None, xbar=None):
+    """dL/dU [8, n] and dL/dpos [3, n] for gbar = dL/d(dudt) (phb_rhs_adjoint), with the
+    neighbour lists of the last build held fixed."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    _need(gbar, (8, n), "gbar")
+    if Ubar is None:
+        Ubar = torch.empty((8, n), dtype=torch.float64, device=plan.device)
+    if xbar is None:
+        xbar = torch.empty((3, n), dtype=torch.float64, device=plan.device)
+    pc = params.c()
+    check(_lib.lib().phb_rhs_adjoint(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                                     _ptr(gbar), _ptr(plan.ws), plan.ws.numel(), _ptr(Ubar),
+                                     _ptr(xbar), _ptr(plan.status_word), _stream()),
+          "phb_rhs_adjoint")
+    return Ubar, xbar
+
+
+def tensors_of(w, device="cuda"):
+    """(pos, lam, U) float64 CUDA tensors of a workloads.Workload."""
+    dev = torch.device(device)
+    return (torch.as_tensor(w.pos, device=dev).contiguous(),
+            torch.as_tensor(w.lam, device=dev).contiguous(),
+            torch.as_tensor(w.U, device=dev).contiguous())
+
+
+def rhs(w, params: Params | None = None, skin: float = 0.0, device="cuda"):
+    """Convenience: plan, neighbours and dU/dt for a workloads.Workload."""
+    params = params or Params(gamma=w.gamma)
+    plan = Plan.for_workload(w, skin=skin, device=device)
+    pos, lam, U = tensors_of(w, device)
+    build_neighbors(plan, pos, lam)
+    st = torch.empty(w.n, dtype=torch.int32, device=plan.device)
+    dudt, _ = mhd_rhs(plan, params, pos, lam, U, fit_status=st)
+    return dudt, st, plan

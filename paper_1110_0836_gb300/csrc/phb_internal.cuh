@@ -1,0 +1,218 @@
+// Internal declarations shared by the CUDA translation units of libphurbas.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/phurbas.h"
+
+namespace phb {
+
+constexpr int kNF = 8;      // fields rho, Vx, Vy, Vz, Bx, By, Bz, sigma
+constexpr int kRec = 24;    // floats per FP32 particle record (6 x float4)
+constexpr int kEdgeAdj = 11;  // doubles per neighbour edge in the adjoint (8 fields + 3 axes)
+
+// Workspace regions (byte offsets in plan->ws_off).  The PC-step and adjoint
+// regions share storage (never used at the same time).
+enum Region {
+  R_MISC = 0,    // int32 [64]: 0 = FP64 route-queue length
+  R_KEYS,        // int32 [n]   cell key of each caller particle
+  R_PERM,        // int32 [n]   slot -> caller index
+  R_INV,         // int32 [n]   caller index -> slot
+  R_CELL,        // int32 [nkeys+1] cell start (exclusive scan of counts)
+  R_CURSOR,      // int32 [nkeys]   scatter cursors
+  R_SCAN,        // int64 [scan blocks] block sums
+  R_SPOS,        // double [3][n] positions, slot order
+  R_SLAM,        // double [n]    lambda, slot order
+  R_SU,          // double [8][n] fields, slot order
+  R_REC,         // float [n][24] FP32 hi/lo records
+  R_SCREEN,      // float4 [n]   wrapped FP32 positions for the neighbour screen
+  R_NCNT,        // int32 [n+1]  neighbour counts
+  R_OFF,         // int64 [n+1]  CSR offsets (slot order)
+  R_IDX,         // int32 [capacity] neighbour slots
+  R_QUEUE,       // int32 [n]    slots routed to FP64
+  R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
+  R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
+  R_PC_Y0,       // double [11][n] saved x^n, U^n (slot order) -- PC step
+  R_ADJ_EDGE,    // double [capacity][11] per-edge adjoint contributions -- adjoint
+  R_ADJ_ROFF,    // int64 [n+1] reverse-list offsets                     -- adjoint
+  R_ADJ_RIDX,    // int64 [capacity] reverse-list edge ids               -- adjoint
+  R_ADJ_RCNT,    // int32 [n+1] reverse-list counts / cursors            -- adjoint
+  R_END_COMMON,  // end of the common part (prefix for RHS / derivs)
+  R_END,         // end of everything
+  R_COUNT
+};
+static_assert(R_COUNT <= 32, "ws_off has 32 entries");
+
+template <typename T>
+__host__ __device__ inline T* region(const phb_plan* p, void* ws, Region r) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + p->ws_off[r]);
+}
+template <typename T>
+__host__ __device__ inline const T* region(const phb_plan* p, const void* ws, Region r) {
+  return reinterpret_cast<const T*>(static_cast<const char*>(ws) + p->ws_off[r]);
+}
+
+// Plain-old-data view of the plan handed to kernels by value.
+struct Grid {
+  double lo[3], len[3], inv_cell[3];
+  int32_t periodic[3], ncell[3], nbrick[3];
+  int32_t n;
+  double rf_factor, skin;
+  double lambda_min, lambda_max;
+  float screen_margin;
+  int64_t capacity;
+};
+
+Grid make_grid(const phb_plan* p);
+
+__device__ __forceinline__ float phb_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double phb_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+__device__ __forceinline__ void raise_flag(int32_t* status_word, int32_t bits) {
+  if (status_word) atomicOr(status_word, bits);
+}
+
+// Cell coordinate on one axis: floor((x - lo) / cell), wrapped (periodic) or
+// clamped (open) into [0, ncell).
+__device__ __forceinline__ int cell_coord(const Grid& g, int a, double x) {
+  double u = floor((x - g.lo[a]) * g.inv_cell[a]);
+  int nc = g.ncell[a];
+  if (g.periodic[a]) {
+    double w = u - nc * floor(u / nc);
+    int c = static_cast<int>(w);
+    return c >= nc ? nc - 1 : (c < 0 ? 0 : c);
+  }
+  return u < 0 ? 0 : (u >= nc ? nc - 1 : static_cast<int>(u));
+}
+
+// 4x4x4 bricks in x-major order, Morton order of the 64 cells inside a brick.
+__device__ __forceinline__ int32_t cell_key(const Grid& g, int cx, int cy, int cz) {
+  int bx = cx >> 2, by = cy >> 2, bz = cz >> 2;
+  int x = cx & 3, y = cy & 3, z = cz & 3;
+  int m = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2) | ((x & 2) << 2) | ((y & 2) << 3) | ((z & 2) << 4);
+  return ((bx * g.nbrick[1] + by) * g.nbrick[2] + bz) * 64 + m;
+}
+
+// Minimum-image FP64 offset, d - len * nearbyint(d / len), correctly rounded
+// at every step and without contraction (bit-identical to the definition).
+__device__ __forceinline__ double min_image64(double d, double len, int periodic) {
+  if (periodic) d = __dsub_rn(d, __dmul_rn(len, rint(__ddiv_rn(d, len))));
+  return d;
+}
+
+// Squared FP64 distance ((dx*dx + dy*dy) + dz*dz), same evaluation order.
+__device__ __forceinline__ double dist2_exact(const Grid& g, const double* spos, int n, int s,
+                                              int t) {
+  double dx = min_image64(__dsub_rn(spos[t], spos[s]), g.len[0], g.periodic[0]);
+  double dy = min_image64(__dsub_rn(spos[n + t], spos[n + s]), g.len[1], g.periodic[1]);
+  double dz = min_image64(__dsub_rn(spos[2 * n + t], spos[2 * n + s]), g.len[2], g.periodic[2]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// List radius r = rf_factor * lambda + skin (two roundings, no contraction).
+__device__ __forceinline__ double list_radius(const Grid& g, double lam) {
+  return __dadd_rn(__dmul_rn(g.rf_factor, lam), g.skin);
+}
+
+// a - b with minimum image for FP32 hi/lo pairs (a = ah + al, b = bh + bl).
+// The hi difference is split exactly (TwoSum) so that a wrap by k box
+// lengths, exact by Sterbenz, loses nothing; accurate to ~1 ulp of the result.
+__device__ __forceinline__ float mi_diff32(float ah, float al, float bh, float bl, float len_h,
+                                           float len_l, float inv_len) {
+  float s = ah - bh;
+  float bp = s - ah;
+  float e = (ah - (s - bp)) + (-bh - bp);
+  float k = rintf(s * inv_len);
+  float t = fmaf(-k, len_h, s);
+  return t + (((al - bl) + e) - k * len_l);
+}
+
+// ------------------------------------------------------------ host helpers
+cudaError_t scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t count,
+                                      int64_t* block_sums, cudaStream_t st);
+cudaError_t scan_exclusive_i32(int32_t* data, int64_t count, int64_t* block_sums, cudaStream_t st);
+int64_t scan_blocks(int64_t count);
+
+phb_status check_common(const phb_plan* plan, const void* ws, size_t ws_bytes, size_t need);
+phb_status launch_status(cudaError_t e);
+
+// Gather caller-order pos, lambda, U into slot order (FP64 copies and FP32
+// hi/lo records).  U may be NULL (positions only).
+cudaError_t gather_sorted(const phb_plan* plan, const Grid& g, const double* pos,
+                          const double* lambda, const double* U, void* ws, int32_t* status_word,
+                          cudaStream_t st);
+
+cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const double* lam, void* ws,
+                                 int32_t* status_word, cudaStream_t st);
+
+// FP32 hi/lo split of an FP64 value.
+__device__ __forceinline__ void split_hl(double v, float& h, float& l) {
+  h = __double2float_rn(v);
+  l = __double2float_rn(v - static_cast<double>(h));
+}
+
+// Write the 6-float4 record of slot s: (xh,yh,zh,0) (xl,yl,zl,0)
+// (rho,sigma,Vx,Vy)_h (rho,sigma,Vx,Vy)_l (Vz,Bx,By,Bz)_h (Vz,Bx,By,Bz)_l.
+__device__ __forceinline__ void write_record(float* rec, int64_t s, const double (&x)[3],
+                                             const double (&u)[8]) {
+  float xh[3], xl[3], uh[8], ul[8];
+  for (int a = 0; a < 3; ++a) split_hl(x[a], xh[a], xl[a]);
+  for (int f = 0; f < 8; ++f) split_hl(u[f], uh[f], ul[f]);
+  float4* r = reinterpret_cast<float4*>(rec) + 6 * s;
+  r[0] = make_float4(xh[0], xh[1], xh[2], 0.f);
+  r[1] = make_float4(xl[0], xl[1], xl[2], 0.f);
+  r[2] = make_float4(uh[0], uh[7], uh[1], uh[2]);
+  r[3] = make_float4(ul[0], ul[7], ul[1], ul[2]);
+  r[4] = make_float4(uh[3], uh[4], uh[5], uh[6]);
+  r[5] = make_float4(ul[3], ul[4], ul[5], ul[6]);
+}
+
+// Fit + RHS / derivatives in slot order; outputs scattered to caller order
+// through `perm` when out_perm is non-null, else written in slot order.
+enum class FitMode { kRHS = 0, kDerivs = 1 };
+struct FitArgs {
+  Grid g;
+  int32_t n;
+  const int32_t* perm_in;      // slot -> caller index for zeta / eta (null: identity)
+  const int32_t* perm_out;     // slot -> caller index for outputs (null: slot order)
+  const double* spos;          // [3][n]
+  const double* slam;          // [n]
+  const double* sU;            // [8][n]
+  const float* rec;            // [n][24]
+  const int64_t* off;          // [n+1]
+  const int32_t* idx;          // [capacity]
+  double gamma;
+  int32_t weight_kind;
+  float cond_threshold;
+  const double* zeta;          // caller order (indexed through perm_in) or null
+  const double* eta;
+  double* dudt;                // [8][n]
+  double* grad;                // [8][3][n]
+  double* hess;                // [8][6][n] or null
+  int32_t* fit_status;         // [n] or null
+  int32_t* queue;              // FP64 route queue
+  int32_t* queue_len;
+  int32_t* status_word;
+};
+
+cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, cudaStream_t st);
+// FP64 fused fit over all slots (list == null) or over list[0 .. *list_len).
+cudaError_t launch_fit_fp64(const FitArgs& a, FitMode mode, const int32_t* list,
+                            const int32_t* list_len, cudaStream_t st);
+int num_sms();
+
+// Launch bookkeeping (measurement helpers, see include/phurbas_bench.h).
+void note_launch(int count = 1);
+// Bracket a fused-fit launch with the next traced event pair (if armed).
+int trace_begin(int kernel_id, cudaStream_t st);
+void trace_end(int slot, cudaStream_t st);
+
+// Run the fused fit over the slot-order state already in the workspace:
+// mixed kernel + FP64 queue, or the FP64 kernel alone.
+cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMode mode,
+                    const int32_t* perm_out, double* dudt, double* grad, double* hess,
+                    int32_t* fit_status, int32_t* status_word, cudaStream_t st);
+
+}  // namespace phb

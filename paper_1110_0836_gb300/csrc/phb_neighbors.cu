@@ -1,0 +1,329 @@
+// Cell binning (counting sort, stable by caller index) and the fixed-radius
+// neighbour search of Paper II Sec. 2 / Sec. 2.1: strict, not mutual, radius
+// of the gathering particle, no iteration.
+//
+// The search screens candidates in FP32 and decides the band of ambiguous
+// candidates with the exact FP64 test, so every set equals the definition
+// ((dx*dx + dy*dy) + dz*dz) < r*r evaluated in FP64 without contraction.
+#include "phb_internal.cuh"
+
+namespace phb {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t n, int t = kThreads) { return static_cast<unsigned>((n + t - 1) / t); }
+
+__global__ void k_keys(Grid g, const double* __restrict__ pos, const double* __restrict__ lam,
+                       int32_t* __restrict__ keys, int32_t* __restrict__ counts,
+                       int32_t* status_word) {
+  const int n = g.n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c[3];
+  bool finite = true;
+  for (int a = 0; a < 3; ++a) {
+    double x = pos[a * n + i];
+    finite &= isfinite(x);
+    c[a] = isfinite(x) ? cell_coord(g, a, x) : 0;
+  }
+  const double l = lam[i];
+  if (!finite || !isfinite(l)) raise_flag(status_word, PHB_FLAG_NONFINITE);
+  if (!(l >= g.lambda_min && l <= g.lambda_max)) raise_flag(status_word, PHB_FLAG_LAMBDA_RANGE);
+  const int32_t k = cell_key(g, c[0], c[1], c[2]);
+  keys[i] = k;
+  atomicAdd(&counts[k], 1);
+}
+
+__global__ void k_scatter(int n, const int32_t* __restrict__ keys, const int32_t* __restrict__ cell_start,
+                          int32_t* __restrict__ cursor, int32_t* __restrict__ perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t k = keys[i];
+  perm[cell_start[k] + atomicAdd(&cursor[k], 1)] = i;
+}
+
+// Make the order inside each cell deterministic: ascending caller index.
+// Insertion sort for the usual handful of particles, Shell sort otherwise.
+__global__ void k_sort_cells(int64_t nkeys, const int32_t* __restrict__ cell_start,
+                             int32_t* __restrict__ perm) {
+  const int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= nkeys) return;
+  const int a = cell_start[c], b = cell_start[c + 1];
+  const int m = b - a;
+  if (m < 2) return;
+  int32_t* v = perm + a;
+  if (m <= 48) {
+    for (int i = 1; i < m; ++i) {
+      int32_t x = v[i];
+      int j = i - 1;
+      while (j >= 0 && v[j] > x) { v[j + 1] = v[j]; --j; }
+      v[j + 1] = x;
+    }
+    return;
+  }
+  int h = 1;
+  while (3 * h + 1 < m) h = 3 * h + 1;  // Knuth gaps 1, 4, 13, 40, ...
+  for (; h >= 1; h /= 3) {
+    for (int i = h; i < m; ++i) {
+      int32_t x = v[i];
+      int j = i;
+      while (j >= h && v[j - h] > x) { v[j] = v[j - h]; j -= h; }
+      v[j] = x;
+    }
+  }
+}
+
+// Slot-order copies of positions and lambda, the inverse permutation and the
+// wrapped FP32 screen positions.
+__global__ void k_gather_pos(Grid g, const int32_t* __restrict__ perm, const double* __restrict__ pos,
+                             const double* __restrict__ lam, int32_t* __restrict__ inv,
+                             double* __restrict__ spos, double* __restrict__ slam,
+                             float4* __restrict__ scr) {
+  const int n = g.n;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int i = perm[s];
+  inv[i] = s;
+  float w[3];
+  for (int a = 0; a < 3; ++a) {
+    double x = pos[a * n + i];
+    spos[a * n + s] = x;
+    double xw = g.periodic[a] ? x - g.len[a] * floor((x - g.lo[a]) / g.len[a]) : x;
+    w[a] = static_cast<float>(xw);
+  }
+  slam[s] = lam[i];
+  scr[s] = make_float4(w[0], w[1], w[2], 0.f);
+}
+
+struct Reach {
+  int start, count;
+  bool wrap, open;
+};
+
+__device__ __forceinline__ Reach axis_reach(const Grid& g, int a, int c, double r) {
+  int R = static_cast<int>(ceil(r * g.inv_cell[a] * (1.0 + 1e-6)));
+  Reach q;
+  q.open = !g.periodic[a];
+  if (g.periodic[a] && 2 * R + 1 >= g.ncell[a]) {
+    q.start = 0;
+    q.count = g.ncell[a];
+    q.wrap = false;
+  } else {
+    q.start = c - R;
+    q.count = 2 * R + 1;
+    q.wrap = g.periodic[a] != 0;
+  }
+  return q;
+}
+
+__device__ __forceinline__ int axis_cell(const Grid& g, int a, const Reach& q, int k, bool& ok) {
+  int c = q.start + k;
+  ok = true;
+  if (q.wrap) {
+    int nc = g.ncell[a];
+    c = c < 0 ? c + nc : (c >= nc ? c - nc : c);
+  } else if (q.open && (c < 0 || c >= g.ncell[a])) {
+    ok = false;
+  }
+  return c;
+}
+
+template <bool kFill>
+__global__ void __launch_bounds__(kThreads) k_neighbors(Grid g, const int32_t* __restrict__ cell_start,
+                                                        const float4* __restrict__ scr,
+                                                        const double* __restrict__ spos,
+                                                        const double* __restrict__ slam,
+                                                        int32_t* __restrict__ ncnt,
+                                                        const int64_t* __restrict__ off,
+                                                        int32_t* __restrict__ idx,
+                                                        int32_t* status_word) {
+  const int n = g.n;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double xs = spos[s], ys = spos[n + s], zs = spos[2 * n + s];
+  const double r = list_radius(g, slam[s]);
+  const double r2 = __dmul_rn(r, r);
+  const double m = static_cast<double>(g.screen_margin) + 4e-7 * r;
+  const float in2 = static_cast<float>(r > m ? (r - m) * (r - m) : 0.0);
+  const float out2 = static_cast<float>((r + m) * (r + m));
+  const float4 me = scr[s];
+  float lenf[3], invlf[3];
+  for (int a = 0; a < 3; ++a) {
+    lenf[a] = static_cast<float>(g.len[a]);
+    invlf[a] = g.periodic[a] ? static_cast<float>(1.0 / g.len[a]) : 0.f;
+  }
+  const Reach qx = axis_reach(g, 0, cell_coord(g, 0, xs), r);
+  const Reach qy = axis_reach(g, 1, cell_coord(g, 1, ys), r);
+  const Reach qz = axis_reach(g, 2, cell_coord(g, 2, zs), r);
+  int64_t base = 0, end = 0;
+  if (kFill) {
+    base = off[s];
+    end = off[s + 1];
+    if (end > g.capacity) raise_flag(status_word, PHB_FLAG_CAPACITY);
+  }
+  int count = 0;
+  for (int kx = 0; kx < qx.count; ++kx) {
+    bool okx;
+    const int cx = axis_cell(g, 0, qx, kx, okx);
+    if (!okx) continue;
+    for (int ky = 0; ky < qy.count; ++ky) {
+      bool oky;
+      const int cy = axis_cell(g, 1, qy, ky, oky);
+      if (!oky) continue;
+      for (int kz = 0; kz < qz.count; ++kz) {
+        bool okz;
+        const int cz = axis_cell(g, 2, qz, kz, okz);
+        if (!okz) continue;
+        const int32_t key = cell_key(g, cx, cy, cz);
+        const int t0 = cell_start[key], t1 = cell_start[key + 1];
+        for (int t = t0; t < t1; ++t) {
+          if (t == s) continue;
+          const float4 o = scr[t];
+          float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
+          dx = fmaf(-lenf[0], rintf(dx * invlf[0]), dx);
+          dy = fmaf(-lenf[1], rintf(dy * invlf[1]), dy);
+          dz = fmaf(-lenf[2], rintf(dz * invlf[2]), dz);
+          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          bool in;
+          if (d2 < in2) in = true;
+          else if (d2 > out2) in = false;
+          else in = dist2_exact(g, spos, n, s, t) < r2;
+          if (in) {
+            if (kFill) {
+              const int64_t e = base + count;
+              if (e < g.capacity && e < end) idx[e] = t;
+            }
+            ++count;
+          }
+        }
+      }
+    }
+  }
+  if (!kFill) ncnt[s] = count;
+}
+
+// -------- export in caller numbering
+__global__ void k_user_counts(int n, const int32_t* __restrict__ inv, const int64_t* __restrict__ off,
+                              int32_t* __restrict__ ucnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  if (i == n) { ucnt[n] = 0; return; }
+  const int s = inv[i];
+  ucnt[i] = static_cast<int32_t>(off[s + 1] - off[s]);
+}
+
+__global__ void k_user_fill(int n, int64_t cap, const int32_t* __restrict__ inv,
+                            const int32_t* __restrict__ perm, const int64_t* __restrict__ off,
+                            const int32_t* __restrict__ idx, const int64_t* __restrict__ uoff,
+                            int32_t* __restrict__ uidx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = inv[i];
+  const int64_t a = off[s], b = off[s + 1] < cap ? off[s + 1] : cap;
+  int32_t* v = uidx + uoff[i];
+  const int m = static_cast<int>(b > a ? b - a : 0);
+  for (int k = 0; k < m; ++k) v[k] = perm[idx[a + k]];
+  for (int k = 1; k < m; ++k) {  // ascending caller index
+    int32_t x = v[k];
+    int j = k - 1;
+    while (j >= 0 && v[j] > x) { v[j + 1] = v[j]; --j; }
+    v[j + 1] = x;
+  }
+}
+
+}  // namespace
+
+cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const double* lam, void* ws,
+                                 int32_t* status_word, cudaStream_t st) {
+  const Grid g = make_grid(p);
+  const int n = g.n;
+  int32_t* keys = region<int32_t>(p, ws, R_KEYS);
+  int32_t* perm = region<int32_t>(p, ws, R_PERM);
+  int32_t* inv = region<int32_t>(p, ws, R_INV);
+  int32_t* cell = region<int32_t>(p, ws, R_CELL);
+  int32_t* cursor = region<int32_t>(p, ws, R_CURSOR);
+  int64_t* bsum = region<int64_t>(p, ws, R_SCAN);
+  double* spos = region<double>(p, ws, R_SPOS);
+  double* slam = region<double>(p, ws, R_SLAM);
+  float4* scr = region<float4>(p, ws, R_SCREEN);
+  int32_t* ncnt = region<int32_t>(p, ws, R_NCNT);
+  int64_t* off = region<int64_t>(p, ws, R_OFF);
+  int32_t* idx = region<int32_t>(p, ws, R_IDX);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(cell, 0, (p->nkeys + 1) * sizeof(int32_t), st))) return e;
+  if ((e = cudaMemsetAsync(cursor, 0, p->nkeys * sizeof(int32_t), st))) return e;
+  k_keys<<<blocks_for(n), kThreads, 0, st>>>(g, pos, lam, keys, cell, status_word);
+  note_launch();
+  if ((e = scan_exclusive_i32(cell, p->nkeys + 1, bsum, st))) return e;
+  k_scatter<<<blocks_for(n), kThreads, 0, st>>>(n, keys, cell, cursor, perm);
+  note_launch();
+  k_sort_cells<<<blocks_for(p->nkeys), kThreads, 0, st>>>(p->nkeys, cell, perm);
+  note_launch();
+  k_gather_pos<<<blocks_for(n), kThreads, 0, st>>>(g, perm, pos, lam, inv, spos, slam, scr);
+  note_launch();
+  k_neighbors<false><<<blocks_for(n), kThreads, 0, st>>>(g, cell, scr, spos, slam, ncnt, nullptr,
+                                                          nullptr, status_word);
+  note_launch();
+  if ((e = cudaMemsetAsync(ncnt + n, 0, sizeof(int32_t), st))) return e;
+  if ((e = scan_exclusive_i32_to_i64(ncnt, off, n + 1, bsum, st))) return e;
+  k_neighbors<true><<<blocks_for(n), kThreads, 0, st>>>(g, cell, scr, spos, slam, ncnt, off, idx,
+                                                         status_word);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t export_neighbors_impl(const phb_plan* p, const void* ws_c, int64_t* uoff, int32_t* uidx,
+                                  cudaStream_t st) {
+  void* ws = const_cast<void*>(ws_c);
+  const int n = static_cast<int>(p->n);
+  const int32_t* perm = region<int32_t>(p, ws, R_PERM);
+  const int32_t* inv = region<int32_t>(p, ws, R_INV);
+  const int64_t* off = region<int64_t>(p, ws, R_OFF);
+  const int32_t* idx = region<int32_t>(p, ws, R_IDX);
+  int32_t* ucnt = region<int32_t>(p, ws, R_QUEUE);  // scratch: n+1 fits before R_PC (>= n+64 ints)
+  int64_t* bsum = region<int64_t>(p, ws, R_SCAN);
+  cudaError_t e;
+  k_user_counts<<<blocks_for(n + 1), kThreads, 0, st>>>(n, inv, off, ucnt);
+  note_launch();
+  if ((e = scan_exclusive_i32_to_i64(ucnt, uoff, n + 1, bsum, st))) return e;
+  k_user_fill<<<blocks_for(n), kThreads, 0, st>>>(n, p->nbr_capacity, inv, perm, off, idx, uoff, uidx);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace phb
+
+using namespace phb;
+
+extern "C" phb_status phb_build_neighbors(const phb_plan* plan, const double* pos,
+                                          const double* lambda, void* ws, size_t ws_bytes,
+                                          int32_t* status_word, phb_stream_t stream) {
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_END_COMMON] : 0);
+  if (s != PHB_OK) return s;
+  if (!pos || !lambda) return PHB_ERR_INVALID_ARG;
+  return launch_status(build_neighbors_impl(plan, pos, lambda, ws, status_word,
+                                            reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" int64_t phb_neighbor_total(const phb_plan* plan, const void* ws, phb_stream_t stream) {
+  if (!plan || !ws || plan->ws_bytes == 0) return -1;
+  int64_t total = -1;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t* off = region<int64_t>(plan, ws, R_OFF);
+  if (cudaMemcpyAsync(&total, off + plan->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) !=
+      cudaSuccess)
+    return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  return total;
+}
+
+extern "C" phb_status phb_export_neighbors(const phb_plan* plan, const void* ws, int64_t* off,
+                                           int32_t* idx, int64_t idx_capacity, phb_stream_t stream) {
+  if (!plan || !ws || !off || !idx || plan->ws_bytes == 0) return PHB_ERR_INVALID_ARG;
+  // the export writes its counts into the route-queue region (n int32 + pad)
+  int64_t total = phb_neighbor_total(plan, ws, stream);
+  if (total < 0) return PHB_ERR_CUDA;
+  if (total > idx_capacity || total > plan->nbr_capacity) return PHB_ERR_CAPACITY;
+  return launch_status(export_neighbors_impl(plan, ws, off, idx, reinterpret_cast<cudaStream_t>(stream)));
+}

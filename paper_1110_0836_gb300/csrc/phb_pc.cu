@@ -1,0 +1,100 @@
+// Second-order predictor-corrector step (Paper II Sec. 2; Sec. 4.2 "explicit
+// Hermitian time integration"), read as Heun's method on Y = (x, U):
+//   Y^p = Y^n + dt F(Y^n),   Y^{n+1} = Y^n + dt/2 (F(Y^n) + F(Y^p)),
+// with dx/dt = V and lambda unchanged.  One neighbour build per step at x^n
+// with radius r_f + skin; both right-hand-side evaluations filter the lists
+// at r_f with their own positions.  The whole step is a fixed sequence of
+// launches on one stream (no host synchronisation), so it can be captured
+// in a CUDA graph.
+#include <cmath>
+
+#include "phb_internal.cuh"
+
+namespace phb {
+namespace {
+
+constexpr int kThreads = 256;
+
+// Y^p = Y^n + dt F(Y^n) in slot order; refresh the FP32 records; flag a
+// displacement above half the skin (the lists would then miss pairs).
+__global__ void k_predict(Grid g, double dt, const double* __restrict__ y0,
+                          const double* __restrict__ f0, double* __restrict__ spos,
+                          double* __restrict__ sU, float* __restrict__ rec, int32_t* status_word) {
+  const int n = g.n;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int64_t N = n;
+  double x[3], u[8];
+  double disp2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double d = dt * y0[(3 + 1 + a) * N + s];  // dt * V^n
+    x[a] = y0[a * N + s] + d;
+    spos[a * N + s] = x[a];
+    disp2 += d * d;
+  }
+  for (int f = 0; f < 8; ++f) {
+    u[f] = y0[(3 + f) * N + s] + dt * f0[f * N + s];
+    sU[f * N + s] = u[f];
+  }
+  if (4.0 * disp2 > g.skin * g.skin) raise_flag(status_word, PHB_FLAG_SKIN);
+  write_record(rec, s, x, u);
+}
+
+// Y^{n+1} = Y^n + dt/2 (F(Y^n) + F(Y^p)), written to the caller's arrays.
+__global__ void k_correct(int n, double dt, const int32_t* __restrict__ perm,
+                          const double* __restrict__ y0, const double* __restrict__ sU_p,
+                          const double* __restrict__ f0, const double* __restrict__ f1,
+                          double* __restrict__ pos, double* __restrict__ U) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int64_t N = n;
+  const int i = perm[s];
+  const double h = 0.5 * dt;
+  for (int a = 0; a < 3; ++a)
+    pos[a * N + i] = y0[a * N + s] + h * (y0[(3 + 1 + a) * N + s] + sU_p[(1 + a) * N + s]);
+  for (int f = 0; f < 8; ++f) U[f * N + i] = y0[(3 + f) * N + s] + h * (f0[f * N + s] + f1[f * N + s]);
+}
+
+}  // namespace
+}  // namespace phb
+
+using namespace phb;
+
+extern "C" phb_status phb_pc_step(const phb_plan* plan, const phb_params* prm, double* pos,
+                                  const double* lambda, double* U, double dt, void* ws,
+                                  size_t ws_bytes, int32_t* status_word, phb_stream_t stream) {
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_PC_Y0] + 11 * 8 * plan->n : 0);
+  if (s != PHB_OK) return s;
+  if (!prm || !pos || !lambda || !U || !std::isfinite(dt)) return PHB_ERR_INVALID_ARG;
+  if (prm->precision != PHB_FP64 && prm->precision != PHB_FP32_MIXED) return PHB_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Grid g = make_grid(plan);
+  const int n = g.n;
+  const int64_t N = n;
+  double* y0 = region<double>(plan, ws, R_PC_Y0);
+  double* f0 = region<double>(plan, ws, R_PC_F0);
+  double* f1 = region<double>(plan, ws, R_PC_F1);
+  double* spos = region<double>(plan, ws, R_SPOS);
+  double* sU = region<double>(plan, ws, R_SU);
+  const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
+  cudaError_t e;
+  if ((e = build_neighbors_impl(plan, pos, lambda, ws, status_word, st))) return launch_status(e);
+  if ((e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st))) return launch_status(e);
+  if ((e = cudaMemcpyAsync(y0, spos, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st)))
+    return launch_status(e);
+  if ((e = cudaMemcpyAsync(y0 + 3 * N, sU, 8 * N * sizeof(double), cudaMemcpyDeviceToDevice, st)))
+    return launch_status(e);
+  if ((e = run_fit(plan, prm, ws, FitMode::kRHS, nullptr, f0, nullptr, nullptr, nullptr,
+                   status_word, st)))
+    return launch_status(e);
+  k_predict<<<blocks, kThreads, 0, st>>>(g, dt, y0, f0, spos, sU, region<float>(plan, ws, R_REC),
+                                         status_word);
+  note_launch();
+  if ((e = run_fit(plan, prm, ws, FitMode::kRHS, nullptr, f1, nullptr, nullptr, nullptr,
+                   status_word, st)))
+    return launch_status(e);
+  k_correct<<<blocks, kThreads, 0, st>>>(n, dt, region<int32_t>(plan, ws, R_PERM), y0, sU, f0, f1,
+                                         pos, U);
+  note_launch();
+  return launch_status(cudaSuccess);
+}

@@ -1,0 +1,127 @@
+// Entry points phb_mls_derivs and phb_mhd_rhs: gather the caller's arrays
+// into cell (slot) order, run the fused fit, scatter results back.
+#include "phb_internal.cuh"
+
+namespace phb {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void k_gather_all(Grid g, const int32_t* __restrict__ perm, const double* __restrict__ pos,
+                             const double* __restrict__ lam, const double* __restrict__ U,
+                             double* __restrict__ spos, double* __restrict__ slam,
+                             double* __restrict__ sU, float* __restrict__ rec,
+                             int32_t* status_word) {
+  const int n = g.n;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int i = perm[s];
+  double x[3], u[8];
+  bool finite = true;
+  for (int a = 0; a < 3; ++a) {
+    x[a] = pos[a * static_cast<int64_t>(n) + i];
+    spos[a * static_cast<int64_t>(n) + s] = x[a];
+    finite &= isfinite(x[a]);
+  }
+  const double l = lam[i];
+  slam[s] = l;
+  if (!(l >= g.lambda_min && l <= g.lambda_max)) raise_flag(status_word, PHB_FLAG_LAMBDA_RANGE);
+  for (int f = 0; f < 8; ++f) {
+    u[f] = U ? U[f * static_cast<int64_t>(n) + i] : 0.0;
+    sU[f * static_cast<int64_t>(n) + s] = u[f];
+    finite &= isfinite(u[f]);
+  }
+  if (!finite) raise_flag(status_word, PHB_FLAG_NONFINITE);
+  write_record(rec, s, x, u);
+}
+
+}  // namespace
+
+cudaError_t gather_sorted(const phb_plan* p, const Grid& g, const double* pos, const double* lam,
+                          const double* U, void* ws, int32_t* status_word, cudaStream_t st) {
+  k_gather_all<<<static_cast<unsigned>((g.n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+      g, region<int32_t>(p, ws, R_PERM), pos, lam, U, region<double>(p, ws, R_SPOS),
+      region<double>(p, ws, R_SLAM), region<double>(p, ws, R_SU), region<float>(p, ws, R_REC),
+      status_word);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMode mode,
+                    const int32_t* perm_out, double* dudt, double* grad, double* hess,
+                    int32_t* fit_status, int32_t* status_word, cudaStream_t st) {
+  FitArgs a;
+  a.g = make_grid(plan);
+  a.n = static_cast<int32_t>(plan->n);
+  a.perm_in = region<int32_t>(plan, ws, R_PERM);
+  a.perm_out = perm_out;
+  a.spos = region<double>(plan, ws, R_SPOS);
+  a.slam = region<double>(plan, ws, R_SLAM);
+  a.sU = region<double>(plan, ws, R_SU);
+  a.rec = region<float>(plan, ws, R_REC);
+  a.off = region<int64_t>(plan, ws, R_OFF);
+  a.idx = region<int32_t>(plan, ws, R_IDX);
+  a.gamma = prm->gamma;
+  a.weight_kind = prm->weight_kind;
+  a.cond_threshold = static_cast<float>(prm->cond_threshold > 0 ? prm->cond_threshold : 300.0);
+  a.zeta = prm->zeta;
+  a.eta = prm->eta;
+  a.dudt = dudt;
+  a.grad = grad;
+  a.hess = hess;
+  a.fit_status = fit_status;
+  a.queue = region<int32_t>(plan, ws, R_QUEUE);
+  a.queue_len = region<int32_t>(plan, ws, R_MISC);
+  a.status_word = status_word;
+  cudaError_t e;
+  if (prm->precision == PHB_FP64) return launch_fit_fp64(a, mode, nullptr, nullptr, st);
+  if ((e = cudaMemsetAsync(a.queue_len, 0, sizeof(int32_t), st))) return e;
+  if ((e = launch_fit_mixed(a, mode, st))) return e;
+  return launch_fit_fp64(a, mode, a.queue, a.queue_len, st);
+}
+
+}  // namespace phb
+
+using namespace phb;
+
+namespace {
+
+phb_status fit_entry(const phb_plan* plan, const phb_params* prm, const double* pos,
+                     const double* lambda, const double* U, void* ws, size_t ws_bytes, FitMode mode,
+                     double* dudt, double* grad, double* hess, int32_t* fit_status,
+                     int32_t* status_word, phb_stream_t stream) {
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_END_COMMON] : 0);
+  if (s != PHB_OK) return s;
+  if (!prm || !pos || !lambda || !U) return PHB_ERR_INVALID_ARG;
+  if (prm->precision != PHB_FP64 && prm->precision != PHB_FP32_MIXED) return PHB_ERR_INVALID_ARG;
+  if (prm->weight_kind != 0 && prm->weight_kind != 1) return PHB_ERR_INVALID_ARG;
+  if (!(prm->gamma > 1.0)) return PHB_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Grid g = make_grid(plan);
+  cudaError_t e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st);
+  if (e == cudaSuccess)
+    e = run_fit(plan, prm, ws, mode, region<int32_t>(plan, ws, R_PERM), dudt, grad, hess,
+                fit_status, status_word, st);
+  return launch_status(e);
+}
+
+}  // namespace
+
+extern "C" phb_status phb_mls_derivs(const phb_plan* plan, const phb_params* params,
+                                     const double* pos, const double* lambda, const double* U,
+                                     void* ws, size_t ws_bytes, double* grad, double* hess,
+                                     int32_t* fit_status, int32_t* status_word,
+                                     phb_stream_t stream) {
+  if (!grad) return PHB_ERR_INVALID_ARG;
+  return fit_entry(plan, params, pos, lambda, U, ws, ws_bytes, FitMode::kDerivs, nullptr, grad,
+                   hess, fit_status, status_word, stream);
+}
+
+extern "C" phb_status phb_mhd_rhs(const phb_plan* plan, const phb_params* params, const double* pos,
+                                  const double* lambda, const double* U, void* ws, size_t ws_bytes,
+                                  double* dudt, int32_t* fit_status, int32_t* status_word,
+                                  phb_stream_t stream) {
+  if (!dudt) return PHB_ERR_INVALID_ARG;
+  return fit_entry(plan, params, pos, lambda, U, ws, ws_bytes, FitMode::kRHS, dudt, nullptr,
+                   nullptr, fit_status, status_word, stream);
+}
