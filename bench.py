@@ -44,12 +44,17 @@ FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle leg")
-    ap.add_argument("--sample", type=int, default=2048, help="oracle sample size")
+    ap.add_argument("--sample", type=int, default=8192, help="oracle sample size")
+    ap.add_argument("--profile", choices=["none", "fit", "step"], default="none",
+                    help="minimal run for an ncu capture: 'fit' = two RHS evaluations with "
+                         "prebuilt lists, 'step' = two predictor-corrector steps")
+    ap.add_argument("--precision", choices=["fp32_mixed", "fp64"], default="fp32_mixed",
+                    help="precision of the --profile run")
     return ap.parse_args()
 
 
@@ -76,7 +81,7 @@ def barrier(world: int):
 
 
 class Clocks:
-    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -92,7 +97,7 @@ class Clocks:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -157,7 +162,7 @@ def oracle_leg(w, sample: int, seed: int = 0):
         out, st = oracle.mhd_rhs(box, w.pos, w.lam, w.U, nb, q, gamma=w.gamma)
         reps += 1
         el = time.perf_counter() - t0
-        if el > 10.0 or reps >= 50:
+        if el > 12.0 or reps >= 20000:
             break
     rate = reps * len(q) / el
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -198,6 +203,35 @@ def run_reference(args):
                                        "neighbour lists precomputed"},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def run_profile(args):
+    """Few launches on the benchmark workload, for ncu (no timing, no oracle)."""
+    import torch
+    import workloads
+    import paper_1110_0836_gb300 as phb
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    phb.build()
+    w = workloads.config(args.workload)
+    dt = cfl_dt(w)
+    vmax = float(np.sqrt((w.U[1:4] ** 2).sum(0)).max())
+    skin = max(4.0 * dt * vmax, 0.02 * 2.3 * float(w.lam.min()))
+    pos, lam, U = phb.tensors_of(w, dev)
+    prm = phb.Params(gamma=w.gamma, precision=args.precision)
+    if args.profile == "fit":
+        plan = phb.Plan.for_workload(w, device=dev)
+        phb.build_neighbors(plan, pos, lam)
+        out = torch.empty((8, w.n), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            phb.mhd_rhs(plan, prm, pos, lam, U, out=out)
+    else:
+        plan = phb.Plan.for_workload(w, skin=skin, device=dev)
+        phb.build_neighbors(plan, pos, lam)
+        for _ in range(2):
+            phb.pc_step(plan, prm, pos, lam, U, dt)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "status": plan.read_status(), "n": w.n}))
 
 
 def run_ours(args):
@@ -325,6 +359,22 @@ def run_ours(args):
     e1.synchronize()
     build_ms = e0.elapsed_time(e1)
 
+    # ---------------- adjoint (FP64 reverse mode, factorisations recomputed)
+    gb = torch.as_tensor(workloads.loss_weights(n), device=dev)
+    Ub = torch.empty((8, n), dtype=torch.float64, device=dev)
+    xb = torch.empty((3, n), dtype=torch.float64, device=dev)
+    phb.rhs_adjoint(plan, fp64, pos0, lam, U0, gb, Ub, xb)
+    ta = []
+    for _ in range(2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        phb.rhs_adjoint(plan, fp64, pos0, lam, U0, gb, Ub, xb)
+        e1.record()
+        e1.synchronize()
+        ta.append(e0.elapsed_time(e1))
+    adj_ms = float(np.mean(ta))
+
     # ---------------- end to end through the API with host buffers
     hpos = pos0.cpu().pin_memory()
     hlam = lam.cpu().pin_memory()
@@ -361,8 +411,10 @@ def run_ours(args):
                "metric": "max over fields of max_i|a-o| / max_i|o| on the oracle sample"}
 
     fst = torch.empty(n, dtype=torch.int32, device=dev)
+    phb.build_neighbors(plan, pos0, lam)
     phb.mhd_rhs(plan, mixed, pos0, lam, U0, fit_status=fst)
     routed = float((fst == 2).float().mean().item())
+    tile_stats = plan.stats()
 
     if rank != 0:
         return
@@ -389,8 +441,11 @@ def run_ours(args):
         "rhs_only": {"fp32_mixed_ms": rhs32_ms, "fp64_ms": rhs64_ms,
                      "fp32_mixed_value": n / (rhs32_ms * 1e-3), "fp64_value": n / (rhs64_ms * 1e-3),
                      "neighbour_build_ms": build_ms},
+        "adjoint": {"ms": adj_ms, "value": n / (adj_ms * 1e-3), "unit": "particle-gradients/s",
+                    "precision": "fp64", "factorisations": "recomputed"},
         "err_vs_oracle": err,
         "routed_to_fp64": routed,
+        "tiles": tile_stats,
     }
     print(json.dumps(line))
     if world > 1:
@@ -402,6 +457,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile != "none":
+        run_profile(args)
     else:
         run_ours(args)
 

@@ -101,10 +101,14 @@ typedef struct {
   double lambda_max;
   int64_t nbr_capacity;  /* entries reserved for neighbour lists (sum of |N(i)|) */
   double cell_frac;      /* cell edge / (rf_factor*lambda_min + skin); 0 = default 0.5 */
+  int32_t tile;          /* particles per fused-fit tile (64 or 128; 0 = default 128) */
+  int32_t stage_cap;     /* neighbourhood records staged per tile (0 = default) */
   /* filled by phb_plan_init */
   double cell[3];        /* cell edge per axis */
-  int32_t ncell[3];      /* cells per axis */
+  int32_t ncell[3];      /* cells per axis (at most 1023) */
   int32_t nbrick[3];     /* 4x4x4-cell bricks per axis */
+  int32_t hilbert_bits;  /* bricks are ordered along a 3-D Hilbert curve of this order */
+  int32_t ntiles;        /* ceil(n / tile) */
   int64_t nkeys;         /* cell-key space: bricks * 64 */
   double screen_margin;  /* absolute distance margin of the FP32 neighbour screen */
   size_t ws_bytes;       /* workspace bytes needed for every operation */

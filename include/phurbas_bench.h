@@ -37,6 +37,15 @@ int64_t phb_launch_count(void);
  * the routed queue), destroys the events and returns the number of launches
  * recorded (or -1 on a CUDA error).  Not thread-safe; one trace at a time. */
 int phb_trace_start(int32_t capacity);
+
+/* Copy diagnostic counters of the last operations on a workspace to the host
+ * (synchronising on `stream`): out[0] = fits routed to FP64 by the last fused
+ * fit, out[1] = tiles of the last neighbour build that read neighbours from
+ * global memory (neighbourhood larger than the staging capacity), out[2] =
+ * such tiles in the last fused fit, out[3] = number of tiles.  count <= 4.
+ * Returns 0, 1 for invalid arguments, 3 on a CUDA error. */
+int phb_workspace_stats(const phb_plan* plan, const void* ws, int32_t* out, int32_t count,
+                        phb_stream_t stream);
 int phb_trace_stop(float* ms, int32_t* kernel_ids, int32_t capacity);
 
 #ifdef __cplusplus

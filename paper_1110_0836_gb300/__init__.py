@@ -8,6 +8,7 @@ FP64), the Heun predictor-corrector step, and the hand-written adjoint.
 from ._lib import PhbError  # noqa: F401
 from .api import (FIELDS, Params, Plan, build_neighbors, export_neighbors, mhd_rhs,  # noqa: F401
                   mls_derivs, pc_step, rhs, rhs_adjoint, tensors_of)
+from .autograd import PhbRHS, rhs_autograd  # noqa: F401
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -20,7 +20,7 @@ PHB_FP64, PHB_FP32_MIXED = 0, 1
 EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_check",
            "phb_build_neighbors", "phb_export_neighbors", "phb_neighbor_total", "phb_mls_derivs",
            "phb_mhd_rhs", "phb_pc_step", "phb_rhs_adjoint", "phb_fma_peak", "phb_launch_count",
-           "phb_trace_start", "phb_trace_stop"]
+           "phb_trace_start", "phb_trace_stop", "phb_workspace_stats"]
 
 
 class Box(C.Structure):
@@ -36,8 +36,10 @@ class Params(C.Structure):
 class Plan(C.Structure):
     _fields_ = [("box", Box), ("n", C.c_int64), ("rf_factor", C.c_double), ("skin", C.c_double),
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double),
-                ("nbr_capacity", C.c_int64), ("cell_frac", C.c_double),
+                ("nbr_capacity", C.c_int64), ("cell_frac", C.c_double), ("tile", C.c_int32),
+                ("stage_cap", C.c_int32),
                 ("cell", C.c_double * 3), ("ncell", C.c_int32 * 3), ("nbrick", C.c_int32 * 3),
+                ("hilbert_bits", C.c_int32), ("ntiles", C.c_int32),
                 ("nkeys", C.c_int64), ("screen_margin", C.c_double), ("ws_bytes", C.c_size_t),
                 ("ws_off", C.c_size_t * 32)]
 
@@ -88,6 +90,8 @@ def lib(path: str | None = None) -> C.CDLL:
     L.phb_trace_start.restype = C.c_int
     L.phb_trace_stop.argtypes = [_vp, _vp, C.c_int32]
     L.phb_trace_stop.restype = C.c_int
+    L.phb_workspace_stats.argtypes = [P(Plan), _vp, _vp, C.c_int32, _vp]
+    L.phb_workspace_stats.restype = C.c_int
     for f in ("phb_plan_init", "phb_check", "phb_build_neighbors", "phb_export_neighbors",
               "phb_mls_derivs", "phb_mhd_rhs", "phb_pc_step", "phb_rhs_adjoint"):
         getattr(L, f).restype = C.c_int

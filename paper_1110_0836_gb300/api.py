@@ -63,12 +63,13 @@ class Plan:
 
     def __init__(self, box_lo, box_len, periodic, n: int, lambda_min: float, lambda_max: float,
                  rf_factor: float = 2.3, skin: float = 0.0, nbr_capacity: int | None = None,
-                 cell_frac: float = 0.0, device="cuda"):
+                 cell_frac: float = 0.0, tile: int = 0, stage_cap: int = 0, device="cuda"):
         self.device = torch.device(device)
         self.args = dict(box_lo=tuple(map(float, box_lo)), box_len=tuple(map(float, box_len)),
                          periodic=tuple(int(bool(p)) for p in periodic), n=int(n),
                          lambda_min=float(lambda_min), lambda_max=float(lambda_max),
-                         rf_factor=float(rf_factor), skin=float(skin), cell_frac=float(cell_frac))
+                         rf_factor=float(rf_factor), skin=float(skin), cell_frac=float(cell_frac),
+                         tile=int(tile), stage_cap=int(stage_cap))
         if nbr_capacity is None:
             # ~51 neighbours at r_f = 2.3 lambda and uniform density; margin for
             # density contrast and the skin shell
@@ -91,6 +92,8 @@ class Plan:
         p.lambda_max = a["lambda_max"]
         p.nbr_capacity = capacity
         p.cell_frac = a["cell_frac"]
+        p.tile = a["tile"]
+        p.stage_cap = a["stage_cap"]
         check(_lib.lib().phb_plan_init(C.byref(p)), "phb_plan_init")
         self.c = p
         self.ws = torch.empty(int(p.ws_bytes), dtype=torch.uint8, device=self.device)
@@ -122,6 +125,14 @@ class Plan:
         if bad:
             raise PhbError(int(_lib.lib().phb_check(bad)), what or "device status")
         return w
+
+    def stats(self) -> dict:
+        """Diagnostic counters of the last build / fused fit (synchronises)."""
+        out = (C.c_int32 * 4)()
+        check(_lib.lib().phb_workspace_stats(C.byref(self.c), _ptr(self.ws), out, 4, _stream()),
+              "phb_workspace_stats")
+        return {"routed_to_fp64": int(out[0]), "build_fallback_tiles": int(out[1]),
+                "fit_fallback_tiles": int(out[2]), "tiles": int(out[3])}
 
     def neighbor_total(self) -> int:
         return int(_lib.lib().phb_neighbor_total(C.byref(self.c), _ptr(self.ws), _stream()))

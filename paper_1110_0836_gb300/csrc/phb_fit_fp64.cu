@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kT) k_fit_fp64(const FitArgs a, const int32_t*
     double invd[kNB];
     if (!singular) {
       mls_assemble(mom, M);
-      const double minpiv = mls_cholesky(M, invd);
+      const double minpiv = mls_cholesky<double>(M, invd);
       double rmin = 1e300, rmax = 0.0;
 #pragma unroll
       for (int k = 0; k < kNB; ++k) {

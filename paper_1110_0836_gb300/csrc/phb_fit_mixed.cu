@@ -1,27 +1,30 @@
 // FP32-mixed fused MLS fit + MHD right-hand side (Paper II Sec. 2).
 //
-// One thread per particle, in cell (slot) order.  Offsets and field
-// differences come from FP32 hi/lo splits of the FP64 values, centred on the
-// particle (q = d / lambda_i and U_j - U_i), so a 1e-6 perturbation on an O(1)
-// background keeps ~7 significant digits.  The 80 distinct moments of the
-// normal matrix and the right-hand sides of the fitted fields are accumulated
-// in FP32 registers in two passes over the neighbour list (moments + first
-// field group, then the second group), the 19x19 normal matrix is factorised
-// by an unrolled in-register Cholesky, and only the linear and quadratic
-// coefficients are back-substituted.  Fits whose Jacobi-scaled conditioning
-// estimate (max L_kk / min L_kk)^2 exceeds the threshold, or whose
-// factorisation fails, are pushed to a queue that the FP64 kernel redoes.
+// One CTA per tile of consecutive particles (cell order), one thread per
+// particle.  The tile's neighbourhood is staged in shared memory as 48-byte
+// records: position and the 8 fields relative to the tile's first particle,
+// computed from FP32 hi/lo splits of the FP64 values (offsets with minimum
+// image), so differences between neighbours keep ~7 significant digits even
+// for a 1e-6 perturbation on an O(1) background.  Each thread accumulates the
+// 80 distinct moments of the normal matrix and the right-hand sides of the
+// fitted fields in FP32 registers in two passes over its neighbour list
+// (moments + first field group, then the second group), factorises the
+// 19x19 normal matrix by an unrolled in-register Cholesky and back-substitutes
+// only the linear and quadratic coefficients.  Fits whose Jacobi-scaled
+// conditioning estimate (max L_kk / min L_kk)^2 exceeds the threshold, or
+// whose factorisation fails, are queued for the FP64 kernel.  Tiles whose
+// neighbourhood exceeds the staging capacity read neighbours from global
+// memory (FP32 hi/lo records) through the same code.
 #include "phb_internal.cuh"
 #include "mls_gen.cuh"
 #include "phb_mhd.cuh"
+#include "phb_tile.cuh"
 
 namespace phb {
 namespace {
 
-constexpr int kT = 128;
-
 struct Per32 {
-  float len_h[3], len_l[3], inv_len[3];
+  float len_h[3], len_l[3], inv_len[3], len[3];
 };
 
 __device__ __forceinline__ float hl(float ah, float al, float bh, float bl) {
@@ -42,46 +45,93 @@ struct Groups {
   }
 };
 
-template <FitMode MODE>
-__global__ void __launch_bounds__(kT, 1) k_fit_mixed(const FitArgs a, const Per32 P) {
-  using G = Groups<MODE>;
-  // park[slot][kT]: the fields' right-hand sides (G::NF x 19 slots) followed by
-  // the 80 moments; after the solve each field's first 9 slots hold its
-  // gradient and packed Hessian.
-  extern __shared__ float park[];
-  constexpr int kMom0 = G::NF * kNB;
-  const int n = a.n;
-  const int s = blockIdx.x * kT + threadIdx.x;
-  if (s >= n) return;
-  const int tid = threadIdx.x;
-  const float4* rec = reinterpret_cast<const float4*>(a.rec);
-  const float4 o0 = rec[6 * s + 0], o1 = rec[6 * s + 1];
-  const double lam = a.slam[s];
-  const double rf = a.g.rf_factor * lam;
-  const float inv_l = static_cast<float>(1.0 / lam);
-  const float inv_rf2 = static_cast<float>(1.0 / (rf * rf));
-  const int64_t beg = a.off[s];
-  const int64_t end = a.off[s + 1] < a.g.capacity ? a.off[s + 1] : a.g.capacity;
-  const bool unweighted = a.weight_kind == 1;
+// Neighbour data from the FP32 hi/lo records in global memory.
+// du (pass A) = (rho, sigma, Vx, Vy) differences; (pass B) = (Vz, Bx, By, Bz).
+struct GlobalSrc {
+  const float4* rec;
+  const int32_t* idx;
+  float4 o[6];
+  Per32 P;
+  __device__ __forceinline__ int index(int64_t e) const { return idx[e]; }
+  __device__ __forceinline__ void pass_a(int t, float& dx, float& dy, float& dz, float (&du)[4]) const {
+    const float4 p0 = rec[6 * t], p1 = rec[6 * t + 1], fh = rec[6 * t + 2], fl = rec[6 * t + 3];
+    dx = mi_diff32(p0.x, p1.x, o[0].x, o[1].x, P.len_h[0], P.len_l[0], P.inv_len[0]);
+    dy = mi_diff32(p0.y, p1.y, o[0].y, o[1].y, P.len_h[1], P.len_l[1], P.inv_len[1]);
+    dz = mi_diff32(p0.z, p1.z, o[0].z, o[1].z, P.len_h[2], P.len_l[2], P.inv_len[2]);
+    du[0] = hl(fh.x, fl.x, o[2].x, o[3].x);
+    du[1] = hl(fh.y, fl.y, o[2].y, o[3].y);
+    du[2] = hl(fh.z, fl.z, o[2].z, o[3].z);
+    du[3] = hl(fh.w, fl.w, o[2].w, o[3].w);
+  }
+  __device__ __forceinline__ void pass_b(int t, float& dx, float& dy, float& dz, float (&du)[4]) const {
+    const float4 p0 = rec[6 * t], p1 = rec[6 * t + 1], gh = rec[6 * t + 4], gl = rec[6 * t + 5];
+    dx = mi_diff32(p0.x, p1.x, o[0].x, o[1].x, P.len_h[0], P.len_l[0], P.inv_len[0]);
+    dy = mi_diff32(p0.y, p1.y, o[0].y, o[1].y, P.len_h[1], P.len_l[1], P.inv_len[1]);
+    dz = mi_diff32(p0.z, p1.z, o[0].z, o[1].z, P.len_h[2], P.len_l[2], P.inv_len[2]);
+    du[0] = hl(gh.x, gl.x, o[4].x, o[5].x);
+    du[1] = hl(gh.y, gl.y, o[4].y, o[5].y);
+    du[2] = hl(gh.z, gl.z, o[4].z, o[5].z);
+    du[3] = hl(gh.w, gl.w, o[4].w, o[5].w);
+  }
+};
 
+// Neighbour data from the staged records in shared memory:
+// r0 = (x, y, z, sigma), r1 = (Vx, Vy, Vz, rho), r2 = (Bx, By, Bz, 0).
+struct StagedSrc {
+  const float4* stage;
+  const uint16_t* lidx;
+  float4 me0, me1, me2;
+  float len[3], inv_len[3];
+  __device__ __forceinline__ void offs(float4 r0, float& dx, float& dy, float& dz) const {
+    // relative offsets are minimum images of size <= len/2; one more wrap
+    // keeps the difference a minimum image too (exact when no wrap occurs)
+    const float ax = r0.x - me0.x, ay = r0.y - me0.y, az = r0.z - me0.z;
+    dx = fmaf(-len[0], rintf(ax * inv_len[0]), ax);
+    dy = fmaf(-len[1], rintf(ay * inv_len[1]), ay);
+    dz = fmaf(-len[2], rintf(az * inv_len[2]), az);
+  }
+  __device__ __forceinline__ int index(int64_t e) const { return lidx[e]; }
+  __device__ __forceinline__ void pass_a(int l, float& dx, float& dy, float& dz, float (&du)[4]) const {
+    const float4 r0 = stage[3 * l], r1 = stage[3 * l + 1];
+    offs(r0, dx, dy, dz);
+    du[0] = r1.w - me1.w;
+    du[1] = r0.w - me0.w;
+    du[2] = r1.x - me1.x;
+    du[3] = r1.y - me1.y;
+  }
+  __device__ __forceinline__ void pass_b(int l, float& dx, float& dy, float& dz, float (&du)[4]) const {
+    const float4 r0 = stage[3 * l], r1 = stage[3 * l + 1], r2 = stage[3 * l + 2];
+    offs(r0, dx, dy, dz);
+    du[0] = r1.z - me1.z;
+    du[1] = r2.x - me2.x;
+    du[2] = r2.y - me2.y;
+    du[3] = r2.z - me2.z;
+  }
+};
+
+// Both accumulation passes of one particle.  Pass A's right-hand sides are
+// parked in shared memory column `col` ([slot][T] layout); the moments and
+// pass B's right-hand sides are returned in registers.
+template <FitMode MODE, int T, class Src>
+__device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t end, float inv_l,
+                                          float inv_rf2, bool unweighted, float* park, int col,
+                                          float (&m)[kNM], float (&bB)[4][kNB]) {
+  using G = Groups<MODE>;
   int cnt = 0;
-  {
-    const float4 o2 = rec[6 * s + 2], o3 = rec[6 * s + 3];
-    float m[kNM];
 #pragma unroll
-    for (int k = 0; k < kNM; ++k) m[k] = 0.f;
+  for (int k = 0; k < kNM; ++k) m[k] = 0.f;
+  {
     float bA[G::NA][kNB];
 #pragma unroll
     for (int f = 0; f < G::NA; ++f)
 #pragma unroll
       for (int k = 0; k < kNB; ++k) bA[f][k] = 0.f;
+    int nxt = beg < end ? src.index(beg) : 0;  // neighbour handle, loaded one ahead
     for (int64_t e = beg; e < end; ++e) {
-      const int t = a.idx[e];
-      const float4 p0 = rec[6 * t + 0], p1 = rec[6 * t + 1];
-      const float4 fh = rec[6 * t + 2], fl = rec[6 * t + 3];
-      const float dx = mi_diff32(p0.x, p1.x, o0.x, o1.x, P.len_h[0], P.len_l[0], P.inv_len[0]);
-      const float dy = mi_diff32(p0.y, p1.y, o0.y, o1.y, P.len_h[1], P.len_l[1], P.inv_len[1]);
-      const float dz = mi_diff32(p0.z, p1.z, o0.z, o1.z, P.len_h[2], P.len_l[2], P.inv_len[2]);
+      const int cur = nxt;
+      if (e + 1 < end) nxt = src.index(e + 1);
+      float dx, dy, dz, du[4];
+      src.pass_a(cur, dx, dy, dz, du);
       const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
       const bool inside = s2 < 1.f;
       const float sw = 1.f - s2;
@@ -90,59 +140,142 @@ __global__ void __launch_bounds__(kT, 1) k_fit_mixed(const FitArgs a, const Per3
       float qg[kNB], wq[kNB + 1];
       mls_monomials(dx * inv_l, dy * inv_l, dz * inv_l, wt, qg, wq);
       mls_accum_moments(qg, wq, m);
-      if (MODE == FitMode::kDerivs) mls_accum_rhs(wq, hl(fh.x, fl.x, o2.x, o3.x), bA[0]);
-      mls_accum_rhs(wq, hl(fh.y, fl.y, o2.y, o3.y), bA[G::NA - 3]);
-      mls_accum_rhs(wq, hl(fh.z, fl.z, o2.z, o3.z), bA[G::NA - 2]);
-      mls_accum_rhs(wq, hl(fh.w, fl.w, o2.w, o3.w), bA[G::NA - 1]);
+      if (MODE == FitMode::kDerivs) mls_accum_rhs(wq, du[0], bA[0]);
+      mls_accum_rhs(wq, du[1], bA[G::NA - 3]);
+      mls_accum_rhs(wq, du[2], bA[G::NA - 2]);
+      mls_accum_rhs(wq, du[3], bA[G::NA - 1]);
     }
 #pragma unroll
     for (int f = 0; f < G::NA; ++f)
 #pragma unroll
-      for (int k = 0; k < kNB; ++k) park[(f * kNB + k) * kT + tid] = bA[f][k];
-#pragma unroll
-    for (int k = 0; k < kNM; ++k) park[(kMom0 + k) * kT + tid] = m[k];
+      for (int k = 0; k < kNB; ++k) park[(f * kNB + k) * T + col] = bA[f][k];
   }
-  {
-    const float4 o4 = rec[6 * s + 4], o5 = rec[6 * s + 5];
-    float bB[4][kNB];
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
+  for (int f = 0; f < 4; ++f)
 #pragma unroll
-      for (int k = 0; k < kNB; ++k) bB[f][k] = 0.f;
-    for (int64_t e = beg; e < end; ++e) {
-      const int t = a.idx[e];
-      const float4 p0 = rec[6 * t + 0], p1 = rec[6 * t + 1];
-      const float4 gh = rec[6 * t + 4], gl = rec[6 * t + 5];
-      const float dx = mi_diff32(p0.x, p1.x, o0.x, o1.x, P.len_h[0], P.len_l[0], P.inv_len[0]);
-      const float dy = mi_diff32(p0.y, p1.y, o0.y, o1.y, P.len_h[1], P.len_l[1], P.inv_len[1]);
-      const float dz = mi_diff32(p0.z, p1.z, o0.z, o1.z, P.len_h[2], P.len_l[2], P.inv_len[2]);
-      const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
-      const float sw = 1.f - s2;
-      const float wt = s2 < 1.f ? (unweighted ? 1.f : sw * sw) : 0.f;
-      float qg[kNB], wq[kNB + 1];
-      mls_monomials(dx * inv_l, dy * inv_l, dz * inv_l, wt, qg, wq);
-      mls_accum_rhs(wq, hl(gh.x, gl.x, o4.x, o5.x), bB[0]);
-      mls_accum_rhs(wq, hl(gh.y, gl.y, o4.y, o5.y), bB[1]);
-      mls_accum_rhs(wq, hl(gh.z, gl.z, o4.z, o5.z), bB[2]);
-      mls_accum_rhs(wq, hl(gh.w, gl.w, o4.w, o5.w), bB[3]);
+    for (int k = 0; k < kNB; ++k) bB[f][k] = 0.f;
+  int nxt = beg < end ? src.index(beg) : 0;
+  for (int64_t e = beg; e < end; ++e) {
+    const int cur = nxt;
+    if (e + 1 < end) nxt = src.index(e + 1);
+    float dx, dy, dz, du[4];
+    src.pass_b(cur, dx, dy, dz, du);
+    const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
+    const float sw = 1.f - s2;
+    const float wt = s2 < 1.f ? (unweighted ? 1.f : sw * sw) : 0.f;
+    float qg[kNB], wq[kNB + 1];
+    mls_monomials(dx * inv_l, dy * inv_l, dz * inv_l, wt, qg, wq);
+    mls_accum_rhs(wq, du[0], bB[0]);
+    mls_accum_rhs(wq, du[1], bB[1]);
+    mls_accum_rhs(wq, du[2], bB[2]);
+    mls_accum_rhs(wq, du[3], bB[3]);
+  }
+  return cnt;
+}
+
+struct TileArgs {
+  const int32_t* cellc;
+  const int2* clin;
+  const uint16_t* lidx;
+  int32_t* fallback_count;
+};
+
+template <FitMode MODE, int T>
+__global__ void __launch_bounds__(T, 256 / T) k_fit_mixed(const FitArgs a, const Per32 P, const TileArgs ta) {
+  using G = Groups<MODE>;
+  // shared memory: [park A: NA*19 slots x T][staged records: stage_cap x 3 float4]
+  // after the accumulation the whole region holds the NF*19 parked slots.
+  extern __shared__ float4 smem4[];
+  float* park = reinterpret_cast<float*>(smem4);
+  float4* stage = smem4 + (G::NA * kNB * T) / 4;
+  __shared__ TileShared ts;
+  __shared__ unsigned bits[kBoxWords];
+  __shared__ int wpre[kBoxWords];
+  __shared__ int base[kMarkCap + 1];
+  __shared__ int cstart[kMarkCap];
+  __shared__ int warp_tmp[T / 32 + 1];
+  const TileArrays tarr{bits, wpre, base, cstart, warp_tmp};
+  const int n = a.n;
+  const int s0 = blockIdx.x * T;
+  const int cnt_tile = min(T, n - s0);
+  const int tid = threadIdx.x;
+  const bool active = tid < cnt_tile;
+  const int s = s0 + tid;
+  const float4* rec = reinterpret_cast<const float4*>(a.rec);
+
+  tile_plan<T>(a.g, s0, cnt_tile, ta.cellc, a.slam, ta.clin, ts, tarr);
+  const bool fb = ts.fallback != 0;
+  if (!fb) {
+    const float4 rh = rec[6 * s0], rl = rec[6 * s0 + 1];
+    const float4 fh = rec[6 * s0 + 2], fl = rec[6 * s0 + 3], gh = rec[6 * s0 + 4], gl = rec[6 * s0 + 5];
+    for (int j = tid; j < ts.ncells; j += T) {
+      const int l0 = base[j], c = base[j + 1] - l0, t0 = cstart[j];
+      for (int p = 0; p < c; ++p) {
+        const float4* r = rec + 6 * (t0 + p);
+        const float4 p0 = r[0], p1 = r[1], f0 = r[2], f1 = r[3], g0 = r[4], g1 = r[5];
+        float4* d = stage + 3 * (l0 + p);
+        d[0] = make_float4(mi_diff32(p0.x, p1.x, rh.x, rl.x, P.len_h[0], P.len_l[0], P.inv_len[0]),
+                           mi_diff32(p0.y, p1.y, rh.y, rl.y, P.len_h[1], P.len_l[1], P.inv_len[1]),
+                           mi_diff32(p0.z, p1.z, rh.z, rl.z, P.len_h[2], P.len_l[2], P.inv_len[2]),
+                           hl(f0.y, f1.y, fh.y, fl.y));
+        d[1] = make_float4(hl(f0.z, f1.z, fh.z, fl.z), hl(f0.w, f1.w, fh.w, fl.w),
+                           hl(g0.x, g1.x, gh.x, gl.x), hl(f0.x, f1.x, fh.x, fl.x));
+        d[2] = make_float4(hl(g0.y, g1.y, gh.y, gl.y), hl(g0.z, g1.z, gh.z, gl.z),
+                           hl(g0.w, g1.w, gh.w, gl.w), 0.f);
+      }
     }
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * kT + tid] = bB[f][k];
+  } else if (tid == 0) {
+    atomicAdd(ta.fallback_count, 1);
   }
+  __syncthreads();
+
+  float m[kNM], bB[4][kNB];
+  int cnt = 0;
+  float inv_l = 1.f;
+  if (active) {
+    const double lam = a.slam[s];
+    const double rf = a.g.rf_factor * lam;
+    inv_l = static_cast<float>(1.0 / lam);
+    const float inv_rf2 = static_cast<float>(1.0 / (rf * rf));
+    const int64_t beg = a.off[s];
+    const int64_t end = a.off[s + 1] < a.g.capacity ? a.off[s + 1] : a.g.capacity;
+    const bool unweighted = a.weight_kind == 1;
+    if (fb) {
+      GlobalSrc src;
+      src.rec = rec;
+      src.idx = a.idx;
+      for (int k = 0; k < 6; ++k) src.o[k] = rec[6 * s + k];
+      src.P = P;
+      cnt = accumulate<MODE, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, m, bB);
+    } else {
+      StagedSrc src;
+      src.stage = stage;
+      src.lidx = ta.lidx;
+      const int js = marked_index(tarr, box_index(a.g, ts, ta.cellc[s]));
+      const int ls = base[js] + (s - cstart[js]);
+      src.me0 = stage[3 * ls];
+      src.me1 = stage[3 * ls + 1];
+      src.me2 = stage[3 * ls + 2];
+      for (int c = 0; c < 3; ++c) {
+        src.len[c] = P.len[c];
+        src.inv_len[c] = P.inv_len[c];
+      }
+      cnt = accumulate<MODE, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, m, bB);
+    }
+  }
+  __syncthreads();  // the staged records are dead from here on
+  if (!active) return;
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = bB[f][k];
 
   const int dst = a.perm_out ? a.perm_out[s] : s;
   const bool singular = cnt < kNB;
   if (!singular) {
     float M[kNT], invd[kNB];
-    {
-      float m[kNM];
-#pragma unroll
-      for (int k = 0; k < kNM; ++k) m[k] = park[(kMom0 + k) * kT + tid];
-      mls_assemble(m, M);
-    }
-    const float minpiv = mls_cholesky(M, invd);
+    mls_assemble(m, M);
+    const float minpiv = mls_cholesky<float>(M, invd);
     // Jacobi-scaled pivots L~_kk^2 = L_kk^2 / M_kk = 1 / (invd_k^2 M_kk)
     float rmin = 3.4e38f, rmax = 0.f;
 #pragma unroll
@@ -161,24 +294,24 @@ __global__ void __launch_bounds__(kT, 1) k_fit_mixed(const FitArgs a, const Per3
     for (int k = 0; k < G::NF; ++k) {
       float b[kNB];
 #pragma unroll
-      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * kT + tid];
+      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
       mls_forward(M, invd, b);
       mls_back9(M, invd, b);
-      float* d = park + (k * kNB) * kT + tid;
-      d[0 * kT] = b[kLin0] * il;
-      d[1 * kT] = b[kLin0 + 1] * il;
-      d[2 * kT] = b[kLin0 + 2] * il;
-      d[3 * kT] = 2.f * b[kQuad0] * il2;
-      d[4 * kT] = b[kQuad0 + 1] * il2;
-      d[5 * kT] = b[kQuad0 + 2] * il2;
-      d[6 * kT] = 2.f * b[kQuad0 + 3] * il2;
-      d[7 * kT] = b[kQuad0 + 4] * il2;
-      d[8 * kT] = 2.f * b[kQuad0 + 5] * il2;
+      float* d = park + (k * kNB) * T + tid;
+      d[0 * T] = b[kLin0] * il;
+      d[1 * T] = b[kLin0 + 1] * il;
+      d[2 * T] = b[kLin0 + 2] * il;
+      d[3 * T] = 2.f * b[kQuad0] * il2;
+      d[4 * T] = b[kQuad0 + 1] * il2;
+      d[5 * T] = b[kQuad0 + 2] * il2;
+      d[6 * T] = 2.f * b[kQuad0 + 3] * il2;
+      d[7 * T] = b[kQuad0 + 4] * il2;
+      d[8 * T] = 2.f * b[kQuad0 + 5] * il2;
     }
   } else {
 #pragma unroll 1
     for (int k = 0; k < G::NF; ++k)
-      for (int j = 0; j < 9; ++j) park[(k * kNB + j) * kT + tid] = 0.f;
+      for (int j = 0; j < 9; ++j) park[(k * kNB + j) * T + tid] = 0.f;
   }
   if (a.fit_status) a.fit_status[dst] = singular ? 1 : 0;
   if (singular) raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
@@ -186,20 +319,20 @@ __global__ void __launch_bounds__(kT, 1) k_fit_mixed(const FitArgs a, const Per3
 #pragma unroll 1
     for (int k = 0; k < G::NF; ++k) {
       const int f = G::field(k);
-      const float* d = park + (k * kNB) * kT + tid;
-      for (int c = 0; c < 3; ++c) a.grad[(f * 3 + c) * static_cast<int64_t>(n) + dst] = d[c * kT];
+      const float* d = park + (k * kNB) * T + tid;
+      for (int c = 0; c < 3; ++c) a.grad[(f * 3 + c) * static_cast<int64_t>(n) + dst] = d[c * T];
       if (a.hess)
         for (int c = 0; c < 6; ++c)
-          a.hess[(f * 6 + c) * static_cast<int64_t>(n) + dst] = d[(3 + c) * kT];
+          a.hess[(f * 6 + c) * static_cast<int64_t>(n) + dst] = d[(3 + c) * T];
     }
   } else {
     MhdDerivs<float> D;
     mhd_zero(D);
 #pragma unroll
     for (int k = 0; k < G::NF; ++k) {
-      const float* d = park + (k * kNB) * kT + tid;
-      const float g[3] = {d[0], d[kT], d[2 * kT]};
-      const float h[6] = {d[3 * kT], d[4 * kT], d[5 * kT], d[6 * kT], d[7 * kT], d[8 * kT]};
+      const float* d = park + (k * kNB) * T + tid;
+      const float g[3] = {d[0], d[T], d[2 * T]};
+      const float h[6] = {d[3 * T], d[4 * T], d[5 * T], d[6 * T], d[7 * T], d[8 * T]};
       mhd_collect(D, G::field(k), g, h);
     }
     const float4 o2 = rec[6 * s + 2], o3 = rec[6 * s + 3], o4 = rec[6 * s + 4], o5 = rec[6 * s + 5];
@@ -227,33 +360,39 @@ Per32 make_per32(const Grid& g) {
     P.len_h[a] = g.periodic[a] ? h : 0.f;
     P.len_l[a] = g.periodic[a] ? static_cast<float>(g.len[a] - static_cast<double>(h)) : 0.f;
     P.inv_len[a] = g.periodic[a] ? static_cast<float>(1.0 / g.len[a]) : 0.f;
+    P.len[a] = h;
   }
   return P;
 }
 
+template <FitMode MODE, int T>
+cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, cudaStream_t st) {
+  using G = Groups<MODE>;
+  const size_t park_a = size_t(G::NA) * kNB * T * sizeof(float);
+  const size_t staged = size_t(a.g.stage_cap) * 3 * sizeof(float4);
+  const size_t park_all = size_t(G::NF) * kNB * T * sizeof(float);
+  const size_t smem = park_a + staged > park_all ? park_a + staged : park_all;
+  cudaFuncSetAttribute(k_fit_mixed<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(smem));
+  const unsigned tiles = static_cast<unsigned>((a.n + T - 1) / T);
+  const int tr = trace_begin(1, st);
+  k_fit_mixed<MODE, T><<<tiles, T, smem, st>>>(a, P, ta);
+  note_launch();
+  trace_end(tr, st);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, cudaStream_t st) {
+cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int32_t* cellc, const int2* clin,
+                             const uint16_t* lidx, int32_t* fallback_count, cudaStream_t st) {
   const Per32 P = make_per32(a.g);
-  const unsigned blocks = static_cast<unsigned>((a.n + kT - 1) / kT);
-  if (mode == FitMode::kDerivs) {
-    const size_t smem = size_t(Groups<FitMode::kDerivs>::NF * kNB + kNM) * kT * sizeof(float);
-    cudaFuncSetAttribute(k_fit_mixed<FitMode::kDerivs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    const int tr = trace_begin(1, st);
-    k_fit_mixed<FitMode::kDerivs><<<blocks, kT, smem, st>>>(a, P);
-    note_launch();
-    trace_end(tr, st);
-  } else {
-    const size_t smem = size_t(Groups<FitMode::kRHS>::NF * kNB + kNM) * kT * sizeof(float);
-    cudaFuncSetAttribute(k_fit_mixed<FitMode::kRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    const int tr = trace_begin(1, st);
-    k_fit_mixed<FitMode::kRHS><<<blocks, kT, smem, st>>>(a, P);
-    note_launch();
-    trace_end(tr, st);
-  }
-  return cudaGetLastError();
+  const TileArgs ta{cellc, clin, lidx, fallback_count};
+  if (mode == FitMode::kDerivs)
+    return a.g.tile == 64 ? launch_t<FitMode::kDerivs, 64>(a, P, ta, st)
+                          : launch_t<FitMode::kDerivs, 128>(a, P, ta, st);
+  return a.g.tile == 64 ? launch_t<FitMode::kRHS, 64>(a, P, ta, st)
+                        : launch_t<FitMode::kRHS, 128>(a, P, ta, st);
 }
 
 }  // namespace phb

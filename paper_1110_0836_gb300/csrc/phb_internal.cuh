@@ -11,12 +11,13 @@ namespace phb {
 
 constexpr int kNF = 8;      // fields rho, Vx, Vy, Vz, Bx, By, Bz, sigma
 constexpr int kRec = 24;    // floats per FP32 particle record (6 x float4)
-constexpr int kEdgeAdj = 11;  // doubles per neighbour edge in the adjoint (8 fields + 3 axes)
+constexpr int kEdgeAdj = 10;  // doubles per neighbour edge in the adjoint (7 fitted fields + 3 axes)
 
 // Workspace regions (byte offsets in plan->ws_off).  The PC-step and adjoint
 // regions share storage (never used at the same time).
 enum Region {
-  R_MISC = 0,    // int32 [64]: 0 = FP64 route-queue length
+  R_MISC = 0,    // int32 [64]: 0 = FP64 route-queue length, 1 = tiles that fell back to
+                 //   global gathers in the last neighbour build
   R_KEYS,        // int32 [n]   cell key of each caller particle
   R_PERM,        // int32 [n]   slot -> caller index
   R_INV,         // int32 [n]   caller index -> slot
@@ -31,14 +32,19 @@ enum Region {
   R_NCNT,        // int32 [n+1]  neighbour counts
   R_OFF,         // int64 [n+1]  CSR offsets (slot order)
   R_IDX,         // int32 [capacity] neighbour slots
+  R_LIDX,        // uint16 [capacity] neighbour index inside the tile's staged neighbourhood
+  R_CELLC,       // int32 [n] packed cell coordinates of each slot (10 bits per axis)
+  R_CLIN,        // int2 [cells] (first slot, count) per linear cell index (x-major)
   R_QUEUE,       // int32 [n]    slots routed to FP64
   R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
   R_PC_Y0,       // double [11][n] saved x^n, U^n (slot order) -- PC step
-  R_ADJ_EDGE,    // double [capacity][11] per-edge adjoint contributions -- adjoint
+  R_ADJ_EDGE,    // double [capacity][10] per-edge adjoint contributions -- adjoint
   R_ADJ_ROFF,    // int64 [n+1] reverse-list offsets                     -- adjoint
   R_ADJ_RIDX,    // int64 [capacity] reverse-list edge ids               -- adjoint
   R_ADJ_RCNT,    // int32 [n+1] reverse-list counts / cursors            -- adjoint
+  R_ADJ_SCR,     // double [266][n] per-particle coefficients c and bbar  -- adjoint
+  R_ADJ_SELF,    // double [11][n] each particle's own adjoint terms      -- adjoint
   R_END_COMMON,  // end of the common part (prefix for RHS / derivs)
   R_END,         // end of everything
   R_COUNT
@@ -56,8 +62,11 @@ __host__ __device__ inline const T* region(const phb_plan* p, const void* ws, Re
 
 // Plain-old-data view of the plan handed to kernels by value.
 struct Grid {
-  double lo[3], len[3], inv_cell[3];
+  double lo[3], len[3], inv_cell[3], cell[3];
   int32_t periodic[3], ncell[3], nbrick[3];
+  int32_t hbits;      // Hilbert order of the brick curve
+  int32_t tile;       // particles per tile
+  int32_t stage_cap;  // staged records per tile
   int32_t n;
   double rf_factor, skin;
   double lambda_min, lambda_max;
@@ -87,12 +96,56 @@ __device__ __forceinline__ int cell_coord(const Grid& g, int a, double x) {
   return u < 0 ? 0 : (u >= nc ? nc - 1 : static_cast<int>(u));
 }
 
-// 4x4x4 bricks in x-major order, Morton order of the 64 cells inside a brick.
+// Index of brick (x, y, z) along a 3-D Hilbert curve of order b (2^b bricks per
+// axis): Skilling's transform of the axes to the transposed Hilbert integer
+// (J. Skilling, AIP Conf. Proc. 707, 381 (2004)), then bit interleaving.
+// Consecutive indices are face-adjacent bricks.
+__host__ __device__ inline uint32_t hilbert3(uint32_t x, uint32_t y, uint32_t z, int b) {
+  if (b <= 0) return 0;
+  uint32_t X[3] = {x, y, z};
+  const uint32_t M = 1u << (b - 1);
+  for (uint32_t Q = M; Q > 1; Q >>= 1) {
+    const uint32_t P = Q - 1;
+    for (int i = 0; i < 3; ++i) {
+      if (X[i] & Q) {
+        X[0] ^= P;
+      } else {
+        const uint32_t t = (X[0] ^ X[i]) & P;
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  X[1] ^= X[0];
+  X[2] ^= X[1];
+  uint32_t t = 0;
+  for (uint32_t Q = M; Q > 1; Q >>= 1)
+    if (X[2] & Q) t ^= Q - 1;
+  X[0] ^= t;
+  X[1] ^= t;
+  X[2] ^= t;
+  uint32_t h = 0;
+  for (int j = b - 1; j >= 0; --j)
+    for (int i = 0; i < 3; ++i) h = (h << 1) | ((X[i] >> j) & 1u);
+  return h;
+}
+
+// Cell key: 4x4x4-cell bricks ordered along the Hilbert curve, Morton order of
+// the 64 cells inside a brick.  Cells that are close in space get close keys,
+// so a run of consecutive particles covers a compact region.
 __device__ __forceinline__ int32_t cell_key(const Grid& g, int cx, int cy, int cz) {
-  int bx = cx >> 2, by = cy >> 2, bz = cz >> 2;
+  const uint32_t hb = hilbert3(static_cast<uint32_t>(cx >> 2), static_cast<uint32_t>(cy >> 2),
+                               static_cast<uint32_t>(cz >> 2), g.hbits);
   int x = cx & 3, y = cy & 3, z = cz & 3;
   int m = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2) | ((x & 2) << 2) | ((y & 2) << 3) | ((z & 2) << 4);
-  return ((bx * g.nbrick[1] + by) * g.nbrick[2] + bz) * 64 + m;
+  return static_cast<int32_t>(hb * 64u + static_cast<uint32_t>(m));
+}
+
+__host__ __device__ inline int32_t pack_cell(int cx, int cy, int cz) { return cx | (cy << 10) | (cz << 20); }
+__host__ __device__ inline void unpack_cell(int32_t p, int& cx, int& cy, int& cz) {
+  cx = p & 1023;
+  cy = (p >> 10) & 1023;
+  cz = (p >> 20) & 1023;
 }
 
 // Minimum-image FP64 offset, d - len * nearbyint(d / len), correctly rounded
@@ -197,7 +250,8 @@ struct FitArgs {
   int32_t* status_word;
 };
 
-cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, cudaStream_t st);
+cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int32_t* cellc, const int2* clin,
+                             const uint16_t* lidx, int32_t* fallback_count, cudaStream_t st);
 // FP64 fused fit over all slots (list == null) or over list[0 .. *list_len).
 cudaError_t launch_fit_fp64(const FitArgs& a, FitMode mode, const int32_t* list,
                             const int32_t* list_len, cudaStream_t st);

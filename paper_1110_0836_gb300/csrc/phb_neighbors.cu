@@ -6,6 +6,7 @@
 // candidates with the exact FP64 test, so every set equals the definition
 // ((dx*dx + dy*dy) + dz*dz) < r*r evaluated in FP64 without contraction.
 #include "phb_internal.cuh"
+#include "phb_tile.cuh"
 
 namespace phb {
 namespace {
@@ -79,21 +80,37 @@ __global__ void k_sort_cells(int64_t nkeys, const int32_t* __restrict__ cell_sta
 __global__ void k_gather_pos(Grid g, const int32_t* __restrict__ perm, const double* __restrict__ pos,
                              const double* __restrict__ lam, int32_t* __restrict__ inv,
                              double* __restrict__ spos, double* __restrict__ slam,
-                             float4* __restrict__ scr) {
+                             float4* __restrict__ scr, int32_t* __restrict__ cellc) {
   const int n = g.n;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int i = perm[s];
   inv[i] = s;
   float w[3];
+  int c[3];
   for (int a = 0; a < 3; ++a) {
     double x = pos[a * n + i];
     spos[a * n + s] = x;
     double xw = g.periodic[a] ? x - g.len[a] * floor((x - g.lo[a]) / g.len[a]) : x;
     w[a] = static_cast<float>(xw);
+    c[a] = isfinite(x) ? cell_coord(g, a, x) : 0;
   }
   slam[s] = lam[i];
   scr[s] = make_float4(w[0], w[1], w[2], 0.f);
+  cellc[s] = pack_cell(c[0], c[1], c[2]);
+}
+
+// (first slot, count) of every cell by linear index, for the tile planner.
+__global__ void k_cell_lin(Grid g, const int32_t* __restrict__ cell_start, int2* __restrict__ clin) {
+  const int64_t total = static_cast<int64_t>(g.ncell[0]) * g.ncell[1] * g.ncell[2];
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= total) return;
+  const int cz = static_cast<int>(k % g.ncell[2]);
+  const int cy = static_cast<int>((k / g.ncell[2]) % g.ncell[1]);
+  const int cx = static_cast<int>(k / (static_cast<int64_t>(g.ncell[2]) * g.ncell[1]));
+  const int32_t key = cell_key(g, cx, cy, cz);
+  const int a = cell_start[key];
+  clin[k] = make_int2(a, cell_start[key + 1] - a);
 }
 
 struct Reach {
@@ -129,19 +146,21 @@ __device__ __forceinline__ int axis_cell(const Grid& g, int a, const Reach& q, i
   return c;
 }
 
+// Thread per particle (slot order): candidates from the cells within reach,
+// looked up through the linear (first slot, count) table; FP32 screen on the
+// wrapped positions, exact FP64 test in the ambiguous band.
 template <bool kFill>
-__global__ void __launch_bounds__(kThreads) k_neighbors(Grid g, const int32_t* __restrict__ cell_start,
-                                                        const float4* __restrict__ scr,
-                                                        const double* __restrict__ spos,
-                                                        const double* __restrict__ slam,
-                                                        int32_t* __restrict__ ncnt,
-                                                        const int64_t* __restrict__ off,
-                                                        int32_t* __restrict__ idx,
-                                                        int32_t* status_word) {
+__global__ void __launch_bounds__(kThreads) k_search(Grid g, const int2* __restrict__ clin,
+                                                     const int32_t* __restrict__ cellc,
+                                                     const float4* __restrict__ scr,
+                                                     const double* __restrict__ spos,
+                                                     const double* __restrict__ slam,
+                                                     int32_t* __restrict__ ncnt,
+                                                     const int64_t* __restrict__ off,
+                                                     int32_t* __restrict__ idx, int32_t* status_word) {
   const int n = g.n;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
-  const double xs = spos[s], ys = spos[n + s], zs = spos[2 * n + s];
   const double r = list_radius(g, slam[s]);
   const double r2 = __dmul_rn(r, r);
   const double m = static_cast<double>(g.screen_margin) + 4e-7 * r;
@@ -153,9 +172,11 @@ __global__ void __launch_bounds__(kThreads) k_neighbors(Grid g, const int32_t* _
     lenf[a] = static_cast<float>(g.len[a]);
     invlf[a] = g.periodic[a] ? static_cast<float>(1.0 / g.len[a]) : 0.f;
   }
-  const Reach qx = axis_reach(g, 0, cell_coord(g, 0, xs), r);
-  const Reach qy = axis_reach(g, 1, cell_coord(g, 1, ys), r);
-  const Reach qz = axis_reach(g, 2, cell_coord(g, 2, zs), r);
+  int c[3];
+  unpack_cell(cellc[s], c[0], c[1], c[2]);
+  const Reach qx = axis_reach(g, 0, c[0], r);
+  const Reach qy = axis_reach(g, 1, c[1], r);
+  const Reach qz = axis_reach(g, 2, c[2], r);
   int64_t base = 0, end = 0;
   if (kFill) {
     base = off[s];
@@ -171,13 +192,13 @@ __global__ void __launch_bounds__(kThreads) k_neighbors(Grid g, const int32_t* _
       bool oky;
       const int cy = axis_cell(g, 1, qy, ky, oky);
       if (!oky) continue;
+      const int64_t row = (static_cast<int64_t>(cx) * g.ncell[1] + cy) * g.ncell[2];
       for (int kz = 0; kz < qz.count; ++kz) {
         bool okz;
         const int cz = axis_cell(g, 2, qz, kz, okz);
         if (!okz) continue;
-        const int32_t key = cell_key(g, cx, cy, cz);
-        const int t0 = cell_start[key], t1 = cell_start[key + 1];
-        for (int t = t0; t < t1; ++t) {
+        const int2 sc = clin[row + cz];
+        for (int t = sc.x; t < sc.x + sc.y; ++t) {
           if (t == s) continue;
           const float4 o = scr[t];
           float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
@@ -201,6 +222,41 @@ __global__ void __launch_bounds__(kThreads) k_neighbors(Grid g, const int32_t* _
     }
   }
   if (!kFill) ncnt[s] = count;
+}
+
+// One CTA per tile: map every list entry of the tile's particles to its index
+// in the tile's staged neighbourhood (the fused fit rebuilds the same plan).
+template <int T>
+__global__ void __launch_bounds__(T) k_localize(Grid g, const int2* __restrict__ clin,
+                                                const int32_t* __restrict__ cellc,
+                                                const double* __restrict__ slam,
+                                                const int64_t* __restrict__ off,
+                                                const int32_t* __restrict__ idx,
+                                                uint16_t* __restrict__ lidx,
+                                                int32_t* fallback_count) {
+  __shared__ TileShared ts;
+  __shared__ unsigned bits[kBoxWords];
+  __shared__ int wpre[kBoxWords];
+  __shared__ int base[kMarkCap + 1];
+  __shared__ int cstart[kMarkCap];
+  __shared__ int warp_tmp[T / 32 + 1];
+  const TileArrays tarr{bits, wpre, base, cstart, warp_tmp};
+  const int n = g.n;
+  const int s0 = blockIdx.x * T;
+  const int cnt = min(T, n - s0);
+  tile_plan<T>(g, s0, cnt, cellc, slam, clin, ts, tarr);
+  if (ts.fallback) {
+    if (threadIdx.x == 0) atomicAdd(fallback_count, 1);
+    return;
+  }
+  const int64_t e0 = off[s0];
+  int64_t e1 = off[s0 + cnt];
+  if (e1 > g.capacity) e1 = g.capacity;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += T) {
+    const int t = idx[e];
+    const int j = marked_index(tarr, box_index(g, ts, cellc[t]));
+    lidx[e] = static_cast<uint16_t>(base[j] + (t - cstart[j]));
+  }
 }
 
 // -------- export in caller numbering
@@ -250,6 +306,10 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   int32_t* ncnt = region<int32_t>(p, ws, R_NCNT);
   int64_t* off = region<int64_t>(p, ws, R_OFF);
   int32_t* idx = region<int32_t>(p, ws, R_IDX);
+  uint16_t* lidx = region<uint16_t>(p, ws, R_LIDX);
+  int32_t* cellc = region<int32_t>(p, ws, R_CELLC);
+  int2* clin = region<int2>(p, ws, R_CLIN);
+  int32_t* misc = region<int32_t>(p, ws, R_MISC);
   cudaError_t e;
   if ((e = cudaMemsetAsync(cell, 0, (p->nkeys + 1) * sizeof(int32_t), st))) return e;
   if ((e = cudaMemsetAsync(cursor, 0, p->nkeys * sizeof(int32_t), st))) return e;
@@ -260,15 +320,25 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   note_launch();
   k_sort_cells<<<blocks_for(p->nkeys), kThreads, 0, st>>>(p->nkeys, cell, perm);
   note_launch();
-  k_gather_pos<<<blocks_for(n), kThreads, 0, st>>>(g, perm, pos, lam, inv, spos, slam, scr);
+  k_gather_pos<<<blocks_for(n), kThreads, 0, st>>>(g, perm, pos, lam, inv, spos, slam, scr, cellc);
   note_launch();
-  k_neighbors<false><<<blocks_for(n), kThreads, 0, st>>>(g, cell, scr, spos, slam, ncnt, nullptr,
-                                                          nullptr, status_word);
+  const int64_t ncells = int64_t(p->ncell[0]) * p->ncell[1] * p->ncell[2];
+  k_cell_lin<<<blocks_for(ncells), kThreads, 0, st>>>(g, cell, clin);
+  note_launch();
+  if ((e = cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), st))) return e;
+  k_search<false><<<blocks_for(n), kThreads, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, nullptr,
+                                                       nullptr, status_word);
   note_launch();
   if ((e = cudaMemsetAsync(ncnt + n, 0, sizeof(int32_t), st))) return e;
   if ((e = scan_exclusive_i32_to_i64(ncnt, off, n + 1, bsum, st))) return e;
-  k_neighbors<true><<<blocks_for(n), kThreads, 0, st>>>(g, cell, scr, spos, slam, ncnt, off, idx,
-                                                         status_word);
+  k_search<true><<<blocks_for(n), kThreads, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, off, idx,
+                                                      status_word);
+  note_launch();
+  const unsigned tiles = static_cast<unsigned>(p->ntiles);
+  if (p->tile == 128)
+    k_localize<128><<<tiles, 128, 0, st>>>(g, clin, cellc, slam, off, idx, lidx, misc + 1);
+  else
+    k_localize<64><<<tiles, 64, 0, st>>>(g, clin, cellc, slam, off, idx, lidx, misc + 1);
   note_launch();
   return cudaGetLastError();
 }

@@ -23,10 +23,14 @@ Grid make_grid(const phb_plan* p) {
     g.lo[a] = p->box.lo[a];
     g.len[a] = p->box.len[a];
     g.inv_cell[a] = 1.0 / p->cell[a];
+    g.cell[a] = p->cell[a];
     g.periodic[a] = p->box.periodic[a] ? 1 : 0;
     g.ncell[a] = p->ncell[a];
     g.nbrick[a] = p->nbrick[a];
   }
+  g.hbits = p->hilbert_bits;
+  g.tile = p->tile;
+  g.stage_cap = p->stage_cap;
   g.n = static_cast<int32_t>(p->n);
   g.rf_factor = p->rf_factor;
   g.skin = p->skin;
@@ -185,23 +189,34 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
     if (p->box.periodic[a] && !(rmax < 0.5 * p->box.len[a])) return PHB_ERR_INVALID_ARG;
   double frac = p->cell_frac > 0 ? p->cell_frac : 0.5;
   double h = frac * rmin;
-  // keep the key space modest: at most 2^27 cells
+  // at most 1023 cells per axis (10-bit packed coordinates), 2^26 cells in all
+  for (int a = 0; a < 3; ++a) h = std::max(h, p->box.len[a] / 1023.0);
   for (int it = 0; it < 64; ++it) {
     double cells = 1;
     for (int a = 0; a < 3; ++a) cells *= std::max(1.0, std::floor(p->box.len[a] / h));
-    if (cells <= double(1 << 27)) break;
-    h *= 1.25;
+    if (cells <= double(1 << 26)) break;
+    h *= 1.1;
   }
-  int64_t nkeys = 64;
+  int maxb = 1;
   for (int a = 0; a < 3; ++a) {
     int nc = static_cast<int>(std::max(1.0, std::floor(p->box.len[a] / h)));
+    nc = std::min(nc, 1023);
     p->ncell[a] = nc;
     p->cell[a] = p->box.len[a] / nc;
     p->nbrick[a] = (nc + 3) / 4;
-    nkeys *= p->nbrick[a];
+    maxb = std::max(maxb, p->nbrick[a]);
   }
+  int hb = 0;
+  while ((1 << hb) < maxb) ++hb;
+  p->hilbert_bits = hb;
+  const int64_t nkeys = (int64_t(1) << (3 * hb)) * 64;
   if (nkeys >= (int64_t(1) << 31) - 2) return PHB_ERR_INVALID_ARG;
   p->nkeys = nkeys;
+  if (p->tile == 0) p->tile = 128;
+  if (p->tile != 64 && p->tile != 128) return PHB_ERR_INVALID_ARG;
+  if (p->stage_cap == 0) p->stage_cap = p->tile == 128 ? 1500 : 768;
+  if (p->stage_cap < 64 || p->stage_cap > 2048) return PHB_ERR_INVALID_ARG;
+  p->ntiles = static_cast<int32_t>((p->n + p->tile - 1) / p->tile);
   // FP32 screen: bound of |d32 - d| per component is 2^-24 (2X + 3L); two
   // components' worth of safety on top, times sqrt(3) for the norm.
   p->screen_margin = 8.0 * std::sqrt(3.0) * std::ldexp(1.0, -24) * (2.0 * xmax + 3.0 * lmax);
@@ -223,6 +238,9 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   sz[R_NCNT] = (n + 1) * 4;
   sz[R_OFF] = (n + 1) * 8;
   sz[R_IDX] = cap * 4;
+  sz[R_LIDX] = cap * 2;
+  sz[R_CELLC] = n * 4;
+  sz[R_CLIN] = size_t(p->ncell[0]) * p->ncell[1] * p->ncell[2] * 8;
   sz[R_QUEUE] = (n + 64) * 4;  // also the export's n+1 counts
   size_t off = 0;
   for (int r = R_MISC; r <= R_QUEUE; ++r) {
@@ -248,6 +266,10 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   ad += align256(size_t(cap) * 8);
   p->ws_off[R_ADJ_RCNT] = ad;
   ad += align256(size_t(n + 1) * 4);
+  p->ws_off[R_ADJ_SCR] = ad;
+  ad += align256(size_t(266) * n * 8);
+  p->ws_off[R_ADJ_SELF] = ad;
+  ad += align256(size_t(11) * n * 8);
   p->ws_off[R_END] = std::max(pc, ad);
   p->ws_bytes = p->ws_off[R_END];
   return PHB_OK;

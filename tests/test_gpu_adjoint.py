@@ -1,0 +1,109 @@
+"""GPU adjoint of the fused fit + RHS (hand-written reverse mode) against the
+oracle's forward-mode derivative and against central finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from _gpu import need_gpu, sample, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(phb, w, **prm):
+    plan = phb.Plan.for_workload(w)
+    pos, lam, U = phb.tensors_of(w)
+    phb.build_neighbors(plan, pos, lam)
+    return plan, pos, lam, U, phb.Params(gamma=w.gamma, precision="fp64", **prm)
+
+
+@pytest.mark.parametrize("with_terms", [False, True])
+def test_dot_product_against_oracle_jvp(with_terms):
+    """<gbar, J v> from the oracle's dual numbers equals <J^T gbar, v> from the
+    GPU adjoint (all particles, neighbour sets fixed)."""
+    phb = need_gpu()
+    w = workloads.random_modes(12, seed=41, amp=0.05)
+    rng = np.random.default_rng(5)
+    kw = {}
+    zeta = eta = None
+    if with_terms:
+        zeta = rng.uniform(0, 0.05, w.n)
+        eta = rng.uniform(0, 0.02, w.n)
+        kw = dict(zeta=torch.tensor(zeta, device="cuda"), eta=torch.tensor(eta, device="cuda"))
+    plan, pos, lam, U, prm = setup(phb, w, **kw)
+    gbar = rng.standard_normal((8, w.n))
+    Ub, xb = phb.rhs_adjoint(plan, prm, pos, lam, U, torch.tensor(gbar, device="cuda"))
+    Ub, xb = Ub.cpu().numpy(), xb.cpu().numpy()
+    vpos = rng.standard_normal((3, w.n)) * w.lam
+    vU = rng.standard_normal((8, w.n))
+    box = oracle.box_of(w)
+    nb = oracle.neighbors(box, w.pos, w.lam)
+    _, jv = oracle.rhs_jvp(box, w.pos, w.lam, w.U, vpos, vU, nb, gamma=w.gamma, zeta=zeta, eta=eta)
+    lhs = float((gbar * jv).sum())
+    rhs = float((Ub * vU).sum() + (xb * vpos).sum())
+    assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), 1.0), (lhs, rhs)
+
+
+def test_gradient_entries_against_oracle_and_central_differences():
+    """L = sum_ik r_ik (dU_k/dt)_i: dL/dx and dL/dU on 64 seeded entries vs the
+    oracle's exact directional derivatives (unit directions) and vs central
+    differences of the GPU FP64 forward (step 1e-6)."""
+    phb = need_gpu()
+    w = workloads.random_modes(12, seed=42, amp=0.05)
+    plan, pos, lam, U, prm = setup(phb, w)
+    r = workloads.loss_weights(w.n, seed=7)
+    Ub, xb = phb.rhs_adjoint(plan, prm, pos, lam, U, torch.tensor(r, device="cuda"))
+    Ub, xb = Ub.cpu().numpy(), xb.cpu().numpy()
+    rng = np.random.default_rng(3)
+    box = oracle.box_of(w)
+    nb = oracle.neighbors(box, w.pos, w.lam)
+    out = torch.empty((8, w.n), dtype=torch.float64, device="cuda")
+    scale = max(np.abs(Ub).max(), np.abs(xb).max() * w.lam.min())
+    for k in range(64):
+        which = "x" if k % 3 == 0 else "U"
+        i = int(rng.integers(w.n))
+        c = int(rng.integers(3 if which == "x" else 8))
+        vpos = np.zeros((3, w.n))
+        vU = np.zeros((8, w.n))
+        (vpos if which == "x" else vU)[c, i] = 1.0
+        _, jv = oracle.rhs_jvp(box, w.pos, w.lam, w.U, vpos, vU, nb, gamma=w.gamma)
+        exact = float((r * jv).sum())
+        got = float(xb[c, i] if which == "x" else Ub[c, i])
+        assert abs(got - exact) <= 1e-9 * scale + 1e-9 * abs(exact), (which, c, i, got, exact)
+        # central differences of the GPU forward (neighbour lists held fixed)
+        h = 1e-6 * (w.lam[i] if which == "x" else 1.0)
+        vals = []
+        for sgn in (1.0, -1.0):
+            p2, U2 = pos.clone(), U.clone()
+            (p2 if which == "x" else U2)[c, i] += sgn * h
+            phb.mhd_rhs(plan, prm, p2, lam, U2, out=out)
+            vals.append(float((out.cpu().numpy() * r).sum()))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - exact) <= 1e-6 * max(abs(exact), scale * (w.lam[i] if which == "x" else 1)), \
+            (which, c, i, fd, exact)
+
+
+def test_autograd_function():
+    phb = need_gpu()
+    w = workloads.random_modes(10, seed=43, amp=0.05)
+    plan, pos, lam, U, prm = setup(phb, w)
+    pos_t = pos.clone().requires_grad_(True)
+    U_t = U.clone().requires_grad_(True)
+    r = torch.tensor(workloads.loss_weights(w.n, seed=9), device="cuda")
+    loss = (phb.rhs_autograd(pos_t, U_t, lam, plan, prm) * r).sum()
+    loss.backward()
+    Ub, xb = phb.rhs_adjoint(plan, prm, pos, lam, U, r)
+    assert torch.equal(U_t.grad, Ub) and torch.equal(pos_t.grad, xb)
+    # forward of the autograd path equals the plain call
+    out, _ = phb.mhd_rhs(plan, prm, pos, lam, U)
+    assert torch.equal(phb.rhs_autograd(pos, U, lam, plan, prm), out)
+
+
+def test_deterministic():
+    phb = need_gpu()
+    w = workloads.random_modes(12, seed=44)
+    plan, pos, lam, U, prm = setup(phb, w)
+    g = torch.tensor(np.random.default_rng(1).standard_normal((8, w.n)), device="cuda")
+    a1 = phb.rhs_adjoint(plan, prm, pos, lam, U, g)
+    a2 = phb.rhs_adjoint(plan, prm, pos, lam, U, g)
+    assert torch.equal(a1[0], a2[0]) and torch.equal(a1[1], a2[1])

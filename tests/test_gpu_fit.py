@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import workloads
-from _gpu import RHS_FLOOR, kind_err, need_gpu, sample, torch
+from _gpu import kind_err, need_gpu, rhs_err, rhs_term_scales, sample, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +37,14 @@ def oracle_run(w, mode="rhs", query=None, **kw):
     return (g, h), st
 
 
+def term_scales(w, query=None, zeta=None, eta=None, **kw):
+    """Scale of each RHS equation's terms at the (query) particles, from oracle derivatives."""
+    (g, h), _ = oracle_run(w, "derivs", query, **kw)
+    q = slice(None) if query is None else query
+    return rhs_term_scales(w.U[:, q], g, h, w.gamma,
+                           None if zeta is None else zeta[q], None if eta is None else eta[q])
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_mixed", 1e-5)])
 def test_derivs_small_lattice(prec, tol):
     phb = need_gpu()
@@ -57,7 +65,7 @@ def test_rhs_small(prec, tol, which):
     out, st, plan = gpu_run(phb, w, phb.Params(gamma=w.gamma, precision=prec))
     exp, sto = oracle_run(w)
     assert (st == 0).all()
-    e = kind_err(out, exp, RHS_FLOOR)
+    e = rhs_err(out, exp, term_scales(w))
     assert e.max() < tol, e
 
 
@@ -69,7 +77,7 @@ def test_rhs_full_size_sampled(prec, tol):
     out, st, plan = gpu_run(phb, w, phb.Params(gamma=w.gamma, precision=prec))
     q = sample(w.n, 600, seed=7)
     exp, sto = oracle_run(w, query=q)
-    e = kind_err(out[:, q], exp, RHS_FLOOR)
+    e = rhs_err(out[:, q], exp, term_scales(w, q))
     assert e.max() < tol, e
     assert (st[q] == 0).all()
 
@@ -84,10 +92,11 @@ def test_viscosity_and_divb_terms_fp64():
                      eta=torch.tensor(eta, device="cuda"))
     out, st, _ = gpu_run(phb, w, prm)
     exp, _ = oracle_run(w, zeta=zeta, eta=eta)
-    assert kind_err(out, exp, RHS_FLOOR).max() < 1e-12
+    sc = term_scales(w, zeta=zeta, eta=eta)
+    assert rhs_err(out, exp, sc).max() < 1e-12
     prm.precision = "fp32_mixed"
     out, st, _ = gpu_run(phb, w, prm)
-    assert kind_err(out, exp, RHS_FLOOR).max() < 1e-5
+    assert rhs_err(out, exp, sc).max() < 1e-5
 
 
 def test_unweighted_fit():
@@ -95,7 +104,7 @@ def test_unweighted_fit():
     w = workloads.random_modes(14, seed=6)
     out, st, _ = gpu_run(phb, w, phb.Params(gamma=w.gamma, precision="fp64", weight_kind=1))
     exp, _ = oracle_run(w, weight_kind=1)
-    assert kind_err(out, exp, RHS_FLOOR).max() < 1e-12
+    assert rhs_err(out, exp, term_scales(w, weight_kind=1)).max() < 1e-12
 
 
 def test_singular_fits_open_box():
@@ -112,9 +121,17 @@ def test_singular_fits_open_box():
         sing = sto == 1
         assert (st[sing] == 1).all()
         assert not g[:, :, sing].any() and not h[:, :, sing].any()
-        ok = ~sing & (st == 0)
-        tol = 1e-12 if prec == "fp64" else 1e-4
-        assert kind_err(g[:, :, ok], go[:, :, ok]).max() < tol
+        ok = ~sing & (st != 1)
+        # interior particles (full neighbour spheres) meet the bars; fits at the
+        # open faces are one-sided and so ill-conditioned that the least-squares
+        # solution itself moves at ~1e-10 under FP64 rounding (QR or not)
+        rf = 2.3 * w.lam.max()
+        inner = ok & np.all((w.pos > rf) & (w.pos < 1 - rf), axis=0)
+        edge = ok & ~inner
+        tol_in, tol_edge = (1e-12, 1e-8) if prec == "fp64" else (1e-5, 1e-3)
+        scale = np.abs(go[:, :, ok]).max(axis=(1, 2))
+        assert (np.abs(g[:, :, inner] - go[:, :, inner]).max(axis=(1, 2)) / scale).max() < tol_in
+        assert (np.abs(g[:, :, edge] - go[:, :, edge]).max(axis=(1, 2)) / scale).max() < tol_edge
         assert plan.read_status() & _lib.FLAG_FIT_SINGULAR
 
 
@@ -126,7 +143,7 @@ def test_forced_fp64_routing():
                                            cond_threshold=1.0))
     exp, _ = oracle_run(w)
     assert (st == 2).all()
-    assert kind_err(out, exp, RHS_FLOOR).max() < 1e-12
+    assert rhs_err(out, exp, term_scales(w)).max() < 1e-12
 
 
 def test_shock_tube_variable_lambda():
@@ -135,11 +152,12 @@ def test_shock_tube_variable_lambda():
     w = workloads.shock_tube(60000, seed=12)
     q = sample(w.n, 1500, seed=2)
     exp, sto = oracle_run(w, query=q)
+    sc = term_scales(w, q)
     out64, st64, _ = gpu_run(phb, w, phb.Params(gamma=w.gamma, precision="fp64"))
-    assert kind_err(out64[:, q], exp, RHS_FLOOR).max() < 1e-12
+    assert rhs_err(out64[:, q], exp, sc).max() < 1e-12
     out32, st32, _ = gpu_run(phb, w, phb.Params(gamma=w.gamma, precision="fp32_mixed"))
     # steep tanh profiles: FP32 accumulation error, see the design doc
-    assert kind_err(out32[:, q], exp, RHS_FLOOR).max() < 2e-4
+    assert rhs_err(out32[:, q], exp, sc).max() < 2e-4
     assert (st32 == 2).mean() < 0.01
 
 
@@ -150,3 +168,22 @@ def test_nonfinite_input_is_flagged():
     w.U[3, 17] = np.nan
     out, st, plan = gpu_run(phb, w, phb.Params(gamma=w.gamma))
     assert plan.read_status() & _lib.FLAG_NONFINITE
+
+
+@pytest.mark.parametrize("tile,stage_cap", [(64, 0), (128, 0), (128, 64), (64, 64)])
+def test_tile_shapes_and_global_fallback(tile, stage_cap):
+    """Both tile sizes, and a staging capacity so small that every tile reads its
+    neighbours from global memory, give the same answers within the bars."""
+    phb = need_gpu()
+    w = workloads.random_modes(16, seed=31)
+    plan = phb.Plan.for_workload(w, tile=tile, stage_cap=stage_cap)
+    exp, _ = oracle_run(w)
+    sc = term_scales(w)
+    for prec, tol in (("fp32_mixed", 1e-5), ("fp64", 1e-12)):
+        out, st, plan = gpu_run(phb, w, phb.Params(gamma=w.gamma, precision=prec), plan=plan)
+        assert rhs_err(out, exp, sc).max() < tol
+    stats = plan.stats()
+    if stage_cap == 64:
+        assert stats["fit_fallback_tiles"] == stats["tiles"] == plan.c.ntiles
+    elif tile == 128:
+        assert stats["fit_fallback_tiles"] < 0.1 * stats["tiles"]

@@ -119,3 +119,15 @@ def test_full_size_lattice_sampled():
     assert_equal_sets(got, oracle_sets(w, q), q)
     cnt = np.array([len(x) for x in got])
     assert cnt.min() >= 40 and cnt.max() <= 62
+
+
+@pytest.mark.parametrize("tile,stage_cap", [(64, 0), (128, 64)])
+def test_tiled_and_fallback_search_agree(tile, stage_cap):
+    phb = need_gpu()
+    w = workloads.shock_tube(20000, seed=5)
+    got, plan = gpu_sets(phb, w, tile=tile, stage_cap=stage_cap)
+    q = sample(w.n, 1500, seed=3)
+    assert_equal_sets(got, oracle_sets(w, q), q)
+    if stage_cap == 64:
+        st = plan.stats()
+        assert st["build_fallback_tiles"] == st["tiles"]
