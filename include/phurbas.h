@@ -206,6 +206,32 @@ phb_status phb_rhs_adjoint(const phb_plan* plan, const phb_params* params, const
                            void* ws, size_t ws_bytes, double* Ubar, double* xbar,
                            int32_t* status_word, phb_stream_t stream);
 
+/* Neighbour build + fused right-hand side (phb_build_neighbors followed by
+ * phb_mhd_rhs) without any device allocation and without a caller workspace.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory where they need the right-hand side (a pool that forbids new
+ * allocations, a framework that owns every device buffer, a loop that must
+ * not block on the allocator).  The caller still passes pos, lambda, U, dudt,
+ * fit_status (may be NULL) and status_word as in phb_mhd_rhs.
+ *   - Scratch: one file-scope device array of phb_noalloc_scratch_bytes()
+ *     (32 MiB) that every GPU which loads the library holds until exit.  A
+ *     plan whose build-and-fit workspace (everything before the
+ *     predictor-corrector regions) is larger returns PHB_ERR_WORKSPACE and
+ *     launches nothing; with constant lambda this allows roughly 48,000
+ *     particles.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; the kernels
+ *     clear what must start at zero.  Calls that overlap on the GPU (other
+ *     streams, other threads) race on the array: serialise them.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+phb_status phb_mhd_rhs_noalloc(const phb_plan* plan, const phb_params* params, const double* pos,
+                               const double* lambda, const double* U, double* dudt,
+                               int32_t* fit_status, int32_t* status_word, phb_stream_t stream);
+
+/* Size in bytes of the scratch array used by phb_mhd_rhs_noalloc. */
+size_t phb_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,8 @@ PHB_FP64, PHB_FP32_MIXED = 0, 1
 EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_check",
            "phb_build_neighbors", "phb_export_neighbors", "phb_neighbor_total", "phb_mls_derivs",
            "phb_mhd_rhs", "phb_pc_step", "phb_rhs_adjoint", "phb_fma_peak", "phb_launch_count",
-           "phb_trace_start", "phb_trace_stop", "phb_workspace_stats"]
+           "phb_trace_start", "phb_trace_stop", "phb_workspace_stats", "phb_mhd_rhs_noalloc",
+           "phb_noalloc_scratch_bytes"]
 
 
 class Box(C.Structure):
@@ -92,6 +93,10 @@ def lib(path: str | None = None) -> C.CDLL:
     L.phb_trace_stop.restype = C.c_int
     L.phb_workspace_stats.argtypes = [P(Plan), _vp, _vp, C.c_int32, _vp]
     L.phb_workspace_stats.restype = C.c_int
+    L.phb_mhd_rhs_noalloc.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.phb_mhd_rhs_noalloc.restype = C.c_int
+    L.phb_noalloc_scratch_bytes.argtypes = []
+    L.phb_noalloc_scratch_bytes.restype = C.c_size_t
     for f in ("phb_plan_init", "phb_check", "phb_build_neighbors", "phb_export_neighbors",
               "phb_mls_derivs", "phb_mhd_rhs", "phb_pc_step", "phb_rhs_adjoint"):
         getattr(L, f).restype = C.c_int
