@@ -103,6 +103,9 @@ typedef struct {
   double cell_frac;      /* cell edge / (rf_factor*lambda_min + skin); 0 = default 0.5 */
   int32_t tile;          /* particles per fused-fit tile (64 or 128; 0 = default 128) */
   int32_t stage_cap;     /* neighbourhood records staged per tile (0 = default) */
+  int32_t schedule;      /* fused fit: 0 = one CTA per tile in cell order; 1 = persistent CTAs
+                            taking tiles from a queue in descending-cost order */
+  int32_t pad2_;
   /* filled by phb_plan_init */
   double cell[3];        /* cell edge per axis */
   int32_t ncell[3];      /* cells per axis (at most 1023) */
@@ -205,6 +208,30 @@ phb_status phb_rhs_adjoint(const phb_plan* plan, const phb_params* params, const
                            const double* lambda, const double* U, const double* gbar,
                            void* ws, size_t ws_bytes, double* Ubar, double* xbar,
                            int32_t* status_word, phb_stream_t stream);
+
+/* Stored-factorisation variant of phb_rhs_adjoint (not in the paper; offered
+ * to compare memory and time against recomputation).
+ * phb_adjoint_record_bytes(plan): bytes of the per-particle record, 343
+ * doubles per particle = the Jacobi-scaled Cholesky factor of the 19 x 19
+ * normal matrix (190), its scaling (19), the fitted coefficients of the seven
+ * fields V, B, sigma (7 x 19) and a singular flag, [343][n] in the
+ * workspace's slot order.  0 for an invalid plan.
+ * phb_adjoint_record: FP64 fits of every particle with the lists of the last
+ * build; writes the record (device, caller-owned, >= record_bytes).
+ * phb_rhs_adjoint_stored: the same result as phb_rhs_adjoint, starting from
+ * a record made with the same plan, lists, pos, lambda and U (not checked;
+ * a stale record gives wrong gradients).  Both return PHB_ERR_INVALID_ARG
+ * for a NULL or too small record; otherwise as phb_rhs_adjoint. */
+size_t phb_adjoint_record_bytes(const phb_plan* plan);
+phb_status phb_adjoint_record(const phb_plan* plan, const phb_params* params, const double* pos,
+                              const double* lambda, const double* U, void* ws, size_t ws_bytes,
+                              double* record, size_t record_bytes, int32_t* status_word,
+                              phb_stream_t stream);
+phb_status phb_rhs_adjoint_stored(const phb_plan* plan, const phb_params* params,
+                                  const double* pos, const double* lambda, const double* U,
+                                  const double* gbar, void* ws, size_t ws_bytes,
+                                  const double* record, size_t record_bytes, double* Ubar,
+                                  double* xbar, int32_t* status_word, phb_stream_t stream);
 
 /* Neighbour build + fused right-hand side (phb_build_neighbors followed by
  * phb_mhd_rhs) without any device allocation and without a caller workspace.

@@ -48,6 +48,13 @@ int phb_workspace_stats(const phb_plan* plan, const void* ws, int32_t* out, int3
                         phb_stream_t stream);
 int phb_trace_stop(float* ms, int32_t* kernel_ids, int32_t capacity);
 
+/* Same read-out as phb_trace_stop without destroying the events or disarming
+ * the trace.  For launches captured into a CUDA graph while the trace was
+ * armed, the event pairs are recorded by the graph at every replay, so a read
+ * after each replay gives that replay's kernel durations.  Returns the number
+ * of recorded pairs (capped at capacity) or -1. */
+int phb_trace_read(float* ms, int32_t* kernel_ids, int32_t capacity);
+
 #ifdef __cplusplus
 }
 #endif

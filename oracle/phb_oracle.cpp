@@ -22,7 +22,7 @@
 //   * a forward-mode (dual number) derivative of the right-hand side with the
 //     neighbour sets frozen, used to pin the hand-written reverse-mode adjoint.
 //
-// Readings where the paper defers to Paper I (all listed in the design doc):
+// Readings where the paper defers to Paper I:
 //   weight w = (1 - s^2)^2 with s = |d| / r_f,i (or w = 1);
 //   basis = the 19 monomials of total degree 1..3 in q = d / lambda_i,
 //   graded-lexicographic order x y z xx xy xz yy yz zz xxx xxy xxz xyy xyz xzz

@@ -6,8 +6,9 @@ fit + ideal-MHD Lagrangian right-hand side (FP32-mixed with FP64 routing, or
 FP64), the Heun predictor-corrector step, and the hand-written adjoint.
 """
 from ._lib import PhbError  # noqa: F401
-from .api import (FIELDS, Params, Plan, build_neighbors, export_neighbors, mhd_rhs,  # noqa: F401
-                  mls_derivs, pc_step, rhs, rhs_adjoint, tensors_of)
+from .api import (FIELDS, Params, Plan, StepGraph, adjoint_record, build_neighbors,  # noqa: F401
+                  export_neighbors, mhd_rhs, mls_derivs, pc_step, rhs, rhs_adjoint,
+                  rhs_adjoint_stored, tensors_of)
 from .autograd import PhbRHS, rhs_autograd  # noqa: F401
 
 

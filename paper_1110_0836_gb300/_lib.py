@@ -16,12 +16,18 @@ PHB_ERR_SKIN, PHB_WARN_FIT, PHB_ERR_TIMEOUT, PHB_ERR_NONFINITE = 5, 6, 7, 8
 FLAG_CAPACITY, FLAG_SKIN, FLAG_FIT_SINGULAR, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_LAMBDA_RANGE = (
     0x01, 0x02, 0x04, 0x08, 0x10, 0x20)
 PHB_FP64, PHB_FP32_MIXED = 0, 1
+# ws_off index where the workspace part shared by neighbour build, fit and RHS ends
+# (position of R_END_COMMON in the library's region enumeration)
+WS_END_COMMON = 29
+# first and last adjoint regions (R_ADJ_EDGE, R_ADJ_SELF; the latter holds 11 doubles per particle)
+WS_ADJ_EDGE, WS_ADJ_SELF = 23, 28
 
 EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_check",
            "phb_build_neighbors", "phb_export_neighbors", "phb_neighbor_total", "phb_mls_derivs",
            "phb_mhd_rhs", "phb_pc_step", "phb_rhs_adjoint", "phb_fma_peak", "phb_launch_count",
-           "phb_trace_start", "phb_trace_stop", "phb_workspace_stats", "phb_mhd_rhs_noalloc",
-           "phb_noalloc_scratch_bytes"]
+           "phb_trace_start", "phb_trace_stop", "phb_trace_read", "phb_workspace_stats", "phb_mhd_rhs_noalloc",
+           "phb_noalloc_scratch_bytes", "phb_adjoint_record_bytes", "phb_adjoint_record",
+           "phb_rhs_adjoint_stored"]
 
 
 class Box(C.Structure):
@@ -38,7 +44,7 @@ class Plan(C.Structure):
     _fields_ = [("box", Box), ("n", C.c_int64), ("rf_factor", C.c_double), ("skin", C.c_double),
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double),
                 ("nbr_capacity", C.c_int64), ("cell_frac", C.c_double), ("tile", C.c_int32),
-                ("stage_cap", C.c_int32),
+                ("stage_cap", C.c_int32), ("schedule", C.c_int32), ("pad2_", C.c_int32),
                 ("cell", C.c_double * 3), ("ncell", C.c_int32 * 3), ("nbrick", C.c_int32 * 3),
                 ("hilbert_bits", C.c_int32), ("ntiles", C.c_int32),
                 ("nkeys", C.c_int64), ("screen_margin", C.c_double), ("ws_bytes", C.c_size_t),
@@ -83,6 +89,12 @@ def lib(path: str | None = None) -> C.CDLL:
                               _vp]
     L.phb_rhs_adjoint.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp, _vp,
                                   _vp, _vp]
+    L.phb_adjoint_record_bytes.argtypes = [P(Plan)]
+    L.phb_adjoint_record_bytes.restype = C.c_size_t
+    L.phb_adjoint_record.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, C.c_size_t, _vp,
+                                     C.c_size_t, _vp, _vp]
+    L.phb_rhs_adjoint_stored.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, _vp, C.c_size_t,
+                                         _vp, C.c_size_t, _vp, _vp, _vp, _vp]
     L.phb_fma_peak.argtypes = [C.c_int32, C.c_int32, C.c_int32, _vp, _vp]
     L.phb_fma_peak.restype = C.c_int
     L.phb_launch_count.argtypes = []
@@ -91,6 +103,8 @@ def lib(path: str | None = None) -> C.CDLL:
     L.phb_trace_start.restype = C.c_int
     L.phb_trace_stop.argtypes = [_vp, _vp, C.c_int32]
     L.phb_trace_stop.restype = C.c_int
+    L.phb_trace_read.argtypes = [_vp, _vp, C.c_int32]
+    L.phb_trace_read.restype = C.c_int
     L.phb_workspace_stats.argtypes = [P(Plan), _vp, _vp, C.c_int32, _vp]
     L.phb_workspace_stats.restype = C.c_int
     L.phb_mhd_rhs_noalloc.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, _vp, _vp, _vp]

@@ -63,13 +63,14 @@ class Plan:
 
     def __init__(self, box_lo, box_len, periodic, n: int, lambda_min: float, lambda_max: float,
                  rf_factor: float = 2.3, skin: float = 0.0, nbr_capacity: int | None = None,
-                 cell_frac: float = 0.0, tile: int = 0, stage_cap: int = 0, device="cuda"):
+                 cell_frac: float = 0.0, tile: int = 0, stage_cap: int = 0, schedule: int = 0,
+                 device="cuda"):
         self.device = torch.device(device)
         self.args = dict(box_lo=tuple(map(float, box_lo)), box_len=tuple(map(float, box_len)),
                          periodic=tuple(int(bool(p)) for p in periodic), n=int(n),
                          lambda_min=float(lambda_min), lambda_max=float(lambda_max),
                          rf_factor=float(rf_factor), skin=float(skin), cell_frac=float(cell_frac),
-                         tile=int(tile), stage_cap=int(stage_cap))
+                         tile=int(tile), stage_cap=int(stage_cap), schedule=int(schedule))
         if nbr_capacity is None:
             # ~51 neighbours at r_f = 2.3 lambda and uniform density; margin for
             # density contrast and the skin shell
@@ -94,6 +95,7 @@ class Plan:
         p.cell_frac = a["cell_frac"]
         p.tile = a["tile"]
         p.stage_cap = a["stage_cap"]
+        p.schedule = a["schedule"]
         check(_lib.lib().phb_plan_init(C.byref(p)), "phb_plan_init")
         self.c = p
         self.ws = torch.empty(int(p.ws_bytes), dtype=torch.uint8, device=self.device)
@@ -230,6 +232,41 @@ def rhs_adjoint(plan: Plan, params: Params, pos, lam, U, gbar, Ubar=None, xbar=N
     return Ubar, xbar
 
 
+def adjoint_record(plan: Plan, params: Params, pos, lam, U, record=None):
+    """Per-particle FP64 factorisations and coefficients for phb_rhs_adjoint_stored
+    (phb_adjoint_record), with the lists of the last build.  Returns the record
+    (float64 [343, n] device tensor, slot order)."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    L = _lib.lib()
+    nbytes = int(L.phb_adjoint_record_bytes(C.byref(plan.c)))
+    if record is None:
+        record = torch.empty(nbytes // 8, dtype=torch.float64, device=plan.device)
+    pc = params.c()
+    check(L.phb_adjoint_record(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                               _ptr(plan.ws), plan.ws.numel(), _ptr(record),
+                               record.numel() * record.element_size(), _ptr(plan.status_word),
+                               _stream()), "phb_adjoint_record")
+    return record
+
+
+def rhs_adjoint_stored(plan: Plan, params: Params, pos, lam, U, gbar, record, Ubar=None, xbar=None):
+    """rhs_adjoint starting from a record of adjoint_record (same plan, lists and inputs)."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    _need(gbar, (8, n), "gbar")
+    if Ubar is None:
+        Ubar = torch.empty((8, n), dtype=torch.float64, device=plan.device)
+    if xbar is None:
+        xbar = torch.empty((3, n), dtype=torch.float64, device=plan.device)
+    pc = params.c()
+    check(_lib.lib().phb_rhs_adjoint_stored(
+        C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U), _ptr(gbar), _ptr(plan.ws),
+        plan.ws.numel(), _ptr(record), record.numel() * record.element_size(), _ptr(Ubar),
+        _ptr(xbar), _ptr(plan.status_word), _stream()), "phb_rhs_adjoint_stored")
+    return Ubar, xbar
+
+
 def tensors_of(w, device="cuda"):
     """(pos, lam, U) float64 CUDA tensors of a workloads.Workload."""
     dev = torch.device(device)
@@ -247,3 +284,32 @@ def rhs(w, params: Params | None = None, skin: float = 0.0, device="cuda"):
     st = torch.empty(w.n, dtype=torch.int32, device=plan.device)
     dudt, _ = mhd_rhs(plan, params, pos, lam, U, fit_status=st)
     return dudt, st, plan
+
+
+class StepGraph:
+    """CUDA graph of `steps` predictor-corrector steps (phb_pc_step), each with its
+    neighbour rebuild, captured once and replayed on the current stream.
+
+    The graph holds the addresses of pos, lam, U, the parameter arrays and the
+    plan's workspace and the value of dt: keep those tensors alive and in place,
+    and do not grow the plan (its capacity must already hold the lists; the
+    status word reports FLAG_CAPACITY and FLAG_SKIN after a replay otherwise).
+    """
+
+    def __init__(self, plan: Plan, params: Params, pos, lam, U, dt: float, steps: int = 1):
+        if steps < 1:
+            raise ValueError("steps must be >= 1")
+        self.plan, self.params, self.steps = plan, params, int(steps)
+        self._keep = (pos, lam, U, params.zeta, params.eta, plan.ws)
+        self.graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device=plan.device)
+        side.wait_stream(torch.cuda.current_stream(plan.device))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side):
+                for _ in range(self.steps):
+                    pc_step(plan, params, pos, lam, U, dt)
+        torch.cuda.current_stream(plan.device).wait_stream(side)
+
+    def replay(self):
+        """Advance pos and U by `steps` steps in place (asynchronous)."""
+        self.graph.replay()

@@ -17,8 +17,11 @@
 //             to U_i and x_i kept by the particle.
 // A second kernel gathers every particle's own terms plus the entries that
 // name it through a reverse neighbour list sorted by entry id, so the result
-// does not depend on thread scheduling.  The factorisation is recomputed
-// here (nothing is stored by the forward call).
+// does not depend on thread scheduling.  By default the factorisation is
+// recomputed here (nothing is stored by the forward call); the stored variant
+// records, per particle, the Cholesky factor, its Jacobi scaling and the
+// fitted coefficients once (kRecord) and the adjoint then starts from that
+// record (kStored) instead of re-accumulating the moments and right-hand sides.
 #include "phb_internal.cuh"
 #include "mls_gen.cuh"
 #include "phb_mhd.cuh"
@@ -31,6 +34,11 @@ constexpr int kThreads = 256;
 constexpr int kNFit = 7;                 // fitted fields: U indices 1..7 (V, B, sigma)
 constexpr int kSm = kNM + kNFit * kNB;   // 213 doubles per thread (the 190-entry M overlays it)
 static_assert(kSm >= kNT, "shared region must hold the normal matrix");
+// record of one particle's forward fit, [k][n] layout: factor (190), Jacobi
+// scaling invd (19), coefficients c_f (7 x 19), then 1 = singular / 0 = regular
+constexpr int kRecFac = 0, kRecInvd = kNT, kRecCoef = kNT + kNB, kRecFlag = kRecCoef + kNFit * kNB;
+constexpr int kRecWords = kRecFlag + 1;
+enum AdjMode { kRecompute = 0, kRecord = 1, kStored = 2 };
 
 // Column view of thread-private shared memory ([k][kT] layout, no bank conflicts).
 struct SCol {
@@ -61,6 +69,7 @@ struct AdjArgs {
   double* scr;           // [266][n]: c_f (7 x 19) then bbar_f (7 x 19)
   double* edge;          // [capacity][10]
   double* self;          // [11][n] slot order
+  double* rec;           // [kRecWords][n] slot order (stored variant) or null
   int32_t* status_word;
 };
 
@@ -144,7 +153,8 @@ __device__ void rhs_adjoint_point(const double (&u)[8], const MhdDerivs<double>&
   gb[3 + 0][1] -= Jb[2];
 }
 
-__global__ void __launch_bounds__(kT) k_adjoint(const AdjArgs a) {
+template <int MODE>
+__global__ void __launch_bounds__(kT, 1) k_adjoint(const AdjArgs a) {
   extern __shared__ double sm[];
   const int s = blockIdx.x * kT + threadIdx.x;
   if (s >= a.n) return;
@@ -152,7 +162,8 @@ __global__ void __launch_bounds__(kT) k_adjoint(const AdjArgs a) {
   const SCol M{my};                 // normal matrix / factor (190), later mbar (80) + bbar (133)
   const SCol MB{my};                // mbar [80]
   const int64_t N = a.n;
-  const GCol cf{a.scr + s, N};                    // c_f, f = 0..6: [f * 19 + k]
+  // c_f, f = 0..6: [f * 19 + k] (in the record for the stored variant)
+  const GCol cf{MODE == kRecompute ? a.scr + s : a.rec + kRecCoef * N + s, N};
   const GCol bbar{a.scr + s + 133 * N, N};        // bbar_f
   double len[3], ilen[3];
   for (int c = 0; c < 3; ++c) {
@@ -169,8 +180,6 @@ __global__ void __launch_bounds__(kT) k_adjoint(const AdjArgs a) {
   const int64_t beg = a.off[s];
   const int64_t end = a.off[s + 1] < a.g.capacity ? a.off[s + 1] : a.g.capacity;
   const int src = a.perm[s];
-  double o[8];
-  for (int f = 0; f < 8; ++f) o[f] = a.gbar[f * N + src];
   const double zeta = a.zeta ? a.zeta[src] : 0.0;
   const double eta = a.eta ? a.eta[src] : 0.0;
 
@@ -178,7 +187,13 @@ __global__ void __launch_bounds__(kT) k_adjoint(const AdjArgs a) {
   int cnt = 0;
   double invd[kNB];
   bool singular;
-  {
+  if (MODE == kStored) {
+    singular = a.rec[kRecFlag * N + s] != 0.0;
+    if (!singular) {
+      for (int k = 0; k < kNT; ++k) M[k] = a.rec[(kRecFac + k) * N + s];
+      for (int k = 0; k < kNB; ++k) invd[k] = a.rec[(kRecInvd + k) * N + s];
+    }
+  } else {
     double m[kNM];
 #pragma unroll
     for (int k = 0; k < kNM; ++k) m[k] = 0.0;
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(kT) k_adjoint(const AdjArgs a) {
     singular = cnt < kNB;
     if (!singular) mls_assemble(m, M);
   }
-  if (!singular) {
+  if (MODE != kStored && !singular) {
     const double minpiv = mls_cholesky<double>(M, invd);
     double rmin = 1e300;
     for (int k = 0; k < kNB; ++k) {
@@ -203,6 +218,15 @@ __global__ void __launch_bounds__(kT) k_adjoint(const AdjArgs a) {
       rmin = r < rmin ? r : rmin;
     }
     singular = !(minpiv > 0.0) || !(rmin > 1e-12);
+  }
+  if (MODE == kRecord) {
+    a.rec[kRecFlag * N + s] = singular ? 1.0 : 0.0;
+    if (singular) {
+      raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
+      return;
+    }
+    for (int k = 0; k < kNT; ++k) a.rec[(kRecFac + k) * N + s] = M[k];
+    for (int k = 0; k < kNB; ++k) a.rec[(kRecInvd + k) * N + s] = invd[k];
   }
   double selfu[8], selfx[3] = {0.0, 0.0, 0.0};
   if (singular) {
@@ -214,7 +238,7 @@ __global__ void __launch_bounds__(kT) k_adjoint(const AdjArgs a) {
     return;
   }
   // ---- forward: right-hand sides in two groups, full coefficients c_f
-  for (int grp = 0; grp < 2; ++grp) {
+  for (int grp = 0; grp < (MODE == kStored ? 0 : 2); ++grp) {
     const int nf = grp == 0 ? 4 : 3;  // fields 1..4 (Vx, Vy, Vz, Bx) then 5..7 (By, Bz, sigma)
     double b[4][kNB];
     for (int f = 0; f < 4; ++f)
@@ -239,6 +263,9 @@ __global__ void __launch_bounds__(kT) k_adjoint(const AdjArgs a) {
       for (int k = 0; k < kNB; ++k) cf[fi * kNB + k] = b[f][k];
     }
   }
+  if (MODE == kRecord) return;
+  double o[8];
+  for (int f = 0; f < 8; ++f) o[f] = a.gbar[f * N + src];
   // ---- derivatives, right-hand-side adjoint, cbar -> bbar = M^-1 cbar
   const double il = inv_l, il2 = inv_l * inv_l;
   {
@@ -394,16 +421,20 @@ __global__ void k_adj_gather(int n, const int32_t* __restrict__ perm, const doub
 
 using namespace phb;
 
-extern "C" phb_status phb_rhs_adjoint(const phb_plan* plan, const phb_params* prm, const double* pos,
-                                      const double* lambda, const double* U, const double* gbar,
-                                      void* ws, size_t ws_bytes, double* Ubar, double* xbar,
-                                      int32_t* status_word, phb_stream_t stream) {
+namespace {
+
+phb_status adjoint_impl(int mode, const phb_plan* plan, const phb_params* prm, const double* pos,
+                        const double* lambda, const double* U, const double* gbar, void* ws,
+                        size_t ws_bytes, double* rec, size_t rec_bytes, double* Ubar, double* xbar,
+                        int32_t* status_word, cudaStream_t st) {
   phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_ADJ_SELF] + 11 * 8 * plan->n : 0);
   if (s != PHB_OK) return s;
-  if (!prm || !pos || !lambda || !U || !gbar || !Ubar || !xbar) return PHB_ERR_INVALID_ARG;
+  if (!prm || !pos || !lambda || !U) return PHB_ERR_INVALID_ARG;
+  if (mode != kRecord && (!gbar || !Ubar || !xbar)) return PHB_ERR_INVALID_ARG;
+  if (mode != kRecompute && (!rec || rec_bytes < size_t(kRecWords) * 8 * size_t(plan->n)))
+    return PHB_ERR_INVALID_ARG;
   if (prm->weight_kind != 0 && prm->weight_kind != 1) return PHB_ERR_INVALID_ARG;
   if (!(prm->gamma > 1.0)) return PHB_ERR_INVALID_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const Grid g = make_grid(plan);
   const int n = g.n;
   cudaError_t e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st);
@@ -425,10 +456,25 @@ extern "C" phb_status phb_rhs_adjoint(const phb_plan* plan, const phb_params* pr
   a.scr = region<double>(plan, ws, R_ADJ_SCR);
   a.edge = region<double>(plan, ws, R_ADJ_EDGE);
   a.self = region<double>(plan, ws, R_ADJ_SELF);
+  a.rec = rec;
   a.status_word = status_word;
   const size_t smem = size_t(kSm) * kT * sizeof(double);
-  cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  k_adjoint<<<static_cast<unsigned>((n + kT - 1) / kT), kT, smem, st>>>(a);
+  const unsigned grid = static_cast<unsigned>((n + kT - 1) / kT);
+  if (mode == kRecompute) {
+    cudaFuncSetAttribute(k_adjoint<kRecompute>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    k_adjoint<kRecompute><<<grid, kT, smem, st>>>(a);
+  } else if (mode == kRecord) {
+    cudaFuncSetAttribute(k_adjoint<kRecord>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    k_adjoint<kRecord><<<grid, kT, smem, st>>>(a);
+    note_launch();
+    return launch_status(cudaSuccess);
+  } else {
+    cudaFuncSetAttribute(k_adjoint<kStored>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    k_adjoint<kStored><<<grid, kT, smem, st>>>(a);
+  }
   note_launch();
   int32_t* rcnt = region<int32_t>(plan, ws, R_ADJ_RCNT);
   int64_t* roff = region<int64_t>(plan, ws, R_ADJ_ROFF);
@@ -449,4 +495,39 @@ extern "C" phb_status phb_rhs_adjoint(const phb_plan* plan, const phb_params* pr
   k_adj_gather<<<nb, kThreads, 0, st>>>(n, a.perm, a.self, a.edge, roff, ridx, Ubar, xbar);
   note_launch();
   return launch_status(cudaSuccess);
+}
+
+}  // namespace
+
+extern "C" phb_status phb_rhs_adjoint(const phb_plan* plan, const phb_params* prm, const double* pos,
+                                      const double* lambda, const double* U, const double* gbar,
+                                      void* ws, size_t ws_bytes, double* Ubar, double* xbar,
+                                      int32_t* status_word, phb_stream_t stream) {
+  return adjoint_impl(kRecompute, plan, prm, pos, lambda, U, gbar, ws, ws_bytes, nullptr, 0, Ubar,
+                      xbar, status_word, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t phb_adjoint_record_bytes(const phb_plan* plan) {
+  return plan && plan->n > 0 ? size_t(kRecWords) * 8 * size_t(plan->n) : 0;
+}
+
+extern "C" phb_status phb_adjoint_record(const phb_plan* plan, const phb_params* prm,
+                                         const double* pos, const double* lambda, const double* U,
+                                         void* ws, size_t ws_bytes, double* record,
+                                         size_t record_bytes, int32_t* status_word,
+                                         phb_stream_t stream) {
+  return adjoint_impl(kRecord, plan, prm, pos, lambda, U, nullptr, ws, ws_bytes, record,
+                      record_bytes, nullptr, nullptr, status_word,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" phb_status phb_rhs_adjoint_stored(const phb_plan* plan, const phb_params* prm,
+                                             const double* pos, const double* lambda,
+                                             const double* U, const double* gbar, void* ws,
+                                             size_t ws_bytes, const double* record,
+                                             size_t record_bytes, double* Ubar, double* xbar,
+                                             int32_t* status_word, phb_stream_t stream) {
+  return adjoint_impl(kStored, plan, prm, pos, lambda, U, gbar, ws, ws_bytes,
+                      const_cast<double*>(record), record_bytes, Ubar, xbar, status_word,
+                      reinterpret_cast<cudaStream_t>(stream));
 }

@@ -50,6 +50,28 @@ extern "C" int phb_trace_start(int32_t capacity) {
   return 0;
 }
 
+extern "C" int phb_trace_read(float* ms, int32_t* kernel_ids, int32_t capacity) {
+  using phb::g_trace;
+  if (!g_trace.armed) return -1;
+  const int n = g_trace.used;
+  // a failed event query leaves a non-sticky error behind: consume it so that
+  // the next launch check does not report it
+  if (n > 0 && cudaEventSynchronize(g_trace.e[n - 1]) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  for (int k = 0; k < n && k < capacity; ++k) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, g_trace.b[k], g_trace.e[k]) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    if (ms) ms[k] = t;
+    if (kernel_ids) kernel_ids[k] = g_trace.id[k];
+  }
+  return n < capacity ? n : capacity;
+}
+
 extern "C" int phb_trace_stop(float* ms, int32_t* kernel_ids, int32_t capacity) {
   using phb::g_trace;
   if (!g_trace.armed) return -1;
@@ -72,6 +94,7 @@ extern "C" int phb_trace_stop(float* ms, int32_t* kernel_ids, int32_t capacity) 
   g_trace.b.clear();
   g_trace.e.clear();
   g_trace.used = 0;
+  if (rc < 0) cudaGetLastError();
   return rc < 0 ? -1 : (n < capacity ? n : capacity);
 }
 

@@ -178,38 +178,69 @@ struct TileArgs {
   const int2* clin;
   const uint16_t* lidx;
   int32_t* fallback_count;
+  const int32_t* order;   // tile order (persistent schedule)
+  int32_t* queue_head;    // persistent tile-queue counter (zeroed before the launch)
+  int32_t ntiles;
 };
 
+// Shared memory of one CTA besides the dynamic park/staging region.
+template <int T>
+struct FitShared {
+  TileShared ts;
+  unsigned bits[kBoxWords];
+  int wpre[kBoxWords];
+  int base[kMarkCap + 1];
+  int cstart[kMarkCap];
+  int warp_tmp[T / 32 + 1];
+  int cnt[T];     // list length of each tile particle
+  int map[T];     // thread -> tile particle, longest lists first
+  int tile;       // persistent schedule: tile taken from the queue
+};
+
+// One tile: stage its neighbourhood, accumulate, solve, write outputs.  All
+// T threads call it (it contains block barriers).  Threads are assigned to
+// the tile's particles in descending list length so that the lanes of a warp
+// run loops of similar length.
 template <FitMode MODE, int T>
-__global__ void __launch_bounds__(T, 256 / T) k_fit_mixed(const FitArgs a, const Per32 P, const TileArgs ta) {
+__device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const TileArgs& ta,
+                                         int tile, float* park, float4* stage, FitShared<T>& sh) {
   using G = Groups<MODE>;
-  // shared memory: [park A: NA*19 slots x T][staged records: stage_cap x 3 float4]
-  // after the accumulation the whole region holds the NF*19 parked slots.
-  extern __shared__ float4 smem4[];
-  float* park = reinterpret_cast<float*>(smem4);
-  float4* stage = smem4 + (G::NA * kNB * T) / 4;
-  __shared__ TileShared ts;
-  __shared__ unsigned bits[kBoxWords];
-  __shared__ int wpre[kBoxWords];
-  __shared__ int base[kMarkCap + 1];
-  __shared__ int cstart[kMarkCap];
-  __shared__ int warp_tmp[T / 32 + 1];
-  const TileArrays tarr{bits, wpre, base, cstart, warp_tmp};
   const int n = a.n;
-  const int s0 = blockIdx.x * T;
+  const int s0 = tile * T;
   const int cnt_tile = min(T, n - s0);
   const int tid = threadIdx.x;
-  const bool active = tid < cnt_tile;
-  const int s = s0 + tid;
   const float4* rec = reinterpret_cast<const float4*>(a.rec);
+  const TileArrays tarr{sh.bits, sh.wpre, sh.base, sh.cstart, sh.warp_tmp};
 
-  tile_plan<T>(a.g, s0, cnt_tile, ta.cellc, a.slam, ta.clin, ts, tarr);
-  const bool fb = ts.fallback != 0;
+  // thread -> particle map, descending list length (ties: slot order)
+  {
+    int len = -1;
+    if (tid < cnt_tile) {
+      const int64_t e1 = a.off[s0 + tid + 1] < a.g.capacity ? a.off[s0 + tid + 1] : a.g.capacity;
+      const int64_t e0 = a.off[s0 + tid] < a.g.capacity ? a.off[s0 + tid] : a.g.capacity;
+      len = static_cast<int>(e1 - e0);
+    }
+    sh.cnt[tid] = len;
+    __syncthreads();
+    int rank = 0;
+    for (int j = 0; j < T; ++j) {
+      const int c = sh.cnt[j];
+      rank += (c > len || (c == len && j < tid)) ? 1 : 0;
+    }
+    sh.map[rank] = tid;
+    __syncthreads();
+  }
+  const int mine = sh.map[tid];
+  const bool active = mine < cnt_tile;
+  const int s = s0 + mine;
+
+  tile_plan<T>(a.g, s0, cnt_tile, ta.cellc, a.slam, ta.clin, sh.ts, tarr);
+  const bool fb = sh.ts.fallback != 0;
   if (!fb) {
     const float4 rh = rec[6 * s0], rl = rec[6 * s0 + 1];
     const float4 fh = rec[6 * s0 + 2], fl = rec[6 * s0 + 3], gh = rec[6 * s0 + 4], gl = rec[6 * s0 + 5];
-    for (int j = tid; j < ts.ncells; j += T) {
-      const int l0 = base[j], c = base[j + 1] - l0, t0 = cstart[j];
+    for (int j = tid; j < sh.ts.ncells; j += T) {
+      const int l0 = sh.base[j], c = sh.base[j + 1] - l0, t0 = sh.cstart[j];
       for (int p = 0; p < c; ++p) {
         const float4* r = rec + 6 * (t0 + p);
         const float4 p0 = r[0], p1 = r[1], f0 = r[2], f1 = r[3], g0 = r[4], g1 = r[5];
@@ -251,8 +282,8 @@ __global__ void __launch_bounds__(T, 256 / T) k_fit_mixed(const FitArgs a, const
       StagedSrc src;
       src.stage = stage;
       src.lidx = ta.lidx;
-      const int js = marked_index(tarr, box_index(a.g, ts, ta.cellc[s]));
-      const int ls = base[js] + (s - cstart[js]);
+      const int js = marked_index(tarr, box_index(a.g, sh.ts, ta.cellc[s]));
+      const int ls = sh.base[js] + (s - sh.cstart[js]);
       src.me0 = stage[3 * ls];
       src.me1 = stage[3 * ls + 1];
       src.me2 = stage[3 * ls + 2];
@@ -264,92 +295,130 @@ __global__ void __launch_bounds__(T, 256 / T) k_fit_mixed(const FitArgs a, const
     }
   }
   __syncthreads();  // the staged records are dead from here on
-  if (!active) return;
+  if (active) {
 #pragma unroll
-  for (int f = 0; f < 4; ++f)
+    for (int f = 0; f < 4; ++f)
 #pragma unroll
-    for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = bB[f][k];
+      for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = bB[f][k];
 
-  const int dst = a.perm_out ? a.perm_out[s] : s;
-  const bool singular = cnt < kNB;
-  if (!singular) {
-    float M[kNT], invd[kNB];
-    mls_assemble(m, M);
-    const float minpiv = mls_cholesky<float>(M, invd);
-    // Jacobi-scaled pivots L~_kk^2 = L_kk^2 / M_kk = 1 / (invd_k^2 M_kk)
-    float rmin = 3.4e38f, rmax = 0.f;
+    const int dst = a.perm_out ? a.perm_out[s] : s;
+    bool singular = cnt < kNB;
+    bool routed = false;
+    if (!singular) {
+      float M[kNT], invd[kNB];
+      mls_assemble(m, M);
+      const float minpiv = mls_cholesky<float>(M, invd);
+      // Jacobi-scaled pivots L~_kk^2 = L_kk^2 / M_kk = 1 / (invd_k^2 M_kk)
+      float rmin = 3.4e38f, rmax = 0.f;
 #pragma unroll
-    for (int k = 0; k < kNB; ++k) {
-      const float r = 1.f / (invd[k] * invd[k] * M[k * (k + 1) / 2 + k]);
-      rmin = fminf(rmin, r);
-      rmax = fmaxf(rmax, r);
-    }
-    if (!(minpiv > 0.f) || !(rmax <= a.cond_threshold * rmin)) {
-      const int q = atomicAdd(a.queue_len, 1);
-      a.queue[q] = s;
-      return;
-    }
-    const float il = inv_l, il2 = inv_l * inv_l;
+      for (int k = 0; k < kNB; ++k) {
+        const float r = 1.f / (invd[k] * invd[k] * M[k * (k + 1) / 2 + k]);
+        rmin = fminf(rmin, r);
+        rmax = fmaxf(rmax, r);
+      }
+      if (!(minpiv > 0.f) || !(rmax <= a.cond_threshold * rmin)) {
+        const int q = atomicAdd(a.queue_len, 1);
+        a.queue[q] = s;
+        routed = true;
+      } else {
+        const float il = inv_l, il2 = inv_l * inv_l;
 #pragma unroll 1
-    for (int k = 0; k < G::NF; ++k) {
-      float b[kNB];
+        for (int k = 0; k < G::NF; ++k) {
+          float b[kNB];
 #pragma unroll
-      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
-      mls_forward(M, invd, b);
-      mls_back9(M, invd, b);
-      float* d = park + (k * kNB) * T + tid;
-      d[0 * T] = b[kLin0] * il;
-      d[1 * T] = b[kLin0 + 1] * il;
-      d[2 * T] = b[kLin0 + 2] * il;
-      d[3 * T] = 2.f * b[kQuad0] * il2;
-      d[4 * T] = b[kQuad0 + 1] * il2;
-      d[5 * T] = b[kQuad0 + 2] * il2;
-      d[6 * T] = 2.f * b[kQuad0 + 3] * il2;
-      d[7 * T] = b[kQuad0 + 4] * il2;
-      d[8 * T] = 2.f * b[kQuad0 + 5] * il2;
-    }
-  } else {
+          for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
+          mls_forward(M, invd, b);
+          mls_back9(M, invd, b);
+          float* d = park + (k * kNB) * T + tid;
+          d[0 * T] = b[kLin0] * il;
+          d[1 * T] = b[kLin0 + 1] * il;
+          d[2 * T] = b[kLin0 + 2] * il;
+          d[3 * T] = 2.f * b[kQuad0] * il2;
+          d[4 * T] = b[kQuad0 + 1] * il2;
+          d[5 * T] = b[kQuad0 + 2] * il2;
+          d[6 * T] = 2.f * b[kQuad0 + 3] * il2;
+          d[7 * T] = b[kQuad0 + 4] * il2;
+          d[8 * T] = 2.f * b[kQuad0 + 5] * il2;
+        }
+      }
+    } else {
 #pragma unroll 1
-    for (int k = 0; k < G::NF; ++k)
-      for (int j = 0; j < 9; ++j) park[(k * kNB + j) * T + tid] = 0.f;
+      for (int k = 0; k < G::NF; ++k)
+        for (int j = 0; j < 9; ++j) park[(k * kNB + j) * T + tid] = 0.f;
+    }
+    if (!routed) {
+      if (a.fit_status) a.fit_status[dst] = singular ? 1 : 0;
+      if (singular) raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
+      if (MODE == FitMode::kDerivs) {
+#pragma unroll 1
+        for (int k = 0; k < G::NF; ++k) {
+          const int f = G::field(k);
+          const float* d = park + (k * kNB) * T + tid;
+          for (int c = 0; c < 3; ++c) a.grad[(f * 3 + c) * static_cast<int64_t>(n) + dst] = d[c * T];
+          if (a.hess)
+            for (int c = 0; c < 6; ++c)
+              a.hess[(f * 6 + c) * static_cast<int64_t>(n) + dst] = d[(3 + c) * T];
+        }
+      } else {
+        MhdDerivs<float> D;
+        mhd_zero(D);
+#pragma unroll
+        for (int k = 0; k < G::NF; ++k) {
+          const float* d = park + (k * kNB) * T + tid;
+          const float g[3] = {d[0], d[T], d[2 * T]};
+          const float h[6] = {d[3 * T], d[4 * T], d[5 * T], d[6 * T], d[7 * T], d[8 * T]};
+          mhd_collect(D, G::field(k), g, h);
+        }
+        const float4 o2 = rec[6 * s + 2], o3 = rec[6 * s + 3], o4 = rec[6 * s + 4], o5 = rec[6 * s + 5];
+        const float u[8] = {o2.x + o3.x, o2.z + o3.z, o2.w + o3.w, o4.x + o5.x,
+                            o4.y + o5.y, o4.z + o5.z, o4.w + o5.w, o2.y + o3.y};
+        const int src = a.perm_in ? a.perm_in[s] : s;
+        const float zeta = a.zeta ? static_cast<float>(a.zeta[src]) : 0.f;
+        const float eta = a.eta ? static_cast<float>(a.eta[src]) : 0.f;
+        float out[8];
+        mhd_rhs(u, D, static_cast<float>(a.gamma), zeta, eta, out);
+        bool finite = true;
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+          finite &= isfinite(out[f]);
+          a.dudt[f * static_cast<int64_t>(n) + dst] = out[f];
+        }
+        if (!finite) raise_flag(a.status_word, PHB_FLAG_NONFINITE);
+      }
+    }
   }
-  if (a.fit_status) a.fit_status[dst] = singular ? 1 : 0;
-  if (singular) raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
-  if (MODE == FitMode::kDerivs) {
-#pragma unroll 1
-    for (int k = 0; k < G::NF; ++k) {
-      const int f = G::field(k);
-      const float* d = park + (k * kNB) * T + tid;
-      for (int c = 0; c < 3; ++c) a.grad[(f * 3 + c) * static_cast<int64_t>(n) + dst] = d[c * T];
-      if (a.hess)
-        for (int c = 0; c < 6; ++c)
-          a.hess[(f * 6 + c) * static_cast<int64_t>(n) + dst] = d[(3 + c) * T];
-    }
-  } else {
-    MhdDerivs<float> D;
-    mhd_zero(D);
-#pragma unroll
-    for (int k = 0; k < G::NF; ++k) {
-      const float* d = park + (k * kNB) * T + tid;
-      const float g[3] = {d[0], d[T], d[2 * T]};
-      const float h[6] = {d[3 * T], d[4 * T], d[5 * T], d[6 * T], d[7 * T], d[8 * T]};
-      mhd_collect(D, G::field(k), g, h);
-    }
-    const float4 o2 = rec[6 * s + 2], o3 = rec[6 * s + 3], o4 = rec[6 * s + 4], o5 = rec[6 * s + 5];
-    const float u[8] = {o2.x + o3.x, o2.z + o3.z, o2.w + o3.w, o4.x + o5.x,
-                        o4.y + o5.y, o4.z + o5.z, o4.w + o5.w, o2.y + o3.y};
-    const int src = a.perm_in ? a.perm_in[s] : s;
-    const float zeta = a.zeta ? static_cast<float>(a.zeta[src]) : 0.f;
-    const float eta = a.eta ? static_cast<float>(a.eta[src]) : 0.f;
-    float out[8];
-    mhd_rhs(u, D, static_cast<float>(a.gamma), zeta, eta, out);
-    bool finite = true;
-#pragma unroll
-    for (int f = 0; f < 8; ++f) {
-      finite &= isfinite(out[f]);
-      a.dudt[f * static_cast<int64_t>(n) + dst] = out[f];
-    }
-    if (!finite) raise_flag(a.status_word, PHB_FLAG_NONFINITE);
+  __syncthreads();  // the park region is reused by the next tile (persistent schedule)
+}
+
+template <FitMode MODE, int T>
+__global__ void __launch_bounds__(T, 256 / T) k_fit_mixed(const FitArgs a, const Per32 P, const TileArgs ta) {
+  using G = Groups<MODE>;
+  // dynamic shared memory: [park A: NA*19 slots x T][staged records: stage_cap x 3 float4];
+  // after the accumulation the whole region holds the NF*19 parked slots.
+  extern __shared__ float4 smem4[];
+  __shared__ FitShared<T> sh;
+  float* park = reinterpret_cast<float*>(smem4);
+  float4* stage = smem4 + (G::NA * kNB * T) / 4;
+  fit_tile<MODE, T>(a, P, ta, blockIdx.x, park, stage, sh);
+}
+
+// Persistent CTAs: take tiles from the cost-ordered queue until it is empty
+// (a wait-free atomic counter; no CTA ever waits on another).
+template <FitMode MODE, int T>
+__global__ void __launch_bounds__(T, 256 / T) k_fit_mixed_persistent(const FitArgs a, const Per32 P,
+                                                                     const TileArgs ta) {
+  using G = Groups<MODE>;
+  extern __shared__ float4 smem4[];
+  __shared__ FitShared<T> sh;
+  float* park = reinterpret_cast<float*>(smem4);
+  float4* stage = smem4 + (G::NA * kNB * T) / 4;
+  for (;;) {
+    if (threadIdx.x == 0) sh.tile = atomicAdd(ta.queue_head, 1);
+    __syncthreads();
+    const int q = sh.tile;
+    __syncthreads();
+    if (q >= ta.ntiles) break;
+    fit_tile<MODE, T>(a, P, ta, ta.order[q], park, stage, sh);
   }
 }
 
@@ -372,22 +441,40 @@ cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, cudaS
   const size_t staged = size_t(a.g.stage_cap) * 3 * sizeof(float4);
   const size_t park_all = size_t(G::NF) * kNB * T * sizeof(float);
   const size_t smem = park_a + staged > park_all ? park_a + staged : park_all;
-  cudaFuncSetAttribute(k_fit_mixed<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(smem));
   const unsigned tiles = static_cast<unsigned>((a.n + T - 1) / T);
-  const int tr = trace_begin(1, st);
-  k_fit_mixed<MODE, T><<<tiles, T, smem, st>>>(a, P, ta);
-  note_launch();
-  trace_end(tr, st);
+  cudaError_t e;
+  if (a.g.schedule == 1) {
+    cudaFuncSetAttribute(k_fit_mixed_persistent<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit_mixed_persistent<MODE, T>, T, smem);
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = static_cast<unsigned>(num_sms() * per_sm);
+    if (grid > tiles) grid = tiles;
+    if ((e = cudaMemsetAsync(ta.queue_head, 0, sizeof(int32_t), st))) return e;
+    const int tr = trace_begin(1, st);
+    k_fit_mixed_persistent<MODE, T><<<grid, T, smem, st>>>(a, P, ta);
+    note_launch();
+    trace_end(tr, st);
+  } else {
+    cudaFuncSetAttribute(k_fit_mixed<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    const int tr = trace_begin(1, st);
+    k_fit_mixed<MODE, T><<<tiles, T, smem, st>>>(a, P, ta);
+    note_launch();
+    trace_end(tr, st);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int32_t* cellc, const int2* clin,
-                             const uint16_t* lidx, int32_t* fallback_count, cudaStream_t st) {
+                             const uint16_t* lidx, int32_t* fallback_count, const int32_t* order,
+                             int32_t* queue_head, cudaStream_t st) {
   const Per32 P = make_per32(a.g);
-  const TileArgs ta{cellc, clin, lidx, fallback_count};
+  const TileArgs ta{cellc, clin, lidx, fallback_count, order, queue_head,
+                    static_cast<int32_t>((a.n + a.g.tile - 1) / a.g.tile)};
   if (mode == FitMode::kDerivs)
     return a.g.tile == 64 ? launch_t<FitMode::kDerivs, 64>(a, P, ta, st)
                           : launch_t<FitMode::kDerivs, 128>(a, P, ta, st);

@@ -17,7 +17,8 @@ constexpr int kEdgeAdj = 10;  // doubles per neighbour edge in the adjoint (7 fi
 // regions share storage (never used at the same time).
 enum Region {
   R_MISC = 0,    // int32 [64]: 0 = FP64 route-queue length, 1 = tiles that fell back to
-                 //   global gathers in the last neighbour build
+                 //   global gathers in the last neighbour build, 2 = same in the last
+                 //   fused fit, 3 = persistent tile-queue counter
   R_KEYS,        // int32 [n]   cell key of each caller particle
   R_PERM,        // int32 [n]   slot -> caller index
   R_INV,         // int32 [n]   caller index -> slot
@@ -35,6 +36,7 @@ enum Region {
   R_LIDX,        // uint16 [capacity] neighbour index inside the tile's staged neighbourhood
   R_CELLC,       // int32 [n] packed cell coordinates of each slot (10 bits per axis)
   R_CLIN,        // int2 [cells] (first slot, count) per linear cell index (x-major)
+  R_TORDER,      // int32 [ntiles] tiles in descending cost class (persistent schedule)
   R_QUEUE,       // int32 [n]    slots routed to FP64
   R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
@@ -67,6 +69,7 @@ struct Grid {
   int32_t hbits;      // Hilbert order of the brick curve
   int32_t tile;       // particles per tile
   int32_t stage_cap;  // staged records per tile
+  int32_t schedule;   // 0: grid of tiles, 1: persistent queue
   int32_t n;
   double rf_factor, skin;
   double lambda_min, lambda_max;
@@ -251,7 +254,8 @@ struct FitArgs {
 };
 
 cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int32_t* cellc, const int2* clin,
-                             const uint16_t* lidx, int32_t* fallback_count, cudaStream_t st);
+                             const uint16_t* lidx, int32_t* fallback_count, const int32_t* order,
+                             int32_t* queue_head, cudaStream_t st);
 // FP64 fused fit over all slots (list == null) or over list[0 .. *list_len).
 cudaError_t launch_fit_fp64(const FitArgs& a, FitMode mode, const int32_t* list,
                             const int32_t* list_len, cudaStream_t st);

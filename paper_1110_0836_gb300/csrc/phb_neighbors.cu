@@ -259,6 +259,39 @@ __global__ void __launch_bounds__(T) k_localize(Grid g, const int2* __restrict__
   }
 }
 
+// Tile order for the persistent fused fit: tiles grouped by cost class
+// floor(log2(list entries + 1)), most expensive class first (longest
+// processing time first keeps the tail of the launch short).  One CTA.
+__global__ void __launch_bounds__(1024) k_tile_order(int n, int T, int ntiles, int64_t cap,
+                                                     const int64_t* __restrict__ off,
+                                                     int32_t* __restrict__ order) {
+  __shared__ int hist[65], cursor[65];
+  const int tid = threadIdx.x;
+  if (tid < 65) hist[tid] = 0;
+  __syncthreads();
+  for (int t = tid; t < ntiles; t += blockDim.x) {
+    const int s0 = t * T, s1 = min(s0 + T, n);
+    const int64_t a = off[s0] < cap ? off[s0] : cap, b = off[s1] < cap ? off[s1] : cap;
+    const int cls = 64 - __clzll(static_cast<unsigned long long>(b - a + 1));
+    atomicAdd(&hist[cls], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int c = 64; c >= 0; --c) {
+      cursor[c] = acc;
+      acc += hist[c];
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < ntiles; t += blockDim.x) {
+    const int s0 = t * T, s1 = min(s0 + T, n);
+    const int64_t a = off[s0] < cap ? off[s0] : cap, b = off[s1] < cap ? off[s1] : cap;
+    const int cls = 64 - __clzll(static_cast<unsigned long long>(b - a + 1));
+    order[atomicAdd(&cursor[cls], 1)] = t;
+  }
+}
+
 // -------- export in caller numbering
 __global__ void k_user_counts(int n, const int32_t* __restrict__ inv, const int64_t* __restrict__ off,
                               int32_t* __restrict__ ucnt) {
@@ -339,6 +372,9 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
     k_localize<128><<<tiles, 128, 0, st>>>(g, clin, cellc, slam, off, idx, lidx, misc + 1);
   else
     k_localize<64><<<tiles, 64, 0, st>>>(g, clin, cellc, slam, off, idx, lidx, misc + 1);
+  note_launch();
+  k_tile_order<<<1, 1024, 0, st>>>(n, p->tile, p->ntiles, p->nbr_capacity, off,
+                                   region<int32_t>(p, ws, R_TORDER));
   note_launch();
   return cudaGetLastError();
 }

@@ -31,6 +31,7 @@ Grid make_grid(const phb_plan* p) {
   g.hbits = p->hilbert_bits;
   g.tile = p->tile;
   g.stage_cap = p->stage_cap;
+  g.schedule = p->schedule;
   g.n = static_cast<int32_t>(p->n);
   g.rf_factor = p->rf_factor;
   g.skin = p->skin;
@@ -217,6 +218,7 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   if (p->stage_cap == 0) p->stage_cap = p->tile == 128 ? 1500 : 768;
   if (p->stage_cap < 64 || p->stage_cap > 2048) return PHB_ERR_INVALID_ARG;
   p->ntiles = static_cast<int32_t>((p->n + p->tile - 1) / p->tile);
+  if (p->schedule != 0 && p->schedule != 1) return PHB_ERR_INVALID_ARG;
   // FP32 screen: bound of |d32 - d| per component is 2^-24 (2X + 3L); two
   // components' worth of safety on top, times sqrt(3) for the norm.
   p->screen_margin = 8.0 * std::sqrt(3.0) * std::ldexp(1.0, -24) * (2.0 * xmax + 3.0 * lmax);
@@ -241,6 +243,7 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   sz[R_LIDX] = cap * 2;
   sz[R_CELLC] = n * 4;
   sz[R_CLIN] = size_t(p->ncell[0]) * p->ncell[1] * p->ncell[2] * 8;
+  sz[R_TORDER] = size_t(p->ntiles) * 4;
   sz[R_QUEUE] = (n + 64) * 4;  // also the export's n+1 counts
   size_t off = 0;
   for (int r = R_MISC; r <= R_QUEUE; ++r) {

@@ -63,6 +63,29 @@ def test_plan_init_valid(L):
     assert p.nkeys == 64 * p.nbrick[0] * p.nbrick[1] * p.nbrick[2]
     offs = list(p.ws_off)[:10]
     assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
+    # the shared prefix ends where the predictor-corrector regions begin
+    from paper_1110_0836_gb300 import _lib
+    end = p.ws_off[_lib.WS_END_COMMON]
+    assert end > offs[-1] and end == p.ws_off[20]  # first predictor-corrector region
+    # adjoint regions: edge contributions (10 doubles per list entry) first, the
+    # per-particle self terms (11 doubles) last, ending the workspace
+    assert p.ws_off[_lib.WS_ADJ_SELF] - p.ws_off[_lib.WS_ADJ_EDGE] >= 10 * 8 * p.nbr_capacity
+    assert p.ws_off[_lib.WS_ADJ_SELF] + 11 * 8 * p.n <= p.ws_bytes
+
+
+@pytest.mark.parametrize("tile,schedule", [(64, 0), (128, 1)])
+def test_plan_init_tile_and_schedule(L, tile, schedule):
+    p = _plan()
+    p.tile, p.schedule = tile, schedule
+    assert L.phb_plan_init(C.byref(p)) == 0
+    assert p.tile == tile and p.schedule == schedule and p.ntiles == -(-p.n // tile)
+
+
+@pytest.mark.parametrize("field,val", [("tile", 96), ("schedule", 2)])
+def test_plan_init_rejects_launch_shape(L, field, val):
+    p = _plan()
+    setattr(p, field, val)
+    assert L.phb_plan_init(C.byref(p)) == 1
 
 
 @pytest.mark.parametrize("kw", [dict(n=0), dict(lmin=-1.0), dict(lmin=0.2, lmax=0.1),

@@ -107,3 +107,38 @@ def test_deterministic():
     a1 = phb.rhs_adjoint(plan, prm, pos, lam, U, g)
     a2 = phb.rhs_adjoint(plan, prm, pos, lam, U, g)
     assert torch.equal(a1[0], a2[0]) and torch.equal(a1[1], a2[1])
+
+
+@pytest.mark.parametrize("open_box", [False, True])
+def test_stored_factorisations_match_recompute(open_box):
+    """The stored-factorisation adjoint (record once, then adjoint from the
+    record) gives bit-identical gradients to the recomputing adjoint, including
+    particles whose fit is singular (open-box corners)."""
+    phb = need_gpu()
+    from paper_1110_0836_gb300 import _lib
+    w = workloads.random_modes(10, seed=45, amp=0.05)
+    if open_box:
+        w.periodic[:] = 0
+    plan, pos, lam, U, prm = setup(phb, w)
+    g = torch.tensor(np.random.default_rng(2).standard_normal((8, w.n)), device="cuda")
+    Ub, xb = phb.rhs_adjoint(plan, prm, pos, lam, U, g)
+    rec = phb.adjoint_record(plan, prm, pos, lam, U)
+    assert rec.numel() == 343 * w.n
+    Ub2, xb2 = phb.rhs_adjoint_stored(plan, prm, pos, lam, U, g, rec)
+    torch.cuda.synchronize()
+    assert torch.equal(Ub, Ub2) and torch.equal(xb, xb2)
+    assert bool(plan.read_status() & _lib.FLAG_FIT_SINGULAR) == open_box
+    # the autograd path with stored factors
+    pos_t = pos.clone().requires_grad_(True)
+    U_t = U.clone().requires_grad_(True)
+    (phb.rhs_autograd(pos_t, U_t, lam, plan, prm, store_factors=True) * g).sum().backward()
+    assert torch.equal(U_t.grad, Ub) and torch.equal(pos_t.grad, xb)
+
+
+def test_stored_record_too_small_is_rejected():
+    phb = need_gpu()
+    w = workloads.random_modes(8, seed=46)
+    plan, pos, lam, U, prm = setup(phb, w)
+    rec = torch.empty(343 * w.n - 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(phb.PhbError):
+        phb.adjoint_record(plan, prm, pos, lam, U, record=rec)

@@ -53,3 +53,47 @@ def test_skin_violation_is_flagged():
     w.U[1] += 1.0
     pos, U, plan = run_pc(phb, w, 0.01, "fp64", skin=0.005)
     assert plan.read_status() & _lib.FLAG_SKIN
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_step_graph_matches_eager_steps(schedule):
+    """Two steps replayed from a captured CUDA graph give bit-identical states to
+    two eagerly launched steps (same kernels, no order-dependent sums)."""
+    phb = need_gpu()
+    w = workloads.random_modes(12, seed=23, amp=0.05)
+    dt, skin = 0.002, 0.02
+    prm = phb.Params(gamma=w.gamma)
+    ref = phb.Plan.for_workload(w, skin=skin, schedule=schedule)
+    pos_e, lam, U_e = phb.tensors_of(w)
+    phb.build_neighbors(ref, pos_e, lam)
+    for _ in range(2):
+        phb.pc_step(ref, prm, pos_e, lam, U_e, dt)
+    plan = phb.Plan.for_workload(w, skin=skin, schedule=schedule)
+    pos_g, _, U_g = phb.tensors_of(w)
+    phb.build_neighbors(plan, pos_g, lam)
+    g = phb.StepGraph(plan, prm, pos_g, lam, U_g, dt, steps=2)
+    g.replay()
+    torch.cuda.synchronize()
+    assert ref.read_status() == 0 and plan.read_status() == 0
+    assert torch.equal(pos_g, pos_e) and torch.equal(U_g, U_e)
+    # a second replay continues from the advanced state
+    pos0, U0 = pos_g.clone(), U_g.clone()
+    g.replay()
+    for _ in range(2):
+        phb.pc_step(ref, prm, pos_e, lam, U_e, dt)
+    torch.cuda.synchronize()
+    assert not torch.equal(pos_g, pos0)
+    assert torch.equal(pos_g, pos_e) and torch.equal(U_g, U_e)
+
+
+def test_autotune_returns_a_timed_candidate(tmp_path, monkeypatch):
+    phb = need_gpu()
+    from paper_1110_0836_gb300 import tune
+    monkeypatch.setenv("PHB_TUNE_CACHE", str(tmp_path / "tune.json"))
+    w = workloads.shock_tube(20000, seed=3)
+    cands = [dict(tile=128, schedule=0, cell_frac=0.5), dict(tile=64, schedule=1, cell_frac=0.5)]
+    res = tune.autotune(w, skin=0.0, reps=2, candidates=cands)
+    assert {k: res[k] for k in ("tile", "schedule", "cell_frac")} in cands
+    assert all(t["ms"] is not None and t["ms"] > 0 for t in res["table"])
+    again = tune.autotune(w, skin=0.0, reps=2, candidates=cands)
+    assert again == res   # served from the cache file
