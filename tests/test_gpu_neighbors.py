@@ -131,3 +131,26 @@ def test_tiled_and_fallback_search_agree(tile, stage_cap):
     if stage_cap == 64:
         st = plan.stats()
         assert st["build_fallback_tiles"] == st["tiles"]
+
+
+@pytest.mark.parametrize("name,nq,skin", [("C3", 400, 0.0), ("C5", 200, 0.0), ("C5", 100, 1e-3)])
+def test_full_size_density_sampled_sets(name, nq, skin):
+    """1,048,576-particle shock tube and 8,000,000-particle shear layer (lambda
+    varying 2x, Poisson placement): sampled lists bit-exact, in the launch
+    configuration the benchmark times."""
+    phb = need_gpu()
+    w = workloads.config(name)
+    plan = phb.Plan.for_workload(w, skin=skin)
+    pos, lam, _ = phb.tensors_of(w)
+    phb.build_neighbors(plan, pos, lam)
+    off, idx = phb.export_neighbors(plan)
+    off, idx = off.cpu().numpy(), idx.cpu().numpy()
+    q = sample(w.n, nq, seed=11)
+    got = {int(i): idx[off[i]:off[i + 1]] for i in q}
+    assert_equal_sets(got, oracle_sets(w, q, skin=skin), q)
+    # the 2x jump of lambda at the refinement band of the shear layer gives
+    # coarse particles up to ~5x the mean count and fine ones as few as ~10
+    cnt = np.diff(off)
+    assert cnt.min() >= 5 and cnt.max() < 400 and 40 < cnt.mean() < 70
+    del plan, pos, lam, off, idx
+    torch.cuda.empty_cache()
