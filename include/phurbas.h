@@ -105,7 +105,9 @@ typedef struct {
   int32_t stage_cap;     /* neighbourhood records staged per tile (0 = default) */
   int32_t schedule;      /* fused fit: 0 = one CTA per tile in cell order; 1 = persistent CTAs
                             taking tiles from a queue in descending-cost order */
-  int32_t pad2_;
+  int32_t ell_width;     /* neighbour search: list entries kept per particle in the
+                            single-pass scratch (0 = default 64; longer lists are
+                            searched again); 8 .. 1024 */
   /* filled by phb_plan_init */
   double cell[3];        /* cell edge per axis */
   int32_t ncell[3];      /* cells per axis (at most 1023) */
@@ -115,7 +117,7 @@ typedef struct {
   int64_t nkeys;         /* cell-key space: bricks * 64 */
   double screen_margin;  /* absolute distance margin of the FP32 neighbour screen */
   size_t ws_bytes;       /* workspace bytes needed for every operation */
-  size_t ws_off[32];     /* byte offsets of the workspace regions (internal) */
+  size_t ws_off[48];     /* byte offsets of the workspace regions (internal) */
 } phb_plan;
 
 /* Operations for phb_workspace_size. */
@@ -244,7 +246,7 @@ phb_status phb_rhs_adjoint_stored(const phb_plan* plan, const phb_params* params
  *     (32 MiB) that every GPU which loads the library holds until exit.  A
  *     plan whose build-and-fit workspace (everything before the
  *     predictor-corrector regions) is larger returns PHB_ERR_WORKSPACE and
- *     launches nothing; with constant lambda this allows roughly 48,000
+ *     launches nothing; with constant lambda this allows roughly 33,000
  *     particles.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -18,9 +18,9 @@ FLAG_CAPACITY, FLAG_SKIN, FLAG_FIT_SINGULAR, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_
 PHB_FP64, PHB_FP32_MIXED = 0, 1
 # ws_off index where the workspace part shared by neighbour build, fit and RHS ends
 # (position of R_END_COMMON in the library's region enumeration)
-WS_END_COMMON = 29
+WS_END_COMMON = 33
 # first and last adjoint regions (R_ADJ_EDGE, R_ADJ_SELF; the latter holds 11 doubles per particle)
-WS_ADJ_EDGE, WS_ADJ_SELF = 23, 28
+WS_ADJ_EDGE, WS_ADJ_SELF = 27, 32
 
 EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_check",
            "phb_build_neighbors", "phb_export_neighbors", "phb_neighbor_total", "phb_mls_derivs",
@@ -44,11 +44,11 @@ class Plan(C.Structure):
     _fields_ = [("box", Box), ("n", C.c_int64), ("rf_factor", C.c_double), ("skin", C.c_double),
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double),
                 ("nbr_capacity", C.c_int64), ("cell_frac", C.c_double), ("tile", C.c_int32),
-                ("stage_cap", C.c_int32), ("schedule", C.c_int32), ("pad2_", C.c_int32),
+                ("stage_cap", C.c_int32), ("schedule", C.c_int32), ("ell_width", C.c_int32),
                 ("cell", C.c_double * 3), ("ncell", C.c_int32 * 3), ("nbrick", C.c_int32 * 3),
                 ("hilbert_bits", C.c_int32), ("ntiles", C.c_int32),
                 ("nkeys", C.c_int64), ("screen_margin", C.c_double), ("ws_bytes", C.c_size_t),
-                ("ws_off", C.c_size_t * 32)]
+                ("ws_off", C.c_size_t * 48)]
 
 
 class PhbError(RuntimeError):

@@ -64,13 +64,14 @@ class Plan:
     def __init__(self, box_lo, box_len, periodic, n: int, lambda_min: float, lambda_max: float,
                  rf_factor: float = 2.3, skin: float = 0.0, nbr_capacity: int | None = None,
                  cell_frac: float = 0.0, tile: int = 0, stage_cap: int = 0, schedule: int = 0,
-                 device="cuda"):
+                 ell_width: int = 0, device="cuda"):
         self.device = torch.device(device)
         self.args = dict(box_lo=tuple(map(float, box_lo)), box_len=tuple(map(float, box_len)),
                          periodic=tuple(int(bool(p)) for p in periodic), n=int(n),
                          lambda_min=float(lambda_min), lambda_max=float(lambda_max),
                          rf_factor=float(rf_factor), skin=float(skin), cell_frac=float(cell_frac),
-                         tile=int(tile), stage_cap=int(stage_cap), schedule=int(schedule))
+                         tile=int(tile), stage_cap=int(stage_cap), schedule=int(schedule),
+                         ell_width=int(ell_width))
         if nbr_capacity is None:
             # ~51 neighbours at r_f = 2.3 lambda and uniform density; margin for
             # density contrast and the skin shell
@@ -96,6 +97,7 @@ class Plan:
         p.tile = a["tile"]
         p.stage_cap = a["stage_cap"]
         p.schedule = a["schedule"]
+        p.ell_width = a["ell_width"]
         check(_lib.lib().phb_plan_init(C.byref(p)), "phb_plan_init")
         self.c = p
         self.ws = torch.empty(int(p.ws_bytes), dtype=torch.uint8, device=self.device)

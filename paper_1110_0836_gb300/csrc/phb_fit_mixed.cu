@@ -18,7 +18,6 @@
 #include "phb_internal.cuh"
 #include "mls_gen.cuh"
 #include "phb_mhd.cuh"
-#include "phb_tile.cuh"
 
 namespace phb {
 namespace {
@@ -174,8 +173,9 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
 }
 
 struct TileArgs {
-  const int32_t* cellc;
-  const int2* clin;
+  const int2* tplan;      // per tile: (staged particles, 1 = not staged)
+  const int32_t* tslot;   // per tile: slot of every staged index (stage_cap stride)
+  const uint16_t* lself;  // per slot: its own staged index
   const uint16_t* lidx;
   int32_t* fallback_count;
   const int32_t* order;   // tile order (persistent schedule)
@@ -186,12 +186,6 @@ struct TileArgs {
 // Shared memory of one CTA besides the dynamic park/staging region.
 template <int T>
 struct FitShared {
-  TileShared ts;
-  unsigned bits[kBoxWords];
-  int wpre[kBoxWords];
-  int base[kMarkCap + 1];
-  int cstart[kMarkCap];
-  int warp_tmp[T / 32 + 1];
   int cnt[T];     // list length of each tile particle
   int map[T];     // thread -> tile particle, longest lists first
   int tile;       // persistent schedule: tile taken from the queue
@@ -210,7 +204,6 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   const int cnt_tile = min(T, n - s0);
   const int tid = threadIdx.x;
   const float4* rec = reinterpret_cast<const float4*>(a.rec);
-  const TileArrays tarr{sh.bits, sh.wpre, sh.base, sh.cstart, sh.warp_tmp};
 
   // thread -> particle map, descending list length (ties: slot order)
   {
@@ -234,26 +227,25 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   const bool active = mine < cnt_tile;
   const int s = s0 + mine;
 
-  tile_plan<T>(a.g, s0, cnt_tile, ta.cellc, a.slam, ta.clin, sh.ts, tarr);
-  const bool fb = sh.ts.fallback != 0;
+  // the neighbourhood planned by the neighbour build: one gather per staged record
+  const int2 tp = ta.tplan[tile];
+  const bool fb = tp.y != 0;
   if (!fb) {
     const float4 rh = rec[6 * s0], rl = rec[6 * s0 + 1];
     const float4 fh = rec[6 * s0 + 2], fl = rec[6 * s0 + 3], gh = rec[6 * s0 + 4], gl = rec[6 * s0 + 5];
-    for (int j = tid; j < sh.ts.ncells; j += T) {
-      const int l0 = sh.base[j], c = sh.base[j + 1] - l0, t0 = sh.cstart[j];
-      for (int p = 0; p < c; ++p) {
-        const float4* r = rec + 6 * (t0 + p);
-        const float4 p0 = r[0], p1 = r[1], f0 = r[2], f1 = r[3], g0 = r[4], g1 = r[5];
-        float4* d = stage + 3 * (l0 + p);
-        d[0] = make_float4(mi_diff32(p0.x, p1.x, rh.x, rl.x, P.len_h[0], P.len_l[0], P.inv_len[0]),
-                           mi_diff32(p0.y, p1.y, rh.y, rl.y, P.len_h[1], P.len_l[1], P.inv_len[1]),
-                           mi_diff32(p0.z, p1.z, rh.z, rl.z, P.len_h[2], P.len_l[2], P.inv_len[2]),
-                           hl(f0.y, f1.y, fh.y, fl.y));
-        d[1] = make_float4(hl(f0.z, f1.z, fh.z, fl.z), hl(f0.w, f1.w, fh.w, fl.w),
-                           hl(g0.x, g1.x, gh.x, gl.x), hl(f0.x, f1.x, fh.x, fl.x));
-        d[2] = make_float4(hl(g0.y, g1.y, gh.y, gl.y), hl(g0.z, g1.z, gh.z, gl.z),
-                           hl(g0.w, g1.w, gh.w, gl.w), 0.f);
-      }
+    const int32_t* slots = ta.tslot + static_cast<int64_t>(tile) * a.g.stage_cap;
+    for (int l = tid; l < tp.x; l += T) {
+      const float4* r = rec + 6 * slots[l];
+      const float4 p0 = r[0], p1 = r[1], f0 = r[2], f1 = r[3], g0 = r[4], g1 = r[5];
+      float4* d = stage + 3 * l;
+      d[0] = make_float4(mi_diff32(p0.x, p1.x, rh.x, rl.x, P.len_h[0], P.len_l[0], P.inv_len[0]),
+                         mi_diff32(p0.y, p1.y, rh.y, rl.y, P.len_h[1], P.len_l[1], P.inv_len[1]),
+                         mi_diff32(p0.z, p1.z, rh.z, rl.z, P.len_h[2], P.len_l[2], P.inv_len[2]),
+                         hl(f0.y, f1.y, fh.y, fl.y));
+      d[1] = make_float4(hl(f0.z, f1.z, fh.z, fl.z), hl(f0.w, f1.w, fh.w, fl.w),
+                         hl(g0.x, g1.x, gh.x, gl.x), hl(f0.x, f1.x, fh.x, fl.x));
+      d[2] = make_float4(hl(g0.y, g1.y, gh.y, gl.y), hl(g0.z, g1.z, gh.z, gl.z),
+                         hl(g0.w, g1.w, gh.w, gl.w), 0.f);
     }
   } else if (tid == 0) {
     atomicAdd(ta.fallback_count, 1);
@@ -282,8 +274,7 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       StagedSrc src;
       src.stage = stage;
       src.lidx = ta.lidx;
-      const int js = marked_index(tarr, box_index(a.g, sh.ts, ta.cellc[s]));
-      const int ls = sh.base[js] + (s - sh.cstart[js]);
+      const int ls = ta.lself[s];
       src.me0 = stage[3 * ls];
       src.me1 = stage[3 * ls + 1];
       src.me2 = stage[3 * ls + 2];
@@ -469,11 +460,11 @@ cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, cudaS
 
 }  // namespace
 
-cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int32_t* cellc, const int2* clin,
-                             const uint16_t* lidx, int32_t* fallback_count, const int32_t* order,
-                             int32_t* queue_head, cudaStream_t st) {
+cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int2* tplan, const int32_t* tslot,
+                             const uint16_t* lself, const uint16_t* lidx, int32_t* fallback_count,
+                             const int32_t* order, int32_t* queue_head, cudaStream_t st) {
   const Per32 P = make_per32(a.g);
-  const TileArgs ta{cellc, clin, lidx, fallback_count, order, queue_head,
+  const TileArgs ta{tplan, tslot, lself, lidx, fallback_count, order, queue_head,
                     static_cast<int32_t>((a.n + a.g.tile - 1) / a.g.tile)};
   if (mode == FitMode::kDerivs)
     return a.g.tile == 64 ? launch_t<FitMode::kDerivs, 64>(a, P, ta, st)

@@ -37,6 +37,10 @@ enum Region {
   R_CELLC,       // int32 [n] packed cell coordinates of each slot (10 bits per axis)
   R_CLIN,        // int2 [cells] (first slot, count) per linear cell index (x-major)
   R_TORDER,      // int32 [ntiles] tiles in descending cost class (persistent schedule)
+  R_ELL,         // int32 [n][ell_width] first list entries of each slot (single-pass search)
+  R_TPLAN,       // int2 [ntiles] (staged particles, 1 = not staged) of each tile's neighbourhood
+  R_TSLOT,       // int32 [ntiles][stage_cap] slot of every staged index of each tile
+  R_LSELF,       // uint16 [n] each slot's own staged index within its tile
   R_QUEUE,       // int32 [n]    slots routed to FP64
   R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
@@ -51,7 +55,7 @@ enum Region {
   R_END,         // end of everything
   R_COUNT
 };
-static_assert(R_COUNT <= 32, "ws_off has 32 entries");
+static_assert(R_COUNT <= 48, "ws_off has 48 entries");
 
 template <typename T>
 __host__ __device__ inline T* region(const phb_plan* p, void* ws, Region r) {
@@ -70,6 +74,7 @@ struct Grid {
   int32_t tile;       // particles per tile
   int32_t stage_cap;  // staged records per tile
   int32_t schedule;   // 0: grid of tiles, 1: persistent queue
+  int32_t ell;        // list entries kept per slot by the single-pass search
   int32_t n;
   double rf_factor, skin;
   double lambda_min, lambda_max;
@@ -253,9 +258,9 @@ struct FitArgs {
   int32_t* status_word;
 };
 
-cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int32_t* cellc, const int2* clin,
-                             const uint16_t* lidx, int32_t* fallback_count, const int32_t* order,
-                             int32_t* queue_head, cudaStream_t st);
+cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int2* tplan, const int32_t* tslot,
+                             const uint16_t* lself, const uint16_t* lidx, int32_t* fallback_count,
+                             const int32_t* order, int32_t* queue_head, cudaStream_t st);
 // FP64 fused fit over all slots (list == null) or over list[0 .. *list_len).
 cudaError_t launch_fit_fp64(const FitArgs& a, FitMode mode, const int32_t* list,
                             const int32_t* list_len, cudaStream_t st);

@@ -146,43 +146,67 @@ __device__ __forceinline__ int axis_cell(const Grid& g, int a, const Reach& q, i
   return c;
 }
 
-// Thread per particle (slot order): candidates from the cells within reach,
-// looked up through the linear (first slot, count) table; FP32 screen on the
-// wrapped positions, exact FP64 test in the ambiguous band.
-template <bool kFill>
-__global__ void __launch_bounds__(kThreads) k_search(Grid g, const int2* __restrict__ clin,
-                                                     const int32_t* __restrict__ cellc,
-                                                     const float4* __restrict__ scr,
-                                                     const double* __restrict__ spos,
-                                                     const double* __restrict__ slam,
-                                                     int32_t* __restrict__ ncnt,
-                                                     const int64_t* __restrict__ off,
-                                                     int32_t* __restrict__ idx, int32_t* status_word) {
-  const int n = g.n;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const double r = list_radius(g, slam[s]);
-  const double r2 = __dmul_rn(r, r);
-  const double m = static_cast<double>(g.screen_margin) + 4e-7 * r;
-  const float in2 = static_cast<float>(r > m ? (r - m) * (r - m) : 0.0);
-  const float out2 = static_cast<float>((r + m) * (r + m));
-  const float4 me = scr[s];
+// Screen of candidate t against particle s: FP32 offsets of the wrapped
+// positions and squared distance against the inner / outer screen radii;
+// the exact FP64 test decides the ambiguous band.  kWrap = false skips the
+// minimum image, which is then the identity (see the caller).
+struct Screen {
+  float in2, out2;
+  double r2;
   float lenf[3], invlf[3];
+};
+
+__device__ __forceinline__ Screen make_screen(const Grid& g, double r) {
+  Screen q;
+  q.r2 = __dmul_rn(r, r);
+  const double m = static_cast<double>(g.screen_margin) + 4e-7 * r;
+  q.in2 = static_cast<float>(r > m ? (r - m) * (r - m) : 0.0);
+  q.out2 = static_cast<float>((r + m) * (r + m));
   for (int a = 0; a < 3; ++a) {
-    lenf[a] = static_cast<float>(g.len[a]);
-    invlf[a] = g.periodic[a] ? static_cast<float>(1.0 / g.len[a]) : 0.f;
+    q.lenf[a] = static_cast<float>(g.len[a]);
+    q.invlf[a] = g.periodic[a] ? static_cast<float>(1.0 / g.len[a]) : 0.f;
   }
-  int c[3];
-  unpack_cell(cellc[s], c[0], c[1], c[2]);
-  const Reach qx = axis_reach(g, 0, c[0], r);
-  const Reach qy = axis_reach(g, 1, c[1], r);
-  const Reach qz = axis_reach(g, 2, c[2], r);
-  int64_t base = 0, end = 0;
-  if (kFill) {
-    base = off[s];
-    end = off[s + 1];
-    if (end > g.capacity) raise_flag(status_word, PHB_FLAG_CAPACITY);
+  return q;
+}
+
+template <bool kWrap>
+__device__ __forceinline__ bool is_neighbour(const Grid& g, const Screen& q, const double* spos,
+                                             int s, int t, float4 me, float4 o) {
+  float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
+  if (kWrap) {
+    dx = fmaf(-q.lenf[0], rintf(dx * q.invlf[0]), dx);
+    dy = fmaf(-q.lenf[1], rintf(dy * q.invlf[1]), dy);
+    dz = fmaf(-q.lenf[2], rintf(dz * q.invlf[2]), dz);
   }
+  const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  if (d2 < q.in2) return true;
+  if (d2 > q.out2) return false;
+  return dist2_exact(g, spos, g.n, s, t) < q.r2;
+}
+
+// Whether every cell of the reach on axis a lies inside the grid without
+// wrapping and spans less than half the box, so that the plain difference of
+// two wrapped positions is already the minimum image: |dx| < (R + 1) cells
+// <= len / 2 gives rint(dx / len) = 0.
+__device__ __forceinline__ bool plain_axis(const Grid& g, int a, int c, const Reach& q) {
+  if (!g.periodic[a]) return true;
+  const int R = q.count / 2;
+  return q.wrap && c - R >= 0 && c + R < g.ncell[a] && 2 * R + 3 <= g.ncell[a];
+}
+
+enum SearchOut { kCount = 0, kFillCsr = 1, kFillEll = 2 };
+
+// One particle's list: candidates from the cells within reach, looked up
+// through the linear (first slot, count) table, in cell order (x, y, z) and
+// slot order inside a cell.  kCount only counts; kFillCsr writes entries
+// [base, end) of the CSR lists; kFillEll writes the first g.ell entries to
+// the slot's row of the single-pass scratch.  Returns the exact count.
+template <int OUT, bool kWrap>
+__device__ int search_one(const Grid& g, const int2* __restrict__ clin, const float4* __restrict__ scr,
+                          const double* __restrict__ spos, const Screen& q, const int (&c)[3],
+                          const Reach& qx, const Reach& qy, const Reach& qz, int s, int64_t base,
+                          int64_t end, int32_t* __restrict__ out) {
+  const float4 me = scr[s];
   int count = 0;
   for (int kx = 0; kx < qx.count; ++kx) {
     bool okx;
@@ -199,63 +223,132 @@ __global__ void __launch_bounds__(kThreads) k_search(Grid g, const int2* __restr
         if (!okz) continue;
         const int2 sc = clin[row + cz];
         for (int t = sc.x; t < sc.x + sc.y; ++t) {
-          if (t == s) continue;
-          const float4 o = scr[t];
-          float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
-          dx = fmaf(-lenf[0], rintf(dx * invlf[0]), dx);
-          dy = fmaf(-lenf[1], rintf(dy * invlf[1]), dy);
-          dz = fmaf(-lenf[2], rintf(dz * invlf[2]), dz);
-          const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          bool in;
-          if (d2 < in2) in = true;
-          else if (d2 > out2) in = false;
-          else in = dist2_exact(g, spos, n, s, t) < r2;
-          if (in) {
-            if (kFill) {
-              const int64_t e = base + count;
-              if (e < g.capacity && e < end) idx[e] = t;
-            }
-            ++count;
+          if (t == s || !is_neighbour<kWrap>(g, q, spos, s, t, me, scr[t])) continue;
+          if (OUT == kFillCsr) {
+            const int64_t e = base + count;
+            if (e < g.capacity && e < end) out[e] = t;
+          } else if (OUT == kFillEll) {
+            if (count < g.ell) out[count] = t;
           }
+          ++count;
         }
       }
     }
   }
-  if (!kFill) ncnt[s] = count;
+  return count;
 }
 
-// One CTA per tile: map every list entry of the tile's particles to its index
-// in the tile's staged neighbourhood (the fused fit rebuilds the same plan).
+template <int OUT>
+__device__ int search_particle(const Grid& g, const int2* __restrict__ clin,
+                               const int32_t* __restrict__ cellc, const float4* __restrict__ scr,
+                               const double* __restrict__ spos, double r, int s, int64_t base,
+                               int64_t end, int32_t* __restrict__ out) {
+  const Screen q = make_screen(g, r);
+  int c[3];
+  unpack_cell(cellc[s], c[0], c[1], c[2]);
+  const Reach qx = axis_reach(g, 0, c[0], r);
+  const Reach qy = axis_reach(g, 1, c[1], r);
+  const Reach qz = axis_reach(g, 2, c[2], r);
+  if (plain_axis(g, 0, c[0], qx) && plain_axis(g, 1, c[1], qy) && plain_axis(g, 2, c[2], qz))
+    return search_one<OUT, false>(g, clin, scr, spos, q, c, qx, qy, qz, s, base, end, out);
+  return search_one<OUT, true>(g, clin, scr, spos, q, c, qx, qy, qz, s, base, end, out);
+}
+
+// Single pass, thread per particle (slot order): exact list lengths and the
+// first g.ell entries of every list.
+__global__ void __launch_bounds__(kThreads) k_search_ell(Grid g, const int2* __restrict__ clin,
+                                                         const int32_t* __restrict__ cellc,
+                                                         const float4* __restrict__ scr,
+                                                         const double* __restrict__ spos,
+                                                         const double* __restrict__ slam,
+                                                         int32_t* __restrict__ ncnt,
+                                                         int32_t* __restrict__ ell) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.n) return;
+  const double r = list_radius(g, slam[s]);
+  ncnt[s] = search_particle<kFillEll>(g, clin, cellc, scr, spos, r, s, 0, 0,
+                                      ell + static_cast<int64_t>(s) * g.ell);
+}
+
+// One CTA per tile: move the tile's lists from the single-pass scratch into
+// the CSR arrays (searching again, straight into CSR, for lists longer than
+// the scratch rows), plan the tile's staged neighbourhood and record it for
+// the fused fit - (staged count, unstaged flag), the slot of every staged
+// index, each tile particle's own staged index - and map every list entry to
+// its staged index.
 template <int T>
-__global__ void __launch_bounds__(T) k_localize(Grid g, const int2* __restrict__ clin,
-                                                const int32_t* __restrict__ cellc,
-                                                const double* __restrict__ slam,
-                                                const int64_t* __restrict__ off,
-                                                const int32_t* __restrict__ idx,
-                                                uint16_t* __restrict__ lidx,
-                                                int32_t* fallback_count) {
+__global__ void __launch_bounds__(T) k_compact(Grid g, const int2* __restrict__ clin,
+                                               const int32_t* __restrict__ cellc,
+                                               const float4* __restrict__ scr,
+                                               const double* __restrict__ spos,
+                                               const double* __restrict__ slam,
+                                               const int32_t* __restrict__ ncnt,
+                                               const int32_t* __restrict__ ell,
+                                               const int64_t* __restrict__ off,
+                                               int32_t* __restrict__ idx, uint16_t* __restrict__ lidx,
+                                               int2* __restrict__ tplan, int32_t* __restrict__ tslot,
+                                               uint16_t* __restrict__ lself, int32_t* fallback_count,
+                                               int32_t* status_word) {
   __shared__ TileShared ts;
   __shared__ unsigned bits[kBoxWords];
   __shared__ int wpre[kBoxWords];
   __shared__ int base[kMarkCap + 1];
   __shared__ int cstart[kMarkCap];
   __shared__ int warp_tmp[T / 32 + 1];
+  __shared__ int64_t toff[T + 1];
   const TileArrays tarr{bits, wpre, base, cstart, warp_tmp};
   const int n = g.n;
+  const int tid = threadIdx.x;
   const int s0 = blockIdx.x * T;
   const int cnt = min(T, n - s0);
-  tile_plan<T>(g, s0, cnt, cellc, slam, clin, ts, tarr);
-  if (ts.fallback) {
-    if (threadIdx.x == 0) atomicAdd(fallback_count, 1);
-    return;
+  for (int k = tid; k <= cnt; k += T) toff[k] = off[s0 + k];
+  __syncthreads();
+  if (tid < cnt) {
+    const int s = s0 + tid;
+    if (toff[tid + 1] > g.capacity) raise_flag(status_word, PHB_FLAG_CAPACITY);
+    if (ncnt[s] > g.ell)
+      search_particle<kFillCsr>(g, clin, cellc, scr, spos, list_radius(g, slam[s]), s, toff[tid],
+                                toff[tid + 1], idx);
   }
-  const int64_t e0 = off[s0];
-  int64_t e1 = off[s0 + cnt];
-  if (e1 > g.capacity) e1 = g.capacity;
-  for (int64_t e = e0 + threadIdx.x; e < e1; e += T) {
-    const int t = idx[e];
-    const int j = marked_index(tarr, box_index(g, ts, cellc[t]));
-    lidx[e] = static_cast<uint16_t>(base[j] + (t - cstart[j]));
+  tile_plan<T>(g, s0, cnt, cellc, slam, clin, ts, tarr);
+  const bool staged = !ts.fallback;
+  if (tid == 0) {
+    tplan[blockIdx.x] = make_int2(staged ? ts.total : 0, staged ? 0 : 1);
+    if (!staged) atomicAdd(fallback_count, 1);
+  }
+  if (staged) {
+    int32_t* ts_out = tslot + static_cast<int64_t>(blockIdx.x) * g.stage_cap;
+    for (int j = tid; j < ts.ncells; j += T) {
+      const int l0 = base[j], m = base[j + 1] - l0, t0 = cstart[j];
+      for (int q = 0; q < m; ++q) ts_out[l0 + q] = t0 + q;
+    }
+    if (tid < cnt) {
+      const int s = s0 + tid;
+      const int j = marked_index(tarr, box_index(g, ts, cellc[s]));
+      lself[s] = static_cast<uint16_t>(base[j] + (s - cstart[j]));
+    }
+  }
+  const int64_t e0 = toff[0];
+  const int64_t e1 = toff[cnt] < g.capacity ? toff[cnt] : g.capacity;
+  for (int64_t e = e0 + tid; e < e1; e += T) {
+    int lo = 0, hi = cnt - 1;  // owner: last k with toff[k] <= e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (toff[mid] <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const int s = s0 + lo;
+    int t;
+    if (ncnt[s] <= g.ell) {
+      t = ell[static_cast<int64_t>(s) * g.ell + (e - toff[lo])];
+      idx[e] = t;
+    } else {
+      t = idx[e];
+    }
+    if (staged) {
+      const int j = marked_index(tarr, box_index(g, ts, cellc[t]));
+      lidx[e] = static_cast<uint16_t>(base[j] + (t - cstart[j]));
+    }
   }
 }
 
@@ -359,19 +452,21 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   k_cell_lin<<<blocks_for(ncells), kThreads, 0, st>>>(g, cell, clin);
   note_launch();
   if ((e = cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), st))) return e;
-  k_search<false><<<blocks_for(n), kThreads, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, nullptr,
-                                                       nullptr, status_word);
+  int32_t* ell = region<int32_t>(p, ws, R_ELL);
+  k_search_ell<<<blocks_for(n), kThreads, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, ell);
   note_launch();
   if ((e = cudaMemsetAsync(ncnt + n, 0, sizeof(int32_t), st))) return e;
   if ((e = scan_exclusive_i32_to_i64(ncnt, off, n + 1, bsum, st))) return e;
-  k_search<true><<<blocks_for(n), kThreads, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, off, idx,
-                                                      status_word);
-  note_launch();
   const unsigned tiles = static_cast<unsigned>(p->ntiles);
+  int2* tplan = region<int2>(p, ws, R_TPLAN);
+  int32_t* tslot = region<int32_t>(p, ws, R_TSLOT);
+  uint16_t* lself = region<uint16_t>(p, ws, R_LSELF);
   if (p->tile == 128)
-    k_localize<128><<<tiles, 128, 0, st>>>(g, clin, cellc, slam, off, idx, lidx, misc + 1);
+    k_compact<128><<<tiles, 128, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, ell, off, idx, lidx,
+                                          tplan, tslot, lself, misc + 1, status_word);
   else
-    k_localize<64><<<tiles, 64, 0, st>>>(g, clin, cellc, slam, off, idx, lidx, misc + 1);
+    k_compact<64><<<tiles, 64, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, ell, off, idx, lidx,
+                                        tplan, tslot, lself, misc + 1, status_word);
   note_launch();
   k_tile_order<<<1, 1024, 0, st>>>(n, p->tile, p->ntiles, p->nbr_capacity, off,
                                    region<int32_t>(p, ws, R_TORDER));

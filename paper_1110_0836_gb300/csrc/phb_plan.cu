@@ -32,6 +32,7 @@ Grid make_grid(const phb_plan* p) {
   g.tile = p->tile;
   g.stage_cap = p->stage_cap;
   g.schedule = p->schedule;
+  g.ell = p->ell_width;
   g.n = static_cast<int32_t>(p->n);
   g.rf_factor = p->rf_factor;
   g.skin = p->skin;
@@ -219,6 +220,8 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   if (p->stage_cap < 64 || p->stage_cap > 2048) return PHB_ERR_INVALID_ARG;
   p->ntiles = static_cast<int32_t>((p->n + p->tile - 1) / p->tile);
   if (p->schedule != 0 && p->schedule != 1) return PHB_ERR_INVALID_ARG;
+  if (p->ell_width == 0) p->ell_width = 64;
+  if (p->ell_width < 8 || p->ell_width > 1024) return PHB_ERR_INVALID_ARG;
   // FP32 screen: bound of |d32 - d| per component is 2^-24 (2X + 3L); two
   // components' worth of safety on top, times sqrt(3) for the norm.
   p->screen_margin = 8.0 * std::sqrt(3.0) * std::ldexp(1.0, -24) * (2.0 * xmax + 3.0 * lmax);
@@ -244,6 +247,10 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   sz[R_CELLC] = n * 4;
   sz[R_CLIN] = size_t(p->ncell[0]) * p->ncell[1] * p->ncell[2] * 8;
   sz[R_TORDER] = size_t(p->ntiles) * 4;
+  sz[R_ELL] = size_t(n) * p->ell_width * 4;
+  sz[R_TPLAN] = size_t(p->ntiles) * 8;
+  sz[R_TSLOT] = size_t(p->ntiles) * p->stage_cap * 4;
+  sz[R_LSELF] = size_t(n) * 2;
   sz[R_QUEUE] = (n + 64) * 4;  // also the export's n+1 counts
   size_t off = 0;
   for (int r = R_MISC; r <= R_QUEUE; ++r) {

@@ -77,8 +77,9 @@ cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMo
   if (prm->precision == PHB_FP64) return launch_fit_fp64(a, mode, nullptr, nullptr, st);
   if ((e = cudaMemsetAsync(a.queue_len, 0, sizeof(int32_t), st))) return e;
   if ((e = cudaMemsetAsync(a.queue_len + 2, 0, sizeof(int32_t), st))) return e;
-  if ((e = launch_fit_mixed(a, mode, region<int32_t>(plan, ws, R_CELLC), region<int2>(plan, ws, R_CLIN),
-                            region<uint16_t>(plan, ws, R_LIDX), a.queue_len + 2,
+  if ((e = launch_fit_mixed(a, mode, region<int2>(plan, ws, R_TPLAN), region<int32_t>(plan, ws, R_TSLOT),
+                            region<uint16_t>(plan, ws, R_LSELF), region<uint16_t>(plan, ws, R_LIDX),
+                            a.queue_len + 2,
                             region<int32_t>(plan, ws, R_TORDER), a.queue_len + 3, st)))
     return e;
   return launch_fit_fp64(a, mode, a.queue, a.queue_len, st);

@@ -66,7 +66,7 @@ def test_plan_init_valid(L):
     # the shared prefix ends where the predictor-corrector regions begin
     from paper_1110_0836_gb300 import _lib
     end = p.ws_off[_lib.WS_END_COMMON]
-    assert end > offs[-1] and end == p.ws_off[20]  # first predictor-corrector region
+    assert end > offs[-1] and end == p.ws_off[_lib.WS_END_COMMON - 9]  # first predictor-corrector region
     # adjoint regions: edge contributions (10 doubles per list entry) first, the
     # per-particle self terms (11 doubles) last, ending the workspace
     assert p.ws_off[_lib.WS_ADJ_SELF] - p.ws_off[_lib.WS_ADJ_EDGE] >= 10 * 8 * p.nbr_capacity
@@ -81,7 +81,8 @@ def test_plan_init_tile_and_schedule(L, tile, schedule):
     assert p.tile == tile and p.schedule == schedule and p.ntiles == -(-p.n // tile)
 
 
-@pytest.mark.parametrize("field,val", [("tile", 96), ("schedule", 2)])
+@pytest.mark.parametrize("field,val", [("tile", 96), ("schedule", 2), ("ell_width", 4),
+                                       ("ell_width", 2000)])
 def test_plan_init_rejects_launch_shape(L, field, val):
     p = _plan()
     setattr(p, field, val)

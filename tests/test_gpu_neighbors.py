@@ -121,11 +121,14 @@ def test_full_size_lattice_sampled():
     assert cnt.min() >= 40 and cnt.max() <= 62
 
 
-@pytest.mark.parametrize("tile,stage_cap", [(64, 0), (128, 64)])
-def test_tiled_and_fallback_search_agree(tile, stage_cap):
+@pytest.mark.parametrize("tile,stage_cap,ell_width", [(64, 0, 0), (128, 64, 0), (128, 0, 8),
+                                                      (64, 0, 40)])
+def test_tiled_and_fallback_search_agree(tile, stage_cap, ell_width):
+    """Tile sizes, unstaged tiles, and single-pass scratch rows shorter than
+    every list (ell_width 8) or than some lists (40): identical sets."""
     phb = need_gpu()
     w = workloads.shock_tube(20000, seed=5)
-    got, plan = gpu_sets(phb, w, tile=tile, stage_cap=stage_cap)
+    got, plan = gpu_sets(phb, w, tile=tile, stage_cap=stage_cap, ell_width=ell_width)
     q = sample(w.n, 1500, seed=3)
     assert_equal_sets(got, oracle_sets(w, q), q)
     if stage_cap == 64:
