@@ -56,7 +56,10 @@ def load(path: str):
                               _f64p, _f64p]
     L.orc_pc_step.argtypes = [C.POINTER(Box), C.c_int64, _f64p, _f64p, _f64p, C.c_double,
                               C.POINTER(Params)]
-    for f in ("orc_neighbors", "orc_mls_derivs", "orc_mhd_rhs", "orc_rhs_jvp", "orc_pc_step"):
+    L.orc_timestep_levels.argtypes = [C.c_int64, _f64p, _f64p, C.c_double, C.c_double, C.c_double,
+                                      C.c_int32, _i64p, _i64p, _i32p]
+    for f in ("orc_neighbors", "orc_mls_derivs", "orc_mhd_rhs", "orc_rhs_jvp", "orc_pc_step",
+              "orc_timestep_levels"):
         getattr(L, f).restype = C.c_int
     return L
 
@@ -200,6 +203,21 @@ def pc_step(box: Box, pos, lam, U, dt, gamma=5.0 / 3.0, rf_factor=2.3, weight_ki
     return pos, U, nsing
 
 
+def timestep_levels(lam, U, nbrs, gamma=5.0 / 3.0, cfl=0.1, dt_max=1.0, max_level=20):
+    """Individual power-of-two time-step levels with the spatial limiter
+    (see orc_timestep_levels); nbrs = CSR lists of all particles."""
+    lam, U = _c(lam), _c(U)
+    n = lam.shape[0]
+    off, idx = nbrs
+    out = np.zeros(n, np.int32)
+    rc = lib().orc_timestep_levels(n, lam, U, float(gamma), float(cfl), float(dt_max),
+                                   int(max_level), _c(off, np.int64),
+                                   _c(idx, np.int64) if len(idx) else np.zeros(1, np.int64), out)
+    if rc:
+        raise ValueError("timestep_levels: invalid arguments or non-physical state")
+    return out
+
+
 def workload_rhs(w, query=None, **kw):
     """Convenience: brute-force neighbours plus dU/dt for a workloads.Workload."""
     box = box_of(w)
@@ -216,7 +234,7 @@ def available() -> bool:
 
 
 __all__ = ["Box", "Params", "lib", "load", "using", "make_box", "box_of", "neighbors", "mls_derivs", "mhd_rhs",
-           "rhs_jvp", "pc_step", "workload_rhs", "available"]
+           "rhs_jvp", "pc_step", "timestep_levels", "workload_rhs", "available"]
 
 if os.environ.get("PHB_ORACLE_EAGER"):
     lib()

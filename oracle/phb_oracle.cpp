@@ -20,7 +20,11 @@
 //   * the second-order predictor-corrector read as Heun's method (Sec. 2,
 //     Sec. 4.2 "explicit Hermitian time integration");
 //   * a forward-mode (dual number) derivative of the right-hand side with the
-//     neighbour sets frozen, used to pin the hand-written reverse-mode adjoint.
+//     neighbour sets frozen, used to pin the hand-written reverse-mode adjoint;
+//   * individual power-of-two time-step levels with the spatial limiter
+//     (Sec. 2: steps independent of the bulk velocity, spatial variation
+//     limited; Sec. 2.1: rounded down to powers of two, information flows
+//     from a particle to its neighbours).
 //
 // Readings where the paper defers to Paper I:
 //   weight w = (1 - s^2)^2 with s = |d| / r_f,i (or w = 1);
@@ -386,6 +390,45 @@ int orc_pc_step(const Box* box, int64_t n, double* pos, const double* lam, doubl
       pos[ax * n + i] += 0.5 * dt * (U[(1 + ax) * n + i] + up[(1 + ax) * n + i]);
   for (int64_t k = 0; k < NF * n; ++k) U[k] += 0.5 * dt * (F0[k] + F1[k]);
   return static_cast<int>(nsing);
+}
+
+// Individual time-step levels (Sec. 2, Sec. 2.1).  Readings: the Courant
+// step of particle i is dt_i = cfl lambda_i / c_i with the fast magnetosonic
+// bound c_i = sqrt((gamma P_i + |B_i|^2) / rho_i) (no bulk velocity, mu_0 = 1),
+// evaluated as  B2 = (Bx*Bx + By*By) + Bz*Bz,  c2 = (gamma*P + B2) / rho,
+// dt = (cfl*lambda) / sqrt(c2)  in FP64 without contraction.  Its level is
+// the smallest L >= 0 with dt_max / 2^L <= dt_i (the step rounded down to a
+// power of two of dt_max), capped at max_level.  The limiter then sends each
+// particle's level to its neighbours: for every i and every j in N(i),
+// L_j >= L_i - 1, applied once from the unlimited levels:
+//   L_j = max(L0_j, max_{i : j in N(i)} (L0_i - 1)).
+// Lists are CSR over all particles (nq = n, query i = i).  levels [n].
+// Returns 0, or 1 for a non-positive dt_max / cfl or a non-physical state.
+int orc_timestep_levels(int64_t n, const double* lam, const double* U, double gamma, double cfl,
+                        double dt_max, int32_t max_level, const int64_t* off, const int64_t* idx,
+                        int32_t* levels) {
+  if (!(dt_max > 0.0) || !(cfl > 0.0) || max_level < 0) return 1;
+  std::vector<int32_t> L0(n);
+  int bad = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double rho = U[i], sig = U[7 * n + i];
+    const double bx = U[4 * n + i], by = U[5 * n + i], bz = U[6 * n + i];
+    const double P = (gamma - 1.0) * sig;
+    const double B2 = (bx * bx + by * by) + bz * bz;
+    const double c2 = (gamma * P + B2) / rho;
+    if (!(rho > 0.0) || !(c2 > 0.0)) bad = 1;
+    const double dt = (cfl * lam[i]) / std::sqrt(c2);
+    int32_t L = 0;
+    while (L < max_level && std::ldexp(dt_max, -L) > dt) ++L;
+    L0[i] = L;
+  }
+  for (int64_t j = 0; j < n; ++j) levels[j] = L0[j];
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+      const int64_t j = idx[e];
+      if (L0[i] - 1 > levels[j]) levels[j] = L0[i] - 1;
+    }
+  return bad;
 }
 
 }  // extern "C"

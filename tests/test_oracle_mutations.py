@@ -14,6 +14,7 @@ import oracle
 from oracle import build as obuild
 
 import test_oracle_fit as tfit
+import test_oracle_levels as tlev
 import test_oracle_neighbors as tnb
 import test_oracle_rhs as trhs
 import test_oracle_step as tstep
@@ -35,6 +36,15 @@ MUTATIONS = {
     "euler_corrector": ("U[k] += 0.5 * dt * (F0[k] + F1[k]);", "U[k] += dt * F0[k];"),
     "basis_xyz_missing": ("p[13] = x * y * z;", "p[13] = x * y;"),
     "lambda_scale": ("grad[f][0] = C[0 * NF + f] * il;", "grad[f][0] = C[0 * NF + f] * il * il;"),
+    "level_off_by_one": ("    int32_t L = 0;\n    while (L < max_level", "    int32_t L = 1;\n    while (L < max_level"),
+    "limiter_two_levels": ("if (L0[i] - 1 > levels[j]) levels[j] = L0[i] - 1;",
+                           "if (L0[i] - 2 > levels[j]) levels[j] = L0[i] - 2;"),
+    "limiter_gathers": ("if (L0[i] - 1 > levels[j]) levels[j] = L0[i] - 1;",
+                        "if (L0[j] - 1 > levels[i]) levels[i] = L0[j] - 1;"),
+    "speed_with_bulk_velocity": ("const double c2 = (gamma * P + B2) / rho;",
+                                 "const double c2 = (gamma * P + B2) / rho + U[n + i] * U[n + i];"),
+    "speed_without_field": ("const double c2 = (gamma * P + B2) / rho;",
+                            "const double c2 = (gamma * P) / rho;"),
 }
 
 PINS = [
@@ -50,6 +60,10 @@ PINS = [
     lambda: trhs.test_divb_diffusion(oracle),
     lambda: trhs.test_viscous_heating_linear_flow(oracle),
     lambda: tstep.test_heun_is_second_order_in_time(oracle),
+    lambda: tlev.test_golden_line(),
+    lambda: tlev.test_power_of_two_rounding_against_the_courant_step(),
+    lambda: tlev.test_bulk_velocity_does_not_change_levels(),
+    lambda: tlev.test_limiter_guarantee_and_minimality(),
 ]
 
 
