@@ -41,7 +41,7 @@ FLOP_PER_NEIGHBOUR = 2 * (80 + 7 * 19)
 FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
 # DRAM bytes (read + write) per launch of the fused fit, from ncu captures of the
 # kernel as it is built now: (workload, kernel, tile) -> bytes.  Absent = null.
-FIT_TRAFFIC = {}
+FIT_TRAFFIC = {("random_modes_64^3", "k_fit_mixed", 128): 67.78e6 + 2.78e6}
 
 
 def parse():
@@ -231,7 +231,35 @@ def oracle_leg(w, sample: int, seed: int = 0):
             "sample": f"{len(q)} particles of {w.name} x {reps} repetitions ({el:.1f} s): FP64 "
                       "Householder-QR fit + RHS, OpenMP over particles, brute-force neighbour "
                       "lists precomputed outside the timing"}
-    return rate, info, q, out
+    return rate, info, q, out, nb
+
+
+def rhs_term_scales(U, grad, hess, gamma):
+    """Per field, the largest magnitude over the sample of the terms combined in
+    that field's equation (ideal MHD, no zeta / eta): the scale against which
+    rounding errors of the right-hand side are measured, so that a field whose
+    terms cancel is measured on its terms' size.  U [8][m], grad [8][3][m],
+    hess [8][6][m] (oracle values)."""
+    rho, sig, B = np.abs(U[0]), np.abs(U[7]), np.abs(U[4:7])
+    gV, gB = np.abs(grad[1:4]), np.abs(grad[4:7])
+    divabs = gV[0, 0] + gV[1, 1] + gV[2, 2]
+    J = gB.sum(axis=(0, 1))
+    sc = np.zeros(8)
+    sc[0] = (rho * divabs).max()
+    sc[1:4] = (((gamma - 1) * np.abs(grad[7]).max(axis=0) + J * B.max(axis=0)) / rho).max()
+    for a in range(3):
+        sc[4 + a] = ((B * gV[a]).sum(axis=0) + B[a] * divabs).max()
+    sc[7] = (gamma * sig * divabs).max()
+    return sc
+
+
+def deriv_err(a, o, floor_frac=1e-2):
+    """Per field: max over sample and components of |a - o| over the field's
+    largest |o| (floored at floor_frac of the largest field's), a, o [8][k][m]."""
+    num = np.abs(a - o).max(axis=(1, 2))
+    den = np.abs(o).max(axis=(1, 2))
+    den = np.maximum(den, floor_frac * den.max())
+    return num / np.where(den > 0, den, 1.0)
 
 
 def run_reference(args):
@@ -425,6 +453,7 @@ def run_ours(args):
     traffic = FIT_TRAFFIC.get((w.name, kname, int(plan.c.tile)))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "DRAM bytes read + written per launch (ncu, profiles/)",
                 "kernel": f"{kname}<kRHS, {int(plan.c.tile)}> (fused FP32 MLS fit + MHD RHS)",
                 "launch_ms": fit_avg, "launches": len(fit_ms),
                 "timed_on": "eager pass over the timed steps (CUDA events on the launching stream)"
@@ -560,10 +589,24 @@ def run_ours(args):
     cpu = None
     err = None
     if rank == 0 and world == 1 and not args.no_oracle:
-        rate, cpu, q, o = oracle_leg(w, args.sample)
-        err = {"fp32_mixed": float(kind_err(d32.cpu().numpy()[:, q], o).max()),
-               "fp64": float(kind_err(d64.cpu().numpy()[:, q], o).max()),
-               "metric": "max over fields of max_i|a-o| / max_i|o| on the oracle sample"}
+        rate, cpu, q, o, nbq = oracle_leg(w, args.sample)
+        import oracle
+        go, ho, _ = oracle.mls_derivs(oracle.box_of(w), w.pos, w.lam, w.U, nbq, q, gamma=w.gamma)
+        sc = rhs_term_scales(w.U[:, q], go, ho, w.gamma)
+        err = {"metric": "time derivatives: per field max_i|a-o| over the field's term scale "
+                         "(largest magnitude of the terms of its equation); derivatives: per "
+                         "field and kind max_i|a-o| / max_i|o| (floor 1e-2 of the largest "
+                         "field); on the oracle sample",
+               "sample": int(len(q))}
+        for name, prm_, d in (("fp32_mixed", mixed, d32), ("fp64", fp64, d64)):
+            e_rhs = np.abs(d.cpu().numpy()[:, q] - o).max(axis=1) / np.where(sc > 0, sc, 1.0)
+            gg, hh, _ = phb.mls_derivs(plan, prm_, pos0, lam, U0)
+            e_g = deriv_err(gg.cpu().numpy()[:, :, q], go)
+            e_h = deriv_err(hh.cpu().numpy()[:, :, q], ho)
+            err[name] = float(e_rhs.max())
+            err[name + "_detail"] = {"rhs": e_rhs.tolist(), "grad": e_g.tolist(),
+                                     "hess": e_h.tolist(),
+                                     "derivs_max": float(max(e_g.max(), e_h.max()))}
 
     fst = torch.empty(n, dtype=torch.int32, device=dev)
     phb.build_neighbors(plan, pos0, lam)

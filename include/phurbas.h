@@ -63,6 +63,7 @@ typedef enum {
 #define PHB_FLAG_NONFINITE 0x08
 #define PHB_FLAG_TIMEOUT 0x10
 #define PHB_FLAG_LAMBDA_RANGE 0x20 /* a lambda outside the plan's [lambda_min, lambda_max] */
+#define PHB_FLAG_BAD_INDEX 0x40    /* an active-subset index outside [0, n) (it was skipped) */
 
 /* Periodic or open box [lo, lo + len) per axis.  On a periodic axis offsets
  * use the minimum image d - len * nearbyint(d / len).  Particles on an open
@@ -106,7 +107,7 @@ typedef struct {
   int32_t schedule;      /* fused fit: 0 = one CTA per tile in cell order; 1 = persistent CTAs
                             taking tiles from a queue in descending-cost order */
   int32_t ell_width;     /* neighbour search: list entries kept per particle in the
-                            single-pass scratch (0 = default 64; longer lists are
+                            single-pass scratch (0 = default 128; longer lists are
                             searched again); 8 .. 1024 */
   /* filled by phb_plan_init */
   double cell[3];        /* cell edge per axis */
@@ -199,6 +200,38 @@ phb_status phb_mhd_rhs(const phb_plan* plan, const phb_params* params, const dou
 phb_status phb_pc_step(const phb_plan* plan, const phb_params* params, double* pos,
                        const double* lambda, double* U, double dt, void* ws, size_t ws_bytes,
                        int32_t* status_word, phb_stream_t stream);
+
+/* Right-hand side of an active subset only (the individual time steps of
+ * Sec. 2 / Sec. 2.1: at a substep only the particles whose step ends there
+ * are evaluated).  Same result as phb_mhd_rhs at the listed particles, with
+ * the lists of the last build; dudt [8][n] and fit_status [n] (may be NULL)
+ * are written at the listed caller indices only.  active: device int32
+ * [n_active] caller indices (duplicates are evaluated once; an index outside
+ * [0, n) is skipped and sets PHB_FLAG_BAD_INDEX).  The FP32-mixed path reads
+ * neighbours through the unstaged (global-memory) form of the fused fit; the
+ * FP64 path is the same kernel as the full evaluation.  Every particle's
+ * pos, lambda and U are still read (neighbours of active particles). */
+phb_status phb_mhd_rhs_active(const phb_plan* plan, const phb_params* params, const double* pos,
+                              const double* lambda, const double* U, const int32_t* active,
+                              int64_t n_active, void* ws, size_t ws_bytes, double* dudt,
+                              int32_t* fit_status, int32_t* status_word, phb_stream_t stream);
+
+/* Individual power-of-two time-step levels (Sec. 2: steps independent of
+ * the bulk velocity, spatial variation limited; Sec. 2.1: steps rounded
+ * down to powers of two, the restriction sent from a particle to its
+ * neighbours).  With the lists of the last build (filtered exactly at r_f),
+ * for every particle: c_i = sqrt((gamma P_i + |B_i|^2) / rho_i), P = (gamma - 1)
+ * sigma, dt_i = cfl lambda_i / c_i (FP64, no contraction); unlimited level
+ * L0_i = the smallest L in [0, max_level] with dt_max / 2^L <= dt_i (or
+ * max_level); then one limiter pass L_j = max(L0_j, max over i with j in N(i)
+ * of L0_i - 1).  A particle of level L advances with dt_max / 2^L.
+ * levels: device int32 [n], caller order.  dt_max > 0, cfl > 0,
+ * 0 <= max_level <= 30, else PHB_ERR_INVALID_ARG; a non-positive density or
+ * squared speed sets PHB_FLAG_NONFINITE. */
+phb_status phb_timestep_levels(const phb_plan* plan, const phb_params* params, const double* pos,
+                               const double* lambda, const double* U, double cfl, double dt_max,
+                               int32_t max_level, void* ws, size_t ws_bytes, int32_t* levels,
+                               int32_t* status_word, phb_stream_t stream);
 
 /* Reverse-mode derivative of the fused fit + right-hand side (not in the
  * paper): given gbar = dL/d(dudt) [8][n], returns Ubar = dL/dU [8][n] and

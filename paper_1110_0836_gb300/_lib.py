@@ -15,19 +15,20 @@ PHB_OK, PHB_ERR_INVALID_ARG, PHB_ERR_WORKSPACE, PHB_ERR_CUDA, PHB_ERR_CAPACITY =
 PHB_ERR_SKIN, PHB_WARN_FIT, PHB_ERR_TIMEOUT, PHB_ERR_NONFINITE = 5, 6, 7, 8
 FLAG_CAPACITY, FLAG_SKIN, FLAG_FIT_SINGULAR, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_LAMBDA_RANGE = (
     0x01, 0x02, 0x04, 0x08, 0x10, 0x20)
+FLAG_BAD_INDEX = 0x40
 PHB_FP64, PHB_FP32_MIXED = 0, 1
 # ws_off index where the workspace part shared by neighbour build, fit and RHS ends
 # (position of R_END_COMMON in the library's region enumeration)
-WS_END_COMMON = 33
+WS_END_COMMON = 36
 # first and last adjoint regions (R_ADJ_EDGE, R_ADJ_SELF; the latter holds 11 doubles per particle)
-WS_ADJ_EDGE, WS_ADJ_SELF = 27, 32
+WS_ADJ_EDGE, WS_ADJ_SELF = 30, 35
 
 EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_check",
            "phb_build_neighbors", "phb_export_neighbors", "phb_neighbor_total", "phb_mls_derivs",
            "phb_mhd_rhs", "phb_pc_step", "phb_rhs_adjoint", "phb_fma_peak", "phb_launch_count",
            "phb_trace_start", "phb_trace_stop", "phb_trace_read", "phb_workspace_stats", "phb_mhd_rhs_noalloc",
            "phb_noalloc_scratch_bytes", "phb_adjoint_record_bytes", "phb_adjoint_record",
-           "phb_rhs_adjoint_stored"]
+           "phb_rhs_adjoint_stored", "phb_mhd_rhs_active", "phb_timestep_levels"]
 
 
 class Box(C.Structure):
@@ -89,6 +90,12 @@ def lib(path: str | None = None) -> C.CDLL:
                               _vp]
     L.phb_rhs_adjoint.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp, _vp,
                                   _vp, _vp]
+    L.phb_mhd_rhs_active.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, C.c_int64, _vp,
+                                     C.c_size_t, _vp, _vp, _vp, _vp]
+    L.phb_mhd_rhs_active.restype = C.c_int
+    L.phb_timestep_levels.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, C.c_double, C.c_double,
+                                      C.c_int32, _vp, C.c_size_t, _vp, _vp, _vp]
+    L.phb_timestep_levels.restype = C.c_int
     L.phb_adjoint_record_bytes.argtypes = [P(Plan)]
     L.phb_adjoint_record_bytes.restype = C.c_size_t
     L.phb_adjoint_record.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, C.c_size_t, _vp,

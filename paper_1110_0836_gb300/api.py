@@ -234,6 +234,54 @@ def rhs_adjoint(plan: Plan, params: Params, pos, lam, U, gbar, Ubar=None, xbar=N
     return Ubar, xbar
 
 
+def mhd_rhs_active(plan: Plan, params: Params, pos, lam, U, active, out=None, fit_status=None):
+    """dU/dt at the caller indices in `active` (int32 CUDA tensor) only
+    (phb_mhd_rhs_active), with the lists of the last build.  out [8, n] is
+    written at those columns; other columns are left as they are."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    if not isinstance(active, torch.Tensor) or not active.is_cuda or active.dtype != torch.int32 \
+            or active.dim() != 1 or not active.is_contiguous():
+        raise ValueError("active must be a contiguous 1-D int32 CUDA tensor")
+    if out is None:
+        out = torch.zeros((8, n), dtype=torch.float64, device=plan.device)
+    _need(out, (8, n), "out")
+    if fit_status is not None:
+        _need(fit_status, (n,), "fit_status", torch.int32)
+    pc = params.c()
+    check(_lib.lib().phb_mhd_rhs_active(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                                        _ptr(active), active.numel(), _ptr(plan.ws), plan.ws.numel(),
+                                        _ptr(out), _ptr(fit_status), _ptr(plan.status_word),
+                                        _stream()), "phb_mhd_rhs_active")
+    return out
+
+
+def timestep_levels(plan: Plan, params: Params, pos, lam, U, cfl: float, dt_max: float,
+                    max_level: int = 20, out=None):
+    """Individual power-of-two time-step levels with the spatial limiter
+    (phb_timestep_levels), int32 [n] caller order, from the lists of the last
+    build.  A particle of level L advances with dt_max / 2**L."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=plan.device)
+    _need(out, (n,), "out", torch.int32)
+    pc = params.c()
+    check(_lib.lib().phb_timestep_levels(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                                         float(cfl), float(dt_max), int(max_level), _ptr(plan.ws),
+                                         plan.ws.numel(), _ptr(out), _ptr(plan.status_word),
+                                         _stream()), "phb_timestep_levels")
+    return out
+
+
+def active_at(levels: torch.Tensor, substep: int, max_level: int) -> torch.Tensor:
+    """Caller indices whose step ends at `substep` of the finest level
+    (dt_max / 2**max_level units) in the binary block scheme: level L is
+    active when substep is a multiple of 2**(max_level - L)."""
+    period = torch.bitwise_left_shift(torch.ones_like(levels), max_level - levels)
+    return torch.nonzero(substep % period == 0).flatten().to(torch.int32)
+
+
 def adjoint_record(plan: Plan, params: Params, pos, lam, U, record=None):
     """Per-particle FP64 factorisations and coefficients for phb_rhs_adjoint_stored
     (phb_adjoint_record), with the lists of the last build.  Returns the record

@@ -22,7 +22,7 @@ constexpr int kT = 64;
 constexpr int kStride = kNM + kNT + kNF * kNB + 1;  // doubles per thread; odd stride avoids bank conflicts
 
 template <FitMode MODE>
-__global__ void __launch_bounds__(kT) k_fit_fp64(const FitArgs a, const int32_t* list,
+__global__ void __launch_bounds__(kT) k_fit_fp64(const FitArgs a, int routed, const int32_t* list,
                                                  const int32_t* list_len) {
   extern __shared__ double sm[];
   double* my = sm + threadIdx.x * kStride;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kT) k_fit_fp64(const FitArgs a, const int32_t*
       refine = !singular && rmax > 1e4 * rmin;
     }
     const int dst = a.perm_out ? a.perm_out[s] : s;
-    if (a.fit_status) a.fit_status[dst] = singular ? 1 : (list ? 2 : 0);
+    if (a.fit_status) a.fit_status[dst] = singular ? 1 : (routed ? 2 : 0);
     if (singular) raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
     const double il = inv_l, il2 = inv_l * inv_l;
     MhdDerivs<double> D;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kT) k_fit_fp64(const FitArgs a, const int32_t*
 }  // namespace
 
 cudaError_t launch_fit_fp64(const FitArgs& a, FitMode mode, const int32_t* list,
-                            const int32_t* list_len, cudaStream_t st) {
+                            const int32_t* list_len, cudaStream_t st, bool routed) {
   const size_t smem = size_t(kStride) * kT * sizeof(double);
   unsigned blocks = list ? static_cast<unsigned>(num_sms() * 2)
                          : static_cast<unsigned>((a.n + kT - 1) / kT);
@@ -174,14 +174,14 @@ cudaError_t launch_fit_fp64(const FitArgs& a, FitMode mode, const int32_t* list,
     cudaFuncSetAttribute(k_fit_fp64<FitMode::kDerivs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     const int tr = trace_begin(list ? 3 : 2, st);
-    k_fit_fp64<FitMode::kDerivs><<<blocks, kT, smem, st>>>(a, list, list_len);
+    k_fit_fp64<FitMode::kDerivs><<<blocks, kT, smem, st>>>(a, routed, list, list_len);
     note_launch();
     trace_end(tr, st);
   } else {
     cudaFuncSetAttribute(k_fit_fp64<FitMode::kRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     const int tr = trace_begin(list ? 3 : 2, st);
-    k_fit_fp64<FitMode::kRHS><<<blocks, kT, smem, st>>>(a, list, list_len);
+    k_fit_fp64<FitMode::kRHS><<<blocks, kT, smem, st>>>(a, routed, list, list_len);
     note_launch();
     trace_end(tr, st);
   }

@@ -46,31 +46,45 @@ struct Groups {
 
 // Neighbour data from the FP32 hi/lo records in global memory.
 // du (pass A) = (rho, sigma, Vx, Vy) differences; (pass B) = (Vz, Bx, By, Bz).
+// fetch_* issues a neighbour's loads, decode_* turns them into offsets and
+// field differences, so that the loop can fetch one neighbour ahead.
 struct GlobalSrc {
   const float4* rec;
   const int32_t* idx;
   float4 o[6];
   Per32 P;
+  struct Raw {
+    float4 p0, p1, h, l;
+  };
+  using RawA = Raw;
+  using RawB = Raw;
   __device__ __forceinline__ int index(int64_t e) const { return idx[e]; }
-  __device__ __forceinline__ void pass_a(int t, float& dx, float& dy, float& dz, float (&du)[4]) const {
-    const float4 p0 = rec[6 * t], p1 = rec[6 * t + 1], fh = rec[6 * t + 2], fl = rec[6 * t + 3];
-    dx = mi_diff32(p0.x, p1.x, o[0].x, o[1].x, P.len_h[0], P.len_l[0], P.inv_len[0]);
-    dy = mi_diff32(p0.y, p1.y, o[0].y, o[1].y, P.len_h[1], P.len_l[1], P.inv_len[1]);
-    dz = mi_diff32(p0.z, p1.z, o[0].z, o[1].z, P.len_h[2], P.len_l[2], P.inv_len[2]);
-    du[0] = hl(fh.x, fl.x, o[2].x, o[3].x);
-    du[1] = hl(fh.y, fl.y, o[2].y, o[3].y);
-    du[2] = hl(fh.z, fl.z, o[2].z, o[3].z);
-    du[3] = hl(fh.w, fl.w, o[2].w, o[3].w);
+  __device__ __forceinline__ Raw fetch_a(int t) const {
+    return Raw{rec[6 * t], rec[6 * t + 1], rec[6 * t + 2], rec[6 * t + 3]};
   }
-  __device__ __forceinline__ void pass_b(int t, float& dx, float& dy, float& dz, float (&du)[4]) const {
-    const float4 p0 = rec[6 * t], p1 = rec[6 * t + 1], gh = rec[6 * t + 4], gl = rec[6 * t + 5];
-    dx = mi_diff32(p0.x, p1.x, o[0].x, o[1].x, P.len_h[0], P.len_l[0], P.inv_len[0]);
-    dy = mi_diff32(p0.y, p1.y, o[0].y, o[1].y, P.len_h[1], P.len_l[1], P.inv_len[1]);
-    dz = mi_diff32(p0.z, p1.z, o[0].z, o[1].z, P.len_h[2], P.len_l[2], P.inv_len[2]);
-    du[0] = hl(gh.x, gl.x, o[4].x, o[5].x);
-    du[1] = hl(gh.y, gl.y, o[4].y, o[5].y);
-    du[2] = hl(gh.z, gl.z, o[4].z, o[5].z);
-    du[3] = hl(gh.w, gl.w, o[4].w, o[5].w);
+  __device__ __forceinline__ Raw fetch_b(int t) const {
+    return Raw{rec[6 * t], rec[6 * t + 1], rec[6 * t + 4], rec[6 * t + 5]};
+  }
+  __device__ __forceinline__ void offs(const Raw& r, float& dx, float& dy, float& dz) const {
+    dx = mi_diff32(r.p0.x, r.p1.x, o[0].x, o[1].x, P.len_h[0], P.len_l[0], P.inv_len[0]);
+    dy = mi_diff32(r.p0.y, r.p1.y, o[0].y, o[1].y, P.len_h[1], P.len_l[1], P.inv_len[1]);
+    dz = mi_diff32(r.p0.z, r.p1.z, o[0].z, o[1].z, P.len_h[2], P.len_l[2], P.inv_len[2]);
+  }
+  __device__ __forceinline__ void decode_a(const Raw& r, float& dx, float& dy, float& dz,
+                                           float (&du)[4]) const {
+    offs(r, dx, dy, dz);
+    du[0] = hl(r.h.x, r.l.x, o[2].x, o[3].x);
+    du[1] = hl(r.h.y, r.l.y, o[2].y, o[3].y);
+    du[2] = hl(r.h.z, r.l.z, o[2].z, o[3].z);
+    du[3] = hl(r.h.w, r.l.w, o[2].w, o[3].w);
+  }
+  __device__ __forceinline__ void decode_b(const Raw& r, float& dx, float& dy, float& dz,
+                                           float (&du)[4]) const {
+    offs(r, dx, dy, dz);
+    du[0] = hl(r.h.x, r.l.x, o[4].x, o[5].x);
+    du[1] = hl(r.h.y, r.l.y, o[4].y, o[5].y);
+    du[2] = hl(r.h.z, r.l.z, o[4].z, o[5].z);
+    du[3] = hl(r.h.w, r.l.w, o[4].w, o[5].w);
   }
 };
 
@@ -81,6 +95,12 @@ struct StagedSrc {
   const uint16_t* lidx;
   float4 me0, me1, me2;
   float len[3], inv_len[3];
+  struct RawA {
+    float4 r0, r1;
+  };
+  struct RawB {
+    float4 r0, r1, r2;
+  };
   __device__ __forceinline__ void offs(float4 r0, float& dx, float& dy, float& dz) const {
     // relative offsets are minimum images of size <= len/2; one more wrap
     // keeps the difference a minimum image too (exact when no wrap occurs)
@@ -90,27 +110,35 @@ struct StagedSrc {
     dz = fmaf(-len[2], rintf(az * inv_len[2]), az);
   }
   __device__ __forceinline__ int index(int64_t e) const { return lidx[e]; }
-  __device__ __forceinline__ void pass_a(int l, float& dx, float& dy, float& dz, float (&du)[4]) const {
-    const float4 r0 = stage[3 * l], r1 = stage[3 * l + 1];
-    offs(r0, dx, dy, dz);
-    du[0] = r1.w - me1.w;
-    du[1] = r0.w - me0.w;
-    du[2] = r1.x - me1.x;
-    du[3] = r1.y - me1.y;
+  __device__ __forceinline__ RawA fetch_a(int l) const { return RawA{stage[3 * l], stage[3 * l + 1]}; }
+  __device__ __forceinline__ RawB fetch_b(int l) const {
+    return RawB{stage[3 * l], stage[3 * l + 1], stage[3 * l + 2]};
   }
-  __device__ __forceinline__ void pass_b(int l, float& dx, float& dy, float& dz, float (&du)[4]) const {
-    const float4 r0 = stage[3 * l], r1 = stage[3 * l + 1], r2 = stage[3 * l + 2];
-    offs(r0, dx, dy, dz);
-    du[0] = r1.z - me1.z;
-    du[1] = r2.x - me2.x;
-    du[2] = r2.y - me2.y;
-    du[3] = r2.z - me2.z;
+  __device__ __forceinline__ void decode_a(const RawA& r, float& dx, float& dy, float& dz,
+                                           float (&du)[4]) const {
+    offs(r.r0, dx, dy, dz);
+    du[0] = r.r1.w - me1.w;
+    du[1] = r.r0.w - me0.w;
+    du[2] = r.r1.x - me1.x;
+    du[3] = r.r1.y - me1.y;
+  }
+  __device__ __forceinline__ void decode_b(const RawB& r, float& dx, float& dy, float& dz,
+                                           float (&du)[4]) const {
+    offs(r.r0, dx, dy, dz);
+    du[0] = r.r1.z - me1.z;
+    du[1] = r.r2.x - me2.x;
+    du[2] = r.r2.y - me2.y;
+    du[3] = r.r2.z - me2.z;
   }
 };
 
 // Both accumulation passes of one particle.  Pass A's right-hand sides are
 // parked in shared memory column `col` ([slot][T] layout); the moments and
-// pass B's right-hand sides are returned in registers.
+// pass B's right-hand sides are returned in registers.  The list index of
+// the next neighbour is loaded one iteration ahead (fetching its data ahead
+// as well measured slower: the extra registers cost more than the hidden
+// shared-memory latency).  Pass B accumulates sum_j p_k (w dU_j) with the weight folded into the field
+// difference (the moments are complete after pass A).
 template <FitMode MODE, int T, class Src>
 __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t end, float inv_l,
                                           float inv_rf2, bool unweighted, float* park, int col,
@@ -125,12 +153,12 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
     for (int f = 0; f < G::NA; ++f)
 #pragma unroll
       for (int k = 0; k < kNB; ++k) bA[f][k] = 0.f;
-    int nxt = beg < end ? src.index(beg) : 0;  // neighbour handle, loaded one ahead
+    int nxt = beg < end ? src.index(beg) : 0;
     for (int64_t e = beg; e < end; ++e) {
       const int cur = nxt;
       if (e + 1 < end) nxt = src.index(e + 1);
       float dx, dy, dz, du[4];
-      src.pass_a(cur, dx, dy, dz, du);
+      src.decode_a(src.fetch_a(cur), dx, dy, dz, du);
       const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
       const bool inside = s2 < 1.f;
       const float sw = 1.f - s2;
@@ -158,16 +186,14 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
     const int cur = nxt;
     if (e + 1 < end) nxt = src.index(e + 1);
     float dx, dy, dz, du[4];
-    src.pass_b(cur, dx, dy, dz, du);
+    src.decode_b(src.fetch_b(cur), dx, dy, dz, du);
     const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
     const float sw = 1.f - s2;
     const float wt = s2 < 1.f ? (unweighted ? 1.f : sw * sw) : 0.f;
-    float qg[kNB], wq[kNB + 1];
-    mls_monomials(dx * inv_l, dy * inv_l, dz * inv_l, wt, qg, wq);
-    mls_accum_rhs(wq, du[0], bB[0]);
-    mls_accum_rhs(wq, du[1], bB[1]);
-    mls_accum_rhs(wq, du[2], bB[2]);
-    mls_accum_rhs(wq, du[3], bB[3]);
+    float qg[kNB];
+    mls_basis(dx * inv_l, dy * inv_l, dz * inv_l, qg);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) mls_accum_rhs_basis(qg, wt * du[f], bB[f]);
   }
   return cnt;
 }
@@ -176,78 +202,76 @@ struct TileArgs {
   const int2* tplan;      // per tile: (staged particles, 1 = not staged)
   const int32_t* tslot;   // per tile: slot of every staged index (stage_cap stride)
   const uint16_t* lself;  // per slot: its own staged index
+  const uint8_t* tmap;    // per tile: thread -> tile particle (longest list first)
   const uint16_t* lidx;
   int32_t* fallback_count;
   const int32_t* order;   // tile order (persistent schedule)
   int32_t* queue_head;    // persistent tile-queue counter (zeroed before the launch)
   int32_t ntiles;
+  const int32_t* list;      // active subset: slots (ascending), or null for all particles
+  const int32_t* list_len;  // device count of the active subset
 };
 
 // Shared memory of one CTA besides the dynamic park/staging region.
 template <int T>
 struct FitShared {
-  int cnt[T];     // list length of each tile particle
-  int map[T];     // thread -> tile particle, longest lists first
   int tile;       // persistent schedule: tile taken from the queue
 };
 
 // One tile: stage its neighbourhood, accumulate, solve, write outputs.  All
 // T threads call it (it contains block barriers).  Threads are assigned to
-// the tile's particles in descending list length so that the lanes of a warp
-// run loops of similar length.
+// the tile's particles in descending list length (map recorded by the
+// neighbour build) so that the lanes of a warp run loops of similar length.
 template <FitMode MODE, int T>
 __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const TileArgs& ta,
                                          int tile, float* park, float4* stage, FitShared<T>& sh) {
   using G = Groups<MODE>;
   const int n = a.n;
-  const int s0 = tile * T;
-  const int cnt_tile = min(T, n - s0);
   const int tid = threadIdx.x;
   const float4* rec = reinterpret_cast<const float4*>(a.rec);
-
-  // thread -> particle map, descending list length (ties: slot order)
-  {
-    int len = -1;
-    if (tid < cnt_tile) {
-      const int64_t e1 = a.off[s0 + tid + 1] < a.g.capacity ? a.off[s0 + tid + 1] : a.g.capacity;
-      const int64_t e0 = a.off[s0 + tid] < a.g.capacity ? a.off[s0 + tid] : a.g.capacity;
-      len = static_cast<int>(e1 - e0);
-    }
-    sh.cnt[tid] = len;
-    __syncthreads();
-    int rank = 0;
-    for (int j = 0; j < T; ++j) {
-      const int c = sh.cnt[j];
-      rank += (c > len || (c == len && j < tid)) ? 1 : 0;
-    }
-    sh.map[rank] = tid;
-    __syncthreads();
-  }
-  const int mine = sh.map[tid];
+  // an active subset runs in chunks of T listed slots through the unstaged path
+  const bool listed = ta.list != nullptr;
+  const int s0 = tile * T;
+  const int cnt_tile = min(T, (listed ? *ta.list_len : n) - s0);
+  const int mine = listed ? tid : ta.tmap[static_cast<int64_t>(tile) * T + tid];
   const bool active = mine < cnt_tile;
-  const int s = s0 + mine;
+  const int s = listed ? (active ? ta.list[s0 + mine] : 0) : s0 + mine;
 
   // the neighbourhood planned by the neighbour build: one gather per staged record
-  const int2 tp = ta.tplan[tile];
+  const int2 tp = listed ? make_int2(0, 1) : ta.tplan[tile];
   const bool fb = tp.y != 0;
   if (!fb) {
     const float4 rh = rec[6 * s0], rl = rec[6 * s0 + 1];
     const float4 fh = rec[6 * s0 + 2], fl = rec[6 * s0 + 3], gh = rec[6 * s0 + 4], gl = rec[6 * s0 + 5];
     const int32_t* slots = ta.tslot + static_cast<int64_t>(tile) * a.g.stage_cap;
-    for (int l = tid; l < tp.x; l += T) {
-      const float4* r = rec + 6 * slots[l];
-      const float4 p0 = r[0], p1 = r[1], f0 = r[2], f1 = r[3], g0 = r[4], g1 = r[5];
-      float4* d = stage + 3 * l;
-      d[0] = make_float4(mi_diff32(p0.x, p1.x, rh.x, rl.x, P.len_h[0], P.len_l[0], P.inv_len[0]),
-                         mi_diff32(p0.y, p1.y, rh.y, rl.y, P.len_h[1], P.len_l[1], P.inv_len[1]),
-                         mi_diff32(p0.z, p1.z, rh.z, rl.z, P.len_h[2], P.len_l[2], P.inv_len[2]),
-                         hl(f0.y, f1.y, fh.y, fl.y));
-      d[1] = make_float4(hl(f0.z, f1.z, fh.z, fl.z), hl(f0.w, f1.w, fh.w, fl.w),
-                         hl(g0.x, g1.x, gh.x, gl.x), hl(f0.x, f1.x, fh.x, fl.x));
-      d[2] = make_float4(hl(g0.y, g1.y, gh.y, gl.y), hl(g0.z, g1.z, gh.z, gl.z),
-                         hl(g0.w, g1.w, gh.w, gl.w), 0.f);
+    // four records per thread in flight: slots first, then all their loads
+    constexpr int kB = 4;
+    for (int l0 = tid; l0 < tp.x; l0 += kB * T) {
+      int sl[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) sl[u] = l0 + u * T < tp.x ? slots[l0 + u * T] : -1;
+      float4 v[kB][6];
+#pragma unroll
+      for (int u = 0; u < kB; ++u)
+        if (sl[u] >= 0)
+#pragma unroll
+          for (int k = 0; k < 6; ++k) v[u][k] = rec[6 * sl[u] + k];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        if (sl[u] < 0) continue;
+        const float4 p0 = v[u][0], p1 = v[u][1], f0 = v[u][2], f1 = v[u][3], g0 = v[u][4], g1 = v[u][5];
+        float4* d = stage + 3 * (l0 + u * T);
+        d[0] = make_float4(mi_diff32(p0.x, p1.x, rh.x, rl.x, P.len_h[0], P.len_l[0], P.inv_len[0]),
+                           mi_diff32(p0.y, p1.y, rh.y, rl.y, P.len_h[1], P.len_l[1], P.inv_len[1]),
+                           mi_diff32(p0.z, p1.z, rh.z, rl.z, P.len_h[2], P.len_l[2], P.inv_len[2]),
+                           hl(f0.y, f1.y, fh.y, fl.y));
+        d[1] = make_float4(hl(f0.z, f1.z, fh.z, fl.z), hl(f0.w, f1.w, fh.w, fl.w),
+                           hl(g0.x, g1.x, gh.x, gl.x), hl(f0.x, f1.x, fh.x, fl.x));
+        d[2] = make_float4(hl(g0.y, g1.y, gh.y, gl.y), hl(g0.z, g1.z, gh.z, gl.z),
+                           hl(g0.w, g1.w, gh.w, gl.w), 0.f);
+      }
     }
-  } else if (tid == 0) {
+  } else if (tid == 0 && !listed) {
     atomicAdd(ta.fallback_count, 1);
   }
   __syncthreads();
@@ -426,15 +450,18 @@ Per32 make_per32(const Grid& g) {
 }
 
 template <FitMode MODE, int T>
-cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, cudaStream_t st) {
+cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, int64_t list_cap,
+                     cudaStream_t st) {
   using G = Groups<MODE>;
   const size_t park_a = size_t(G::NA) * kNB * T * sizeof(float);
   const size_t staged = size_t(a.g.stage_cap) * 3 * sizeof(float4);
   const size_t park_all = size_t(G::NF) * kNB * T * sizeof(float);
   const size_t smem = park_a + staged > park_all ? park_a + staged : park_all;
-  const unsigned tiles = static_cast<unsigned>((a.n + T - 1) / T);
+  const int64_t units = ta.list ? list_cap : a.n;
+  const unsigned tiles = static_cast<unsigned>((units + T - 1) / T);
   cudaError_t e;
-  if (a.g.schedule == 1) {
+  if (units == 0) return cudaGetLastError();
+  if (a.g.schedule == 1 && !ta.list) {
     cudaFuncSetAttribute(k_fit_mixed_persistent<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     int per_sm = 0;
@@ -461,16 +488,18 @@ cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, cudaS
 }  // namespace
 
 cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int2* tplan, const int32_t* tslot,
-                             const uint16_t* lself, const uint16_t* lidx, int32_t* fallback_count,
-                             const int32_t* order, int32_t* queue_head, cudaStream_t st) {
+                             const uint16_t* lself, const uint8_t* tmap, const uint16_t* lidx,
+                             int32_t* fallback_count, const int32_t* order, int32_t* queue_head,
+                             const int32_t* list, const int32_t* list_len, int64_t list_cap,
+                             cudaStream_t st) {
   const Per32 P = make_per32(a.g);
-  const TileArgs ta{tplan, tslot, lself, lidx, fallback_count, order, queue_head,
-                    static_cast<int32_t>((a.n + a.g.tile - 1) / a.g.tile)};
+  const TileArgs ta{tplan, tslot, lself, tmap, lidx, fallback_count, order, queue_head,
+                    static_cast<int32_t>((a.n + a.g.tile - 1) / a.g.tile), list, list_len};
   if (mode == FitMode::kDerivs)
-    return a.g.tile == 64 ? launch_t<FitMode::kDerivs, 64>(a, P, ta, st)
-                          : launch_t<FitMode::kDerivs, 128>(a, P, ta, st);
-  return a.g.tile == 64 ? launch_t<FitMode::kRHS, 64>(a, P, ta, st)
-                        : launch_t<FitMode::kRHS, 128>(a, P, ta, st);
+    return a.g.tile == 64 ? launch_t<FitMode::kDerivs, 64>(a, P, ta, list_cap, st)
+                          : launch_t<FitMode::kDerivs, 128>(a, P, ta, list_cap, st);
+  return a.g.tile == 64 ? launch_t<FitMode::kRHS, 64>(a, P, ta, list_cap, st)
+                        : launch_t<FitMode::kRHS, 128>(a, P, ta, list_cap, st);
 }
 
 }  // namespace phb

@@ -41,6 +41,9 @@ enum Region {
   R_TPLAN,       // int2 [ntiles] (staged particles, 1 = not staged) of each tile's neighbourhood
   R_TSLOT,       // int32 [ntiles][stage_cap] slot of every staged index of each tile
   R_LSELF,       // uint16 [n] each slot's own staged index within its tile
+  R_TMAP,        // uint8 [ntiles][tile] fit thread -> tile particle, longest list first
+  R_ALIST,       // int32 [n+64] slots of an active subset (ascending)
+  R_AFLAG,       // int32 [n+1]  active-subset marks / their exclusive scan
   R_QUEUE,       // int32 [n]    slots routed to FP64
   R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
@@ -258,12 +261,17 @@ struct FitArgs {
   int32_t* status_word;
 };
 
+// Fused FP32-mixed fit over all slots (list == null, staged tiles) or over
+// the slots list[0 .. *list_len) (at most list_cap; unstaged path).
 cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int2* tplan, const int32_t* tslot,
-                             const uint16_t* lself, const uint16_t* lidx, int32_t* fallback_count,
-                             const int32_t* order, int32_t* queue_head, cudaStream_t st);
-// FP64 fused fit over all slots (list == null) or over list[0 .. *list_len).
+                             const uint16_t* lself, const uint8_t* tmap, const uint16_t* lidx,
+                             int32_t* fallback_count, const int32_t* order, int32_t* queue_head,
+                             const int32_t* list, const int32_t* list_len, int64_t list_cap,
+                             cudaStream_t st);
+// FP64 fused fit over all slots (list == null) or over list[0 .. *list_len);
+// routed: the list is the FP32-mixed kernel's route queue (fit status 2).
 cudaError_t launch_fit_fp64(const FitArgs& a, FitMode mode, const int32_t* list,
-                            const int32_t* list_len, cudaStream_t st);
+                            const int32_t* list_len, cudaStream_t st, bool routed = false);
 int num_sms();
 
 // Launch bookkeeping (measurement helpers, see include/phurbas_bench.h).
@@ -273,9 +281,12 @@ int trace_begin(int kernel_id, cudaStream_t st);
 void trace_end(int slot, cudaStream_t st);
 
 // Run the fused fit over the slot-order state already in the workspace:
-// mixed kernel + FP64 queue, or the FP64 kernel alone.
+// mixed kernel + FP64 queue, or the FP64 kernel alone; over all slots, or
+// over list[0 .. *list_len) (list_cap entries at most) when list is given.
 cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMode mode,
                     const int32_t* perm_out, double* dudt, double* grad, double* hess,
-                    int32_t* fit_status, int32_t* status_word, cudaStream_t st);
+                    int32_t* fit_status, int32_t* status_word, cudaStream_t st,
+                    const int32_t* list = nullptr, const int32_t* list_len = nullptr,
+                    int64_t list_cap = 0);
 
 }  // namespace phb

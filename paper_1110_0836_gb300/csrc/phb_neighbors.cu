@@ -196,28 +196,82 @@ __device__ __forceinline__ bool plain_axis(const Grid& g, int a, int c, const Re
 
 enum SearchOut { kCount = 0, kFillCsr = 1, kFillEll = 2 };
 
-// One particle's list: candidates from the cells within reach, looked up
-// through the linear (first slot, count) table, in cell order (x, y, z) and
-// slot order inside a cell.  kCount only counts; kFillCsr writes entries
+// Cell culling: the reach box of 2R+1 cells per axis is cut to the cells
+// that can hold a point within r of the particle.  With f the particle's
+// fractional position in its cell, the nearest point of the cell at offset i
+// is (i - f) cells away for i > 0, (-i - 1 + f) for i < 0 and 0 for i = 0.
+// Distances are taken with a margin of 1e-3 cells plus the screen margin, so
+// that only cells that cannot hold a neighbour are skipped; an axis whose
+// reach covers the whole periodic grid is not culled.
+struct Cull {
+  float f[3];      // fractional position in the cell, clamped to [0, 1]
+  float cell[3];   // cell edges
+  float rr;        // (r + margin)^2
+  bool on[3];      // axis culled
+};
+
+__device__ __forceinline__ float cull_d(const Cull& k, int a, int i) {
+  if (!k.on[a] || i == 0) return 0.f;
+  const float d = i > 0 ? i - k.f[a] : -i - 1 + k.f[a];
+  return d > 0.f ? d * k.cell[a] : 0.f;
+}
+
+__device__ __forceinline__ Cull make_cull(const Grid& g, const double* spos, int s, const int (&c)[3],
+                                          const Reach& qx, const Reach& qy, const Reach& qz, double r) {
+  Cull k;
+  const Reach* q[3] = {&qx, &qy, &qz};
+  double mc = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double u = (spos[a * g.n + s] - g.lo[a]) * g.inv_cell[a];
+    const double f = g.periodic[a] ? u - floor(u) : u - c[a];
+    k.f[a] = static_cast<float>(f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f));
+    k.cell[a] = static_cast<float>(g.cell[a]);
+    k.on[a] = !(g.periodic[a] && !q[a]->wrap);  // not the whole-axis reach
+    mc = g.cell[a] > mc ? g.cell[a] : mc;
+  }
+  const double rm = r + 1e-3 * mc + static_cast<double>(g.screen_margin);
+  k.rr = static_cast<float>(rm * rm);
+  return k;
+}
+
+// One particle's list: candidates from the culled cells within reach, looked
+// up through the linear (first slot, count) table, in cell order (x, y, z)
+// and slot order inside a cell.  kCount only counts; kFillCsr writes entries
 // [base, end) of the CSR lists; kFillEll writes the first g.ell entries to
 // the slot's row of the single-pass scratch.  Returns the exact count.
 template <int OUT, bool kWrap>
 __device__ int search_one(const Grid& g, const int2* __restrict__ clin, const float4* __restrict__ scr,
-                          const double* __restrict__ spos, const Screen& q, const int (&c)[3],
+                          const double* __restrict__ spos, const Screen& q, const Cull& cu,
                           const Reach& qx, const Reach& qy, const Reach& qz, int s, int64_t base,
                           int64_t end, int32_t* __restrict__ out) {
   const float4 me = scr[s];
+  const int Rx = qx.count / 2, Ry = qy.count / 2, Rz = qz.count / 2;
   int count = 0;
   for (int kx = 0; kx < qx.count; ++kx) {
     bool okx;
     const int cx = axis_cell(g, 0, qx, kx, okx);
     if (!okx) continue;
+    const float dx = cull_d(cu, 0, kx - Rx);
+    const float rx = cu.rr - dx * dx;
+    if (rx < 0.f) continue;
     for (int ky = 0; ky < qy.count; ++ky) {
       bool oky;
       const int cy = axis_cell(g, 1, qy, ky, oky);
       if (!oky) continue;
+      const float dy = cull_d(cu, 1, ky - Ry);
+      const float ry = rx - dy * dy;
+      if (ry < 0.f) continue;
+      // z cells within reach of this row
+      int z0 = 0, z1 = qz.count - 1;
+      if (cu.on[2]) {
+        const float sz = sqrtf(ry) / cu.cell[2];
+        const int hi = static_cast<int>(floorf(sz + cu.f[2]));
+        const int lo = -static_cast<int>(floorf(sz + 1.f - cu.f[2]));
+        z0 = max(0, lo + Rz);
+        z1 = min(qz.count - 1, hi + Rz);
+      }
       const int64_t row = (static_cast<int64_t>(cx) * g.ncell[1] + cy) * g.ncell[2];
-      for (int kz = 0; kz < qz.count; ++kz) {
+      for (int kz = z0; kz <= z1; ++kz) {
         bool okz;
         const int cz = axis_cell(g, 2, qz, kz, okz);
         if (!okz) continue;
@@ -249,14 +303,15 @@ __device__ int search_particle(const Grid& g, const int2* __restrict__ clin,
   const Reach qx = axis_reach(g, 0, c[0], r);
   const Reach qy = axis_reach(g, 1, c[1], r);
   const Reach qz = axis_reach(g, 2, c[2], r);
+  const Cull cu = make_cull(g, spos, s, c, qx, qy, qz, r);
   if (plain_axis(g, 0, c[0], qx) && plain_axis(g, 1, c[1], qy) && plain_axis(g, 2, c[2], qz))
-    return search_one<OUT, false>(g, clin, scr, spos, q, c, qx, qy, qz, s, base, end, out);
-  return search_one<OUT, true>(g, clin, scr, spos, q, c, qx, qy, qz, s, base, end, out);
+    return search_one<OUT, false>(g, clin, scr, spos, q, cu, qx, qy, qz, s, base, end, out);
+  return search_one<OUT, true>(g, clin, scr, spos, q, cu, qx, qy, qz, s, base, end, out);
 }
 
 // Single pass, thread per particle (slot order): exact list lengths and the
 // first g.ell entries of every list.
-__global__ void __launch_bounds__(kThreads) k_search_ell(Grid g, const int2* __restrict__ clin,
+__global__ void __launch_bounds__(kThreads, 3) k_search_ell(Grid g, const int2* __restrict__ clin,
                                                          const int32_t* __restrict__ cellc,
                                                          const float4* __restrict__ scr,
                                                          const double* __restrict__ spos,
@@ -287,8 +342,8 @@ __global__ void __launch_bounds__(T) k_compact(Grid g, const int2* __restrict__ 
                                                const int64_t* __restrict__ off,
                                                int32_t* __restrict__ idx, uint16_t* __restrict__ lidx,
                                                int2* __restrict__ tplan, int32_t* __restrict__ tslot,
-                                               uint16_t* __restrict__ lself, int32_t* fallback_count,
-                                               int32_t* status_word) {
+                                               uint16_t* __restrict__ lself, uint8_t* __restrict__ tmap,
+                                               int32_t* fallback_count, int32_t* status_word) {
   __shared__ TileShared ts;
   __shared__ unsigned bits[kBoxWords];
   __shared__ int wpre[kBoxWords];
@@ -296,6 +351,7 @@ __global__ void __launch_bounds__(T) k_compact(Grid g, const int2* __restrict__ 
   __shared__ int cstart[kMarkCap];
   __shared__ int warp_tmp[T / 32 + 1];
   __shared__ int64_t toff[T + 1];
+  __shared__ int tlen[T];
   const TileArrays tarr{bits, wpre, base, cstart, warp_tmp};
   const int n = g.n;
   const int tid = threadIdx.x;
@@ -303,6 +359,19 @@ __global__ void __launch_bounds__(T) k_compact(Grid g, const int2* __restrict__ 
   const int cnt = min(T, n - s0);
   for (int k = tid; k <= cnt; k += T) toff[k] = off[s0 + k];
   __syncthreads();
+  // fit thread -> tile particle in descending list length (ties: slot order),
+  // so that the lanes of a fit warp run loops of similar length
+  tlen[tid] = tid < cnt ? static_cast<int>(toff[tid + 1] - toff[tid]) : -1;
+  __syncthreads();
+  {
+    const int len = tlen[tid];
+    int rank = 0;
+    for (int j = 0; j < T; ++j) {
+      const int c = tlen[j];
+      rank += (c > len || (c == len && j < tid)) ? 1 : 0;
+    }
+    tmap[static_cast<int64_t>(blockIdx.x) * T + rank] = static_cast<uint8_t>(tid);
+  }
   if (tid < cnt) {
     const int s = s0 + tid;
     if (toff[tid + 1] > g.capacity) raise_flag(status_word, PHB_FLAG_CAPACITY);
@@ -461,12 +530,13 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   int2* tplan = region<int2>(p, ws, R_TPLAN);
   int32_t* tslot = region<int32_t>(p, ws, R_TSLOT);
   uint16_t* lself = region<uint16_t>(p, ws, R_LSELF);
+  uint8_t* tmap = region<uint8_t>(p, ws, R_TMAP);
   if (p->tile == 128)
     k_compact<128><<<tiles, 128, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, ell, off, idx, lidx,
-                                          tplan, tslot, lself, misc + 1, status_word);
+                                          tplan, tslot, lself, tmap, misc + 1, status_word);
   else
     k_compact<64><<<tiles, 64, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, ell, off, idx, lidx,
-                                        tplan, tslot, lself, misc + 1, status_word);
+                                        tplan, tslot, lself, tmap, misc + 1, status_word);
   note_launch();
   k_tile_order<<<1, 1024, 0, st>>>(n, p->tile, p->ntiles, p->nbr_capacity, off,
                                    region<int32_t>(p, ws, R_TORDER));

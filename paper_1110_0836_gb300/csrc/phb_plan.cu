@@ -220,7 +220,7 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   if (p->stage_cap < 64 || p->stage_cap > 2048) return PHB_ERR_INVALID_ARG;
   p->ntiles = static_cast<int32_t>((p->n + p->tile - 1) / p->tile);
   if (p->schedule != 0 && p->schedule != 1) return PHB_ERR_INVALID_ARG;
-  if (p->ell_width == 0) p->ell_width = 64;
+  if (p->ell_width == 0) p->ell_width = 128;
   if (p->ell_width < 8 || p->ell_width > 1024) return PHB_ERR_INVALID_ARG;
   // FP32 screen: bound of |d32 - d| per component is 2^-24 (2X + 3L); two
   // components' worth of safety on top, times sqrt(3) for the norm.
@@ -251,6 +251,9 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   sz[R_TPLAN] = size_t(p->ntiles) * 8;
   sz[R_TSLOT] = size_t(p->ntiles) * p->stage_cap * 4;
   sz[R_LSELF] = size_t(n) * 2;
+  sz[R_TMAP] = size_t(p->ntiles) * p->tile;
+  sz[R_ALIST] = size_t(n + 64) * 4;
+  sz[R_AFLAG] = size_t(n + 1) * 4;
   sz[R_QUEUE] = (n + 64) * 4;  // also the export's n+1 counts
   size_t off = 0;
   for (int r = R_MISC; r <= R_QUEUE; ++r) {
@@ -309,7 +312,7 @@ extern "C" const char* phb_status_string(int32_t s) {
 extern "C" phb_status phb_check(int32_t w) {
   if (w & PHB_FLAG_TIMEOUT) return PHB_ERR_TIMEOUT;
   if (w & PHB_FLAG_CAPACITY) return PHB_ERR_CAPACITY;
-  if (w & PHB_FLAG_LAMBDA_RANGE) return PHB_ERR_INVALID_ARG;
+  if (w & (PHB_FLAG_LAMBDA_RANGE | PHB_FLAG_BAD_INDEX)) return PHB_ERR_INVALID_ARG;
   if (w & PHB_FLAG_SKIN) return PHB_ERR_SKIN;
   if (w & PHB_FLAG_NONFINITE) return PHB_ERR_NONFINITE;
   if (w & PHB_FLAG_FIT_SINGULAR) return PHB_WARN_FIT;

@@ -35,6 +35,32 @@ __global__ void k_gather_all(Grid g, const int32_t* __restrict__ perm, const dou
   write_record(rec, s, x, u);
 }
 
+// Active subset: mark the slots of the listed caller indices, then list the
+// marked slots in ascending order from the exclusive scan of the marks.
+__global__ void k_mark_active(int n, int64_t m, const int32_t* __restrict__ active,
+                              const int32_t* __restrict__ inv, int32_t* __restrict__ mark,
+                              int32_t* status_word) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const int32_t i = active[k];
+  if (i < 0 || i >= n) {
+    raise_flag(status_word, PHB_FLAG_BAD_INDEX);
+    return;
+  }
+  mark[inv[i]] = 1;
+}
+
+__global__ void k_list_active(int n, const int32_t* __restrict__ scan, int32_t* __restrict__ list,
+                              int32_t* __restrict__ list_len) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > n) return;
+  if (s == n) {
+    *list_len = scan[n];
+    return;
+  }
+  if (scan[s + 1] != scan[s]) list[scan[s]] = s;
+}
+
 }  // namespace
 
 cudaError_t gather_sorted(const phb_plan* p, const Grid& g, const double* pos, const double* lam,
@@ -49,7 +75,8 @@ cudaError_t gather_sorted(const phb_plan* p, const Grid& g, const double* pos, c
 
 cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMode mode,
                     const int32_t* perm_out, double* dudt, double* grad, double* hess,
-                    int32_t* fit_status, int32_t* status_word, cudaStream_t st) {
+                    int32_t* fit_status, int32_t* status_word, cudaStream_t st,
+                    const int32_t* list, const int32_t* list_len, int64_t list_cap) {
   FitArgs a;
   a.g = make_grid(plan);
   a.n = static_cast<int32_t>(plan->n);
@@ -74,15 +101,17 @@ cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMo
   a.queue_len = region<int32_t>(plan, ws, R_MISC);
   a.status_word = status_word;
   cudaError_t e;
-  if (prm->precision == PHB_FP64) return launch_fit_fp64(a, mode, nullptr, nullptr, st);
+  if (prm->precision == PHB_FP64) return launch_fit_fp64(a, mode, list, list_len, st);
   if ((e = cudaMemsetAsync(a.queue_len, 0, sizeof(int32_t), st))) return e;
   if ((e = cudaMemsetAsync(a.queue_len + 2, 0, sizeof(int32_t), st))) return e;
   if ((e = launch_fit_mixed(a, mode, region<int2>(plan, ws, R_TPLAN), region<int32_t>(plan, ws, R_TSLOT),
-                            region<uint16_t>(plan, ws, R_LSELF), region<uint16_t>(plan, ws, R_LIDX),
+                            region<uint16_t>(plan, ws, R_LSELF), region<uint8_t>(plan, ws, R_TMAP),
+                            region<uint16_t>(plan, ws, R_LIDX),
                             a.queue_len + 2,
-                            region<int32_t>(plan, ws, R_TORDER), a.queue_len + 3, st)))
+                            region<int32_t>(plan, ws, R_TORDER), a.queue_len + 3, list, list_len,
+                            list_cap, st)))
     return e;
-  return launch_fit_fp64(a, mode, a.queue, a.queue_len, st);
+  return launch_fit_fp64(a, mode, a.queue, a.queue_len, st, true);
 }
 
 }  // namespace phb
@@ -120,6 +149,42 @@ extern "C" phb_status phb_mls_derivs(const phb_plan* plan, const phb_params* par
   if (!grad) return PHB_ERR_INVALID_ARG;
   return fit_entry(plan, params, pos, lambda, U, ws, ws_bytes, FitMode::kDerivs, nullptr, grad,
                    hess, fit_status, status_word, stream);
+}
+
+extern "C" phb_status phb_mhd_rhs_active(const phb_plan* plan, const phb_params* prm,
+                                         const double* pos, const double* lambda, const double* U,
+                                         const int32_t* active, int64_t n_active, void* ws,
+                                         size_t ws_bytes, double* dudt, int32_t* fit_status,
+                                         int32_t* status_word, phb_stream_t stream) {
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_END_COMMON] : 0);
+  if (s != PHB_OK) return s;
+  if (!prm || !pos || !lambda || !U || !dudt || n_active < 0 || (n_active > 0 && !active))
+    return PHB_ERR_INVALID_ARG;
+  if (prm->precision != PHB_FP64 && prm->precision != PHB_FP32_MIXED) return PHB_ERR_INVALID_ARG;
+  if (prm->weight_kind != 0 && prm->weight_kind != 1) return PHB_ERR_INVALID_ARG;
+  if (!(prm->gamma > 1.0)) return PHB_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Grid g = make_grid(plan);
+  const int n = g.n;
+  int32_t* mark = region<int32_t>(plan, ws, R_AFLAG);
+  int32_t* list = region<int32_t>(plan, ws, R_ALIST);
+  int32_t* list_len = region<int32_t>(plan, ws, R_MISC) + 4;
+  cudaError_t e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st);
+  if (e) return launch_status(e);
+  if ((e = cudaMemsetAsync(mark, 0, (size_t(n) + 1) * sizeof(int32_t), st))) return launch_status(e);
+  if (n_active > 0) {
+    k_mark_active<<<static_cast<unsigned>((n_active + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+        n, n_active, active, region<int32_t>(plan, ws, R_INV), mark, status_word);
+    note_launch();
+  }
+  if ((e = scan_exclusive_i32(mark, n + 1, region<int64_t>(plan, ws, R_SCAN), st))) return launch_status(e);
+  k_list_active<<<static_cast<unsigned>((n + 1 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+      n, mark, list, list_len);
+  note_launch();
+  const int64_t cap = n_active < n ? n_active : n;
+  e = run_fit(plan, prm, ws, FitMode::kRHS, region<int32_t>(plan, ws, R_PERM), dudt, nullptr,
+              nullptr, fit_status, status_word, st, list, list_len, cap);
+  return launch_status(e);
 }
 
 extern "C" phb_status phb_mhd_rhs(const phb_plan* plan, const phb_params* params, const double* pos,

@@ -97,3 +97,45 @@ def test_autotune_returns_a_timed_candidate(tmp_path, monkeypatch):
     assert all(t["ms"] is not None and t["ms"] > 0 for t in res["table"])
     again = tune.autotune(w, skin=0.0, reps=2, candidates=cands)
     assert again == res   # served from the cache file
+
+
+def _evolve_wave(phb, n_side, prec, cfl=0.05, jitter=0.1):
+    """One period of the App. A fast magnetosonic wave (amplitude 1e-6) with
+    the predictor-corrector step; mean |U - U_exact| / amplitude summed over
+    the eight fields, against the travelling eigenmode sin(k x - omega t)."""
+    w = workloads.linear_wave(n_side, jitter=jitter)
+    m = w.meta
+    om, k, A, vhat = m["omega"], m["k"], m["amplitude"], m["vhat"]
+    T = 2 * np.pi / om
+    nsteps = int(np.ceil(T / (cfl * m["h"] * k / om)))
+    dt = T / nsteps
+    plan = phb.Plan.for_workload(w, skin=0.05 * 2.3 * m["h"])
+    pos, lam, U = phb.tensors_of(w)
+    phb.build_neighbors(plan, pos, lam)
+    g = phb.StepGraph(plan, phb.Params(gamma=w.gamma, precision=prec), pos, lam, U, dt)
+    for _ in range(nsteps):
+        g.replay()
+    torch.cuda.synchronize()
+    assert plan.read_status() == 0
+    x = pos[0].cpu().numpy()
+    s = A * np.sin(k * x - om * T)
+    kv = k * vhat[0]
+    ex = workloads.background(w.n, B0=m["B0"], P0=m["P0"], gamma=w.gamma)
+    ex[0] += m["rho0"] * kv / om * s
+    ex[1:4] += vhat[:, None] * s
+    ex[4:7] += ((kv * m["B0"][:, None] - k * m["B0"][0] * vhat[:, None]) / om) * s
+    ex[7] += w.gamma * m["P0"] * kv / om * s / (w.gamma - 1)
+    return float((np.abs(U.cpu().numpy() - ex).mean(axis=1) / A).sum())
+
+
+def test_linear_wave_convergence_and_mixed_precision():
+    """Time-evolved linear wave (App. A; Sec. 3.1 shapes): the error after one
+    period falls at least second order from 16^3 to 32^3 jittered lattices,
+    and the FP32-mixed path tracks the FP64 path on the 1e-6 signal."""
+    phb = need_gpu()
+    e16 = _evolve_wave(phb, 16, "fp64")
+    e32 = _evolve_wave(phb, 32, "fp64")
+    order = np.log2(e16 / e32)
+    assert order >= 2.0, (e16, e32, order)
+    m32 = _evolve_wave(phb, 32, "fp32_mixed")
+    assert abs(m32 - e32) <= 0.02 * e32, (m32, e32)
