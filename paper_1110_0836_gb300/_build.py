@@ -16,6 +16,11 @@ SOURCES = ["phb_plan.cu", "phb_neighbors.cu", "phb_rhs.cu", "phb_fit_mixed.cu", 
 HEADERS = ["phb_internal.cuh", "phb_mhd.cuh", "mls_gen.cuh", "phb_tile.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# Per-file extra flags.  The adjoint's recording and replaying kernels are two
+# instances of one template; without implicit FMA contraction (explicit fma()
+# calls stay fused) they round every shared expression identically, so the
+# stored-factorisation adjoint is bit-identical to the recomputing one.
+EXTRA = {"phb_adjoint.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -39,7 +44,7 @@ def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
     if _stale(obj, path):
-        cmd = [nvcc(), *ARCH, *FLAGS, "-c", path, "-o", obj + ".tmp"]
+        cmd = [nvcc(), *ARCH, *FLAGS, *EXTRA.get(src, []), "-c", path, "-o", obj + ".tmp"]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

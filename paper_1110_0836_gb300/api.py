@@ -41,7 +41,7 @@ class Params:
     gamma: float = 5.0 / 3.0
     precision: str = "fp32_mixed"     # or "fp64"
     weight_kind: int = 0              # 0: (1 - s^2)^2, 1: unweighted
-    cond_threshold: float = 300.0     # FP32-mixed: route fits above this estimate to FP64
+    cond_threshold: float = 3e4       # FP32-mixed: route fits above this conditioning estimate to FP64
     zeta: torch.Tensor | None = None  # bulk viscosity [n] (caller order) or None
     eta: torch.Tensor | None = None   # div B diffusivity [n] or None
 

@@ -137,8 +137,10 @@ struct StagedSrc {
 // pass B's right-hand sides are returned in registers.  The list index of
 // the next neighbour is loaded one iteration ahead (fetching its data ahead
 // as well measured slower: the extra registers cost more than the hidden
-// shared-memory latency).  Pass B accumulates sum_j p_k (w dU_j) with the weight folded into the field
-// difference (the moments are complete after pass A).
+// shared-memory latency).  Both passes fold the weight into the field
+// difference for the right-hand sides, so only w and the ten w q^cubic
+// products the moments need are formed (the moments are complete after
+// pass A).
 template <FitMode MODE, int T, class Src>
 __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t end, float inv_l,
                                           float inv_rf2, bool unweighted, float* park, int col,
@@ -165,12 +167,12 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
       const float wt = inside ? (unweighted ? 1.f : sw * sw) : 0.f;
       cnt += inside ? 1 : 0;
       float qg[kNB], wq[kNB + 1];
-      mls_monomials(dx * inv_l, dy * inv_l, dz * inv_l, wt, qg, wq);
+      mls_monomials_cubic_w(dx * inv_l, dy * inv_l, dz * inv_l, wt, qg, wq);
       mls_accum_moments(qg, wq, m);
-      if (MODE == FitMode::kDerivs) mls_accum_rhs(wq, du[0], bA[0]);
-      mls_accum_rhs(wq, du[1], bA[G::NA - 3]);
-      mls_accum_rhs(wq, du[2], bA[G::NA - 2]);
-      mls_accum_rhs(wq, du[3], bA[G::NA - 1]);
+      if (MODE == FitMode::kDerivs) mls_accum_rhs_basis(qg, wt * du[0], bA[0]);
+      mls_accum_rhs_basis(qg, wt * du[1], bA[G::NA - 3]);
+      mls_accum_rhs_basis(qg, wt * du[2], bA[G::NA - 2]);
+      mls_accum_rhs_basis(qg, wt * du[3], bA[G::NA - 1]);
     }
 #pragma unroll
     for (int f = 0; f < G::NA; ++f)
@@ -323,15 +325,10 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       float M[kNT], invd[kNB];
       mls_assemble(m, M);
       const float minpiv = mls_cholesky<float>(M, invd);
-      // Jacobi-scaled pivots L~_kk^2 = L_kk^2 / M_kk = 1 / (invd_k^2 M_kk)
-      float rmin = 3.4e38f, rmax = 0.f;
-#pragma unroll
-      for (int k = 0; k < kNB; ++k) {
-        const float r = 1.f / (invd[k] * invd[k] * M[k * (k + 1) / 2 + k]);
-        rmin = fminf(rmin, r);
-        rmax = fmaxf(rmax, r);
-      }
-      if (!(minpiv > 0.f) || !(rmax <= a.cond_threshold * rmin)) {
+      // conditioning estimate of the Jacobi-scaled matrix: n_b times the
+      // greedy estimate of ||M_s^-1||_inf (|M_s,rc| <= 1, so ||M_s||_inf <= n_b)
+      const float kappa = static_cast<float>(kNB) * mls_inv_norm_est<float>(M, invd);
+      if (!(minpiv > 0.f) || !(kappa <= a.cond_threshold)) {
         const int q = atomicAdd(a.queue_len, 1);
         a.queue[q] = s;
         routed = true;

@@ -399,24 +399,27 @@ __global__ void __launch_bounds__(T) k_compact(Grid g, const int2* __restrict__ 
   }
   const int64_t e0 = toff[0];
   const int64_t e1 = toff[cnt] < g.capacity ? toff[cnt] : g.capacity;
-  for (int64_t e = e0 + tid; e < e1; e += T) {
-    int lo = 0, hi = cnt - 1;  // owner: last k with toff[k] <= e
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (toff[mid] <= e) lo = mid;
-      else hi = mid - 1;
-    }
-    const int s = s0 + lo;
-    int t;
-    if (ncnt[s] <= g.ell) {
-      t = ell[static_cast<int64_t>(s) * g.ell + (e - toff[lo])];
-      idx[e] = t;
-    } else {
-      t = idx[e];
-    }
-    if (staged) {
-      const int j = marked_index(tarr, box_index(g, ts, cellc[t]));
-      lidx[e] = static_cast<uint16_t>(base[j] + (t - cstart[j]));
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int p = warp; p < cnt; p += T / 32) {
+    const int s = s0 + p;
+    const int m = tlen[p];
+    const bool over = m > g.ell;
+    const int64_t eb = toff[p];
+    const int64_t row = static_cast<int64_t>(s) * g.ell;
+    for (int k = lane; k < m; k += 32) {
+      const int64_t e = eb + k;
+      if (e >= e1) break;
+      int t;
+      if (over) {
+        t = idx[e];
+      } else {
+        t = ell[row + k];
+        idx[e] = t;
+      }
+      if (staged) {
+        const int j = marked_index(tarr, box_index(g, ts, cellc[t]));
+        lidx[e] = static_cast<uint16_t>(base[j] + (t - cstart[j]));
+      }
     }
   }
 }

@@ -90,7 +90,7 @@ cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMo
   a.idx = region<int32_t>(plan, ws, R_IDX);
   a.gamma = prm->gamma;
   a.weight_kind = prm->weight_kind;
-  a.cond_threshold = static_cast<float>(prm->cond_threshold > 0 ? prm->cond_threshold : 300.0);
+  a.cond_threshold = static_cast<float>(prm->cond_threshold > 0 ? prm->cond_threshold : 3e4);
   a.zeta = prm->zeta;
   a.eta = prm->eta;
   a.dudt = dudt;
