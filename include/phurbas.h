@@ -105,7 +105,7 @@ typedef struct {
   double lambda_min;
   double lambda_max;
   int64_t nbr_capacity;  /* entries reserved for neighbour lists (sum of |N(i)|) */
-  double cell_frac;      /* cell edge / (rf_factor*lambda_min + skin); 0 = default 0.5 */
+  double cell_frac;      /* cell edge / (rf_factor*lambda_min + skin); 0 = default 1 */
   int32_t tile;          /* particles per fused-fit tile (64 or 128; 0 = default 128) */
   int32_t stage_cap;     /* neighbourhood records staged per tile (0 = default) */
   int32_t schedule;      /* fused fit: 0 = one CTA per tile in cell order; 1 = persistent CTAs

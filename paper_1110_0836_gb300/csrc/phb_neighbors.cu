@@ -45,34 +45,19 @@ __global__ void k_scatter(int n, const int32_t* __restrict__ keys, const int32_t
 }
 
 // Make the order inside each cell deterministic: ascending caller index.
-// Insertion sort for the usual handful of particles, Shell sort otherwise.
-__global__ void k_sort_cells(int64_t nkeys, const int32_t* __restrict__ cell_start,
-                             int32_t* __restrict__ perm) {
-  const int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (c >= nkeys) return;
-  const int a = cell_start[c], b = cell_start[c + 1];
-  const int m = b - a;
-  if (m < 2) return;
-  int32_t* v = perm + a;
-  if (m <= 48) {
-    for (int i = 1; i < m; ++i) {
-      int32_t x = v[i];
-      int j = i - 1;
-      while (j >= 0 && v[j] > x) { v[j + 1] = v[j]; --j; }
-      v[j + 1] = x;
-    }
-    return;
-  }
-  int h = 1;
-  while (3 * h + 1 < m) h = 3 * h + 1;  // Knuth gaps 1, 4, 13, 40, ...
-  for (; h >= 1; h /= 3) {
-    for (int i = h; i < m; ++i) {
-      int32_t x = v[i];
-      int j = i;
-      while (j >= h && v[j - h] > x) { v[j] = v[j - h]; j -= h; }
-      v[j] = x;
-    }
-  }
+// Thread per particle: its rank among the particles of its cell is the number
+// of them with a smaller caller index (the cells' members come from the
+// atomic scatter in arbitrary order).
+__global__ void k_rank_cells(int n, const int32_t* __restrict__ keys,
+                             const int32_t* __restrict__ cell_start,
+                             const int32_t* __restrict__ scattered, int32_t* __restrict__ perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t k = keys[i];
+  const int a = cell_start[k], b = cell_start[k + 1];
+  int rank = 0;
+  for (int t = a; t < b; ++t) rank += scattered[t] < i ? 1 : 0;
+  perm[a + rank] = i;
 }
 
 // Slot-order copies of positions and lambda, the inverse permutation and the
@@ -514,9 +499,11 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   k_keys<<<blocks_for(n), kThreads, 0, st>>>(g, pos, lam, keys, cell, status_word);
   note_launch();
   if ((e = scan_exclusive_i32(cell, p->nkeys + 1, bsum, st))) return e;
-  k_scatter<<<blocks_for(n), kThreads, 0, st>>>(n, keys, cell, cursor, perm);
+  // the inverse-permutation region (written later by k_gather_pos) holds the
+  // scattered order until the ranking puts it into ascending caller index
+  k_scatter<<<blocks_for(n), kThreads, 0, st>>>(n, keys, cell, cursor, inv);
   note_launch();
-  k_sort_cells<<<blocks_for(p->nkeys), kThreads, 0, st>>>(p->nkeys, cell, perm);
+  k_rank_cells<<<blocks_for(n), kThreads, 0, st>>>(n, keys, cell, inv, perm);
   note_launch();
   k_gather_pos<<<blocks_for(n), kThreads, 0, st>>>(g, perm, pos, lam, inv, spos, slam, scr, cellc);
   note_launch();

@@ -189,7 +189,7 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   const double rmax = p->rf_factor * p->lambda_max + p->skin;
   for (int a = 0; a < 3; ++a)
     if (p->box.periodic[a] && !(rmax < 0.5 * p->box.len[a])) return PHB_ERR_INVALID_ARG;
-  double frac = p->cell_frac > 0 ? p->cell_frac : 0.5;
+  double frac = p->cell_frac > 0 ? p->cell_frac : 1.0;
   double h = frac * rmin;
   // at most 1023 cells per axis (10-bit packed coordinates), 2^26 cells in all
   for (int a = 0; a < 3; ++a) h = std::max(h, p->box.len[a] / 1023.0);

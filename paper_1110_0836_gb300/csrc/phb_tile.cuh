@@ -162,9 +162,16 @@ __device__ void tile_plan(const Grid& g, int s0, int cnt, const int32_t* __restr
   }
   __syncthreads();
   if (ts.fallback) return;
+  // a particle in the same cell as the previous slot, with the same reach,
+  // marks nothing new (cells hold consecutive slots)
+  const int32_t pc = tid < cnt ? cellc[s0 + tid] : -1;
+  const int pr = R[0] | (R[1] << 10) | (R[2] << 20);
+  const int32_t prev_c = __shfl_up_sync(0xffffffffu, pc, 1);
+  const int prev_r = __shfl_up_sync(0xffffffffu, pr, 1);
+  const bool dup = (tid & 31) > 0 && prev_c == pc && prev_r == pr;
   // mark the reach box of every particle (whole axis where the reach wraps),
   // one masked atomicOr per run of cells along z
-  if (tid < cnt) {
+  if (tid < cnt && !dup) {
     int n3[3], st[3];
     for (int a = 0; a < 3; ++a) {
       if (g.periodic[a] && 2 * R[a] + 1 > g.ncell[a]) {

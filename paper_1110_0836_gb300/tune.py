@@ -18,12 +18,12 @@ import torch
 from .api import Params, Plan, build_neighbors, mhd_rhs, tensors_of
 
 CANDIDATES = [
+    dict(tile=128, schedule=0, cell_frac=1.0),
+    dict(tile=128, schedule=1, cell_frac=1.0),
+    dict(tile=64, schedule=0, cell_frac=1.0),
     dict(tile=128, schedule=0, cell_frac=0.5),
     dict(tile=128, schedule=1, cell_frac=0.5),
     dict(tile=64, schedule=0, cell_frac=0.5),
-    dict(tile=64, schedule=1, cell_frac=0.5),
-    dict(tile=128, schedule=0, cell_frac=0.6),
-    dict(tile=128, schedule=1, cell_frac=0.6),
 ]
 
 

@@ -56,10 +56,10 @@ def test_plan_init_valid(L):
     p = _plan()
     assert L.phb_plan_init(C.byref(p)) == 0
     assert p.ws_bytes > 0 and L.phb_workspace_size(C.byref(p), 0) == p.ws_bytes
-    # cell edge >= half the radius, every axis covered
+    # cell edge >= the list radius (default cell_frac 1), every axis covered
     for a in range(3):
         assert p.ncell[a] >= 1 and abs(p.cell[a] * p.ncell[a] - 1.0) < 1e-12
-        assert p.cell[a] >= 0.5 * 2.3 / 16 * (1 - 1e-12)
+        assert p.cell[a] >= 2.3 / 16 * (1 - 1e-12)
     assert p.nkeys == 64 * p.nbrick[0] * p.nbrick[1] * p.nbrick[2]
     offs = list(p.ws_off)[:10]
     assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
