@@ -41,7 +41,7 @@ FLOP_PER_NEIGHBOUR = 2 * (80 + 7 * 19)
 FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
 # DRAM bytes (read + write) per launch of the fused fit, from ncu captures of the
 # kernel as it is built now: (workload, kernel, tile) -> bytes.  Absent = null.
-FIT_TRAFFIC = {("random_modes_64^3", "k_fit_mixed", 128): 69.34e6 + 3.04e6}
+FIT_TRAFFIC = {("random_modes_64^3", "k_fit_mixed", 128): 69.36e6 + 3.05e6}
 
 
 def parse():
@@ -285,7 +285,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{w.name}: {WORKLOAD_TEXT.get(w.name, w.name)}",
+            "config": {"workload": f"{w.name}: {WORKLOAD_TEXT.get(args.workload, w.name)}",
                        "particles": w.n, "sample_per_step": int(len(q))},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "cpu": cpu_model(),
@@ -622,7 +622,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 storage, FP32 fit, FP64 routing)",
         "data": "synthetic",
-        "config": {"workload": f"{w.name}: {WORKLOAD_TEXT.get(w.name, w.name)}",
+        "config": {"workload": f"{w.name}: {WORKLOAD_TEXT.get(args.workload, w.name)}",
                    "particles": n,
                    "step": "one predictor-corrector step: binning + neighbour lists (skin) + 2 fused "
                            "FP32-mixed fit/RHS evaluations + Heun update; 2 particle-RHS per particle",

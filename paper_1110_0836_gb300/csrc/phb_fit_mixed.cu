@@ -134,9 +134,9 @@ struct StagedSrc {
 
 // Both accumulation passes of one particle.  Pass A's right-hand sides are
 // parked in shared memory column `col` ([slot][T] layout); the moments and
-// pass B's right-hand sides are returned in registers.  The list index of
-// the next neighbour is loaded one iteration ahead (fetching its data ahead
-// as well measured slower: the extra registers cost more than the hidden
+// pass B's right-hand sides are returned in registers.  List indices are
+// loaded four neighbours ahead (fetching the neighbours' data ahead as well
+// measured slower: the extra registers cost more than the hidden
 // shared-memory latency).  Both passes fold the weight into the field
 // difference for the right-hand sides, so only w and the ten w q^cubic
 // products the moments need are formed (the moments are complete after
@@ -155,10 +155,14 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
     for (int f = 0; f < G::NA; ++f)
 #pragma unroll
       for (int k = 0; k < kNB; ++k) bA[f][k] = 0.f;
-    int nxt = beg < end ? src.index(beg) : 0;
+    int n1 = beg < end ? src.index(beg) : 0;
+    int n2 = beg + 1 < end ? src.index(beg + 1) : 0;
+    int n3 = beg + 2 < end ? src.index(beg + 2) : 0;
+    int n4 = beg + 3 < end ? src.index(beg + 3) : 0;
     for (int64_t e = beg; e < end; ++e) {
-      const int cur = nxt;
-      if (e + 1 < end) nxt = src.index(e + 1);
+      const int cur = n1;
+      n1 = n2; n2 = n3; n3 = n4;
+      if (e + 4 < end) n4 = src.index(e + 4);
       float dx, dy, dz, du[4];
       src.decode_a(src.fetch_a(cur), dx, dy, dz, du);
       const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
@@ -183,10 +187,14 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
   for (int f = 0; f < 4; ++f)
 #pragma unroll
     for (int k = 0; k < kNB; ++k) bB[f][k] = 0.f;
-  int nxt = beg < end ? src.index(beg) : 0;
+  int n1 = beg < end ? src.index(beg) : 0;
+  int n2 = beg + 1 < end ? src.index(beg + 1) : 0;
+  int n3 = beg + 2 < end ? src.index(beg + 2) : 0;
+  int n4 = beg + 3 < end ? src.index(beg + 3) : 0;
   for (int64_t e = beg; e < end; ++e) {
-    const int cur = nxt;
-    if (e + 1 < end) nxt = src.index(e + 1);
+    const int cur = n1;
+    n1 = n2; n2 = n3; n3 = n4;
+    if (e + 4 < end) n4 = src.index(e + 4);
     float dx, dy, dz, du[4];
     src.decode_b(src.fetch_b(cur), dx, dy, dz, du);
     const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
@@ -246,8 +254,8 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     const float4 rh = rec[6 * s0], rl = rec[6 * s0 + 1];
     const float4 fh = rec[6 * s0 + 2], fl = rec[6 * s0 + 3], gh = rec[6 * s0 + 4], gl = rec[6 * s0 + 5];
     const int32_t* slots = ta.tslot + static_cast<int64_t>(tile) * a.g.stage_cap;
-    // four records per thread in flight: slots first, then all their loads
-    constexpr int kB = 4;
+    // eight records per thread in flight: slots first, then all their loads
+    constexpr int kB = 8;
     for (int l0 = tid; l0 < tp.x; l0 += kB * T) {
       int sl[kB];
 #pragma unroll

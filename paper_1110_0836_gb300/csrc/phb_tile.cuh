@@ -2,11 +2,11 @@
 // cells are ordered brick by brick along a Hilbert curve, a tile covers a
 // compact set of cells.  Its neighbourhood - the union of the reach boxes of
 // its particles' cells, marked in a bitmap over the dilated bounding box - is
-// staged in shared memory once per tile, so the per-neighbour loads of the
-// neighbour search and of the fused fit become shared-memory loads.  The
-// staging order (marked cells in x-major box order, particles of a cell in
-// slot order) defines the 16-bit tile-local neighbour indices written by the
-// neighbour search.
+// planned once per neighbour build (the compaction kernel records the slot of
+// every staged index) and staged in shared memory by every fused fit, so the
+// fit's per-neighbour loads are shared-memory loads.  The staging order
+// (marked cells in x-major box order, particles of a cell in slot order)
+// defines the 16-bit tile-local neighbour indices of the lists.
 //
 // A tile whose bounding box holds more than kBoxCap cells, whose
 // neighbourhood has more than kMarkCap cells or more than stage_cap particles
