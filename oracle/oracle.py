@@ -29,7 +29,8 @@ class Box(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("rf_factor", C.c_double), ("weight_kind", C.c_int32),
-                ("pad", C.c_int32), ("zeta", C.c_void_p), ("eta", C.c_void_p)]
+                ("pad", C.c_int32), ("zeta", C.c_void_p), ("eta", C.c_void_p),
+                ("frozen", C.c_void_p)]
 
 
 _LIB = None
@@ -99,7 +100,7 @@ def box_of(w) -> Box:
 class _P:
     """Params plus the numpy arrays its pointers refer to (kept alive)."""
 
-    def __init__(self, gamma, rf_factor=2.3, weight_kind=0, zeta=None, eta=None):
+    def __init__(self, gamma, rf_factor=2.3, weight_kind=0, zeta=None, eta=None, frozen=None):
         self.keep = []
         self.p = Params()
         self.p.gamma = float(gamma)
@@ -107,6 +108,11 @@ class _P:
         self.p.weight_kind = int(weight_kind)
         self.p.zeta = self._ptr(zeta)
         self.p.eta = self._ptr(eta)
+        self.p.frozen = None
+        if frozen is not None:
+            fz = np.ascontiguousarray(np.asarray(frozen) != 0, np.uint8)
+            self.keep.append(fz)
+            self.p.frozen = fz.ctypes.data
 
     def _ptr(self, a):
         if a is None:
@@ -195,10 +201,11 @@ def rhs_jvp(box: Box, pos, lam, U, dpos, dU, nbrs, query=None, gamma=5.0 / 3.0, 
 
 
 def pc_step(box: Box, pos, lam, U, dt, gamma=5.0 / 3.0, rf_factor=2.3, weight_kind=0, zeta=None,
-            eta=None):
-    """One Heun step of all particles (O(n^2) brute force): returns new (pos, U)."""
+            eta=None, frozen=None):
+    """One Heun step of all particles (O(n^2) brute force): returns new (pos, U).
+    frozen: optional [n] mask of particles that keep x and U (fixed values)."""
     pos, lam, U = _c(pos).copy(), _c(lam), _c(U).copy()
-    P = _P(gamma, rf_factor, weight_kind, zeta, eta)
+    P = _P(gamma, rf_factor, weight_kind, zeta, eta, frozen)
     nsing = lib().orc_pc_step(C.byref(box), lam.shape[0], pos, lam, U, float(dt), C.byref(P.p))
     return pos, U, nsing
 

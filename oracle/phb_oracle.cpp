@@ -59,6 +59,7 @@ struct Params {
   int32_t pad;
   const double* zeta;   // [n] or null (0)
   const double* eta;    // [n] or null (0)
+  const uint8_t* frozen;  // [n] or null: nonzero = no time evolution (pc_step only)
 };
 
 // ---------------------------------------------------------------- dual numbers
@@ -360,8 +361,9 @@ int orc_rhs_jvp(const Box* box, int64_t n, const double* pos, const double* lam,
 // One Heun (second-order predictor-corrector) step of all n particles, in
 // place, with brute-force neighbour sets at x^n and again at x^p:
 //   Y^p = Y^n + dt F(Y^n);   Y^{n+1} = Y^n + dt/2 (F(Y^n) + F(Y^p)),
-// Y = (x, U), dx/dt = V, lambda unchanged.  O(n^2): small n only.
-// Returns the number of singular fits seen in either stage.
+// Y = (x, U), dx/dt = V, lambda unchanged; particles marked frozen keep their
+// Y (the fixed-value boundaries of the Sec. 3 annulus test).  O(n^2): small n
+// only.  Returns the number of singular fits seen in either stage.
 int orc_pc_step(const Box* box, int64_t n, double* pos, const double* lam, double* U, double dt,
                 const Params* prm) {
   std::vector<int64_t> all(n);
@@ -379,16 +381,23 @@ int orc_pc_step(const Box* box, int64_t n, double* pos, const double* lam, doubl
     for (int64_t i = 0; i < n; ++i) nsing += st[i];
   };
   int64_t nsing = 0;
+  // frozen particles (fixed-value boundaries) keep x and U through both stages
+  auto moving = [&](int64_t i) { return !(prm->frozen && prm->frozen[i]); };
   std::vector<double> F0(NF * n), F1(NF * n), xp(3 * n), up(NF * n);
   eval(pos, U, F0.data(), nsing);
   for (int ax = 0; ax < 3; ++ax)
-    for (int64_t i = 0; i < n; ++i) xp[ax * n + i] = pos[ax * n + i] + dt * U[(1 + ax) * n + i];
-  for (int64_t k = 0; k < NF * n; ++k) up[k] = U[k] + dt * F0[k];
+    for (int64_t i = 0; i < n; ++i)
+      xp[ax * n + i] = pos[ax * n + i] + (moving(i) ? dt * U[(1 + ax) * n + i] : 0.0);
+  for (int f = 0; f < NF; ++f)
+    for (int64_t i = 0; i < n; ++i)
+      up[f * n + i] = U[f * n + i] + (moving(i) ? dt * F0[f * n + i] : 0.0);
   eval(xp.data(), up.data(), F1.data(), nsing);
   for (int ax = 0; ax < 3; ++ax)
     for (int64_t i = 0; i < n; ++i)
-      pos[ax * n + i] += 0.5 * dt * (U[(1 + ax) * n + i] + up[(1 + ax) * n + i]);
-  for (int64_t k = 0; k < NF * n; ++k) U[k] += 0.5 * dt * (F0[k] + F1[k]);
+      if (moving(i)) pos[ax * n + i] += 0.5 * dt * (U[(1 + ax) * n + i] + up[(1 + ax) * n + i]);
+  for (int f = 0; f < NF; ++f)
+    for (int64_t i = 0; i < n; ++i)
+      if (moving(i)) U[f * n + i] += 0.5 * dt * (F0[f * n + i] + F1[f * n + i]);
   return static_cast<int>(nsing);
 }
 

@@ -33,7 +33,10 @@ MUTATIONS = {
     "induction_compression": ("- B[a] * divV", "+ B[a] * divV"),
     "not_strict": ("return d2 < r * r;", "return d2 <= r * r;"),
     "no_min_image": ("if (periodic) d = d - len", "if (periodic < 0) d = d - len"),
-    "euler_corrector": ("U[k] += 0.5 * dt * (F0[k] + F1[k]);", "U[k] += dt * F0[k];"),
+    "euler_corrector": ("U[f * n + i] += 0.5 * dt * (F0[f * n + i] + F1[f * n + i]);",
+                        "U[f * n + i] += dt * F0[f * n + i];"),
+    "frozen_ignored": ("auto moving = [&](int64_t i) { return !(prm->frozen && prm->frozen[i]); };",
+                       "auto moving = [&](int64_t i) { return i >= 0; };"),
     "basis_xyz_missing": ("p[13] = x * y * z;", "p[13] = x * y;"),
     "lambda_scale": ("grad[f][0] = C[0 * NF + f] * il;", "grad[f][0] = C[0 * NF + f] * il * il;"),
     "level_off_by_one": ("    int32_t L = 0;\n    while (L < max_level", "    int32_t L = 1;\n    while (L < max_level"),
@@ -60,6 +63,7 @@ PINS = [
     lambda: trhs.test_divb_diffusion(oracle),
     lambda: trhs.test_viscous_heating_linear_flow(oracle),
     lambda: tstep.test_heun_is_second_order_in_time(oracle),
+    lambda: tstep.test_frozen_particles_in_uniform_flow(oracle),
     lambda: tlev.test_golden_line(),
     lambda: tlev.test_power_of_two_rounding_against_the_courant_step(),
     lambda: tlev.test_bulk_velocity_does_not_change_levels(),

@@ -57,3 +57,37 @@ def test_jvp_matches_central_differences(orc):
                         zeta=zeta, eta=eta)
     fd = (op - om) / (2 * h)
     assert rel_err(dout, fd).max() < 1e-6
+
+
+def test_frozen_particles_in_uniform_flow(orc):
+    """Fixed-value boundaries (the Sec. 3 annulus test keeps particles outside
+    a radius range from evolving): in a uniform flow every right-hand side
+    vanishes exactly, so frozen particles keep x and U bit for bit while the
+    others advect by V dt exactly, although the frozen ones now lag behind."""
+    w = workloads.linear_wave(8, amplitude=0.0)
+    w.U[1:4] = np.array([[0.3], [-0.2], [0.1]])
+    rng = np.random.default_rng(4)
+    frozen = rng.random(w.n) < 0.3
+    box = orc.box_of(w)
+    dt = 0.0625
+    pos, U, ns = orc.pc_step(box, w.pos, w.lam, w.U, dt, gamma=w.gamma, frozen=frozen)
+    assert ns == 0
+    np.testing.assert_array_equal(U, w.U)
+    np.testing.assert_array_equal(pos[:, frozen], w.pos[:, frozen])
+    np.testing.assert_array_equal(pos[:, ~frozen], w.pos[:, ~frozen] + dt * w.U[1:4, ~frozen])
+
+
+def test_frozen_mask_all_zero_is_the_plain_step_and_frozen_keep_state(orc):
+    w = workloads.random_modes(8, seed=9, amp=0.05)
+    box = orc.box_of(w)
+    dt = 0.002
+    p0, u0, _ = orc.pc_step(box, w.pos, w.lam, w.U, dt, gamma=w.gamma)
+    p1, u1, _ = orc.pc_step(box, w.pos, w.lam, w.U, dt, gamma=w.gamma,
+                            frozen=np.zeros(w.n, bool))
+    assert np.array_equal(p0, p1) and np.array_equal(u0, u1)
+    frozen = np.zeros(w.n, bool)
+    frozen[: w.n // 4] = True
+    p2, u2, _ = orc.pc_step(box, w.pos, w.lam, w.U, dt, gamma=w.gamma, frozen=frozen)
+    assert np.array_equal(p2[:, frozen], w.pos[:, frozen])
+    assert np.array_equal(u2[:, frozen], w.U[:, frozen])
+    assert not np.array_equal(u2[:, ~frozen], w.U[:, ~frozen])
