@@ -91,6 +91,12 @@ typedef struct {
                             within a factor ~0.4-1.8 on the test sets */
   const double* zeta;    /* bulk viscosity per particle [n], or NULL for 0 */
   const double* eta;     /* div B diffusivity per particle [n], or NULL for 0 */
+  const uint8_t* frozen; /* phb_pc_step only: device mask [n] (caller order) or
+                            NULL.  A particle with frozen[i] != 0 keeps its
+                            position and state through the step (the
+                            fixed-value boundaries of the Sec. 3 tests); its
+                            right-hand side is still evaluated and it stays a
+                            neighbour of the others.  Read by no other call. */
 } phb_params;
 
 /* A plan fixes the particle count, box, radius law and the cell grid.  The
@@ -142,6 +148,13 @@ const char* phb_status_string(int32_t status);
 /* Map a device status word (already copied to the host) to the most severe
  * phb_status it encodes. */
 phb_status phb_check(int32_t status_word);
+
+/* Sizes of the ABI structs as this library was compiled: out[0] =
+ * sizeof(phb_box), out[1] = sizeof(phb_params), out[2] = sizeof(phb_plan),
+ * for the first `count` (1..3) of them, so a binding can check its copy of
+ * the layouts.  Host only, no device call.  Returns 0, or 1 for a NULL out or
+ * a count outside 1..3. */
+int phb_struct_sizes(int64_t* out, int32_t count);
 
 /* Build the neighbour sets of all particles (Sec. 2; Sec. 2.1: strict,
  * fixed radius, not mutual, no iteration):

@@ -28,7 +28,8 @@ EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_chec
            "phb_mhd_rhs", "phb_pc_step", "phb_rhs_adjoint", "phb_fma_peak", "phb_launch_count",
            "phb_trace_start", "phb_trace_stop", "phb_trace_read", "phb_workspace_stats", "phb_mhd_rhs_noalloc",
            "phb_noalloc_scratch_bytes", "phb_adjoint_record_bytes", "phb_adjoint_record",
-           "phb_rhs_adjoint_stored", "phb_mhd_rhs_active", "phb_timestep_levels"]
+           "phb_rhs_adjoint_stored", "phb_mhd_rhs_active", "phb_timestep_levels",
+           "phb_struct_sizes"]
 
 
 class Box(C.Structure):
@@ -38,7 +39,8 @@ class Box(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("weight_kind", C.c_int32), ("precision", C.c_int32),
-                ("cond_threshold", C.c_double), ("zeta", C.c_void_p), ("eta", C.c_void_p)]
+                ("cond_threshold", C.c_double), ("zeta", C.c_void_p), ("eta", C.c_void_p),
+                ("frozen", C.c_void_p)]
 
 
 class Plan(C.Structure):
@@ -118,6 +120,13 @@ def lib(path: str | None = None) -> C.CDLL:
     L.phb_mhd_rhs_noalloc.restype = C.c_int
     L.phb_noalloc_scratch_bytes.argtypes = []
     L.phb_noalloc_scratch_bytes.restype = C.c_size_t
+    L.phb_struct_sizes.argtypes = [_vp, C.c_int32]
+    L.phb_struct_sizes.restype = C.c_int
+    sizes = (C.c_int64 * 3)()
+    if L.phb_struct_sizes(sizes, 3) != 0 or tuple(sizes) != (C.sizeof(Box), C.sizeof(Params),
+                                                             C.sizeof(Plan)):
+        raise RuntimeError(f"{p}: struct sizes {tuple(sizes)} differ from the binding's "
+                           f"{(C.sizeof(Box), C.sizeof(Params), C.sizeof(Plan))}; rebuild")
     for f in ("phb_plan_init", "phb_check", "phb_build_neighbors", "phb_export_neighbors",
               "phb_mls_derivs", "phb_mhd_rhs", "phb_pc_step", "phb_rhs_adjoint"):
         getattr(L, f).restype = C.c_int

@@ -44,6 +44,7 @@ class Params:
     cond_threshold: float = 3e4       # FP32-mixed: route fits above this conditioning estimate to FP64
     zeta: torch.Tensor | None = None  # bulk viscosity [n] (caller order) or None
     eta: torch.Tensor | None = None   # div B diffusivity [n] or None
+    frozen: torch.Tensor | None = None  # pc_step: bool/uint8 [n], nonzero = keep x and U
 
     def c(self) -> _lib.Params:
         p = _lib.Params()
@@ -55,6 +56,10 @@ class Params:
         p.cond_threshold = float(self.cond_threshold)
         p.zeta = None if self.zeta is None else self.zeta.data_ptr()
         p.eta = None if self.eta is None else self.eta.data_ptr()
+        if self.frozen is not None and (self.frozen.dtype not in (torch.bool, torch.uint8)
+                                        or not self.frozen.is_contiguous()):
+            raise ValueError("frozen must be a contiguous bool or uint8 tensor")
+        p.frozen = None if self.frozen is None else self.frozen.data_ptr()
         return p
 
 
@@ -210,6 +215,8 @@ def pc_step(plan: Plan, params: Params, pos, lam, U, dt: float):
     """One predictor-corrector step in place (phb_pc_step).  Needs plan.skin > 2 dt max|V|."""
     n = plan.n
     _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    if params.frozen is not None:
+        _need(params.frozen, (n,), "frozen", params.frozen.dtype)
     pc = params.c()
     check(_lib.lib().phb_pc_step(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
                                  float(dt), _ptr(plan.ws), plan.ws.numel(), _ptr(plan.status_word),
@@ -350,7 +357,7 @@ class StepGraph:
         if steps < 1:
             raise ValueError("steps must be >= 1")
         self.plan, self.params, self.steps = plan, params, int(steps)
-        self._keep = (pos, lam, U, params.zeta, params.eta, plan.ws)
+        self._keep = (pos, lam, U, params.zeta, params.eta, params.frozen, plan.ws)
         self.graph = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream(device=plan.device)
         side.wait_stream(torch.cuda.current_stream(plan.device))

@@ -5,7 +5,7 @@
 // with radius r_f + skin; both right-hand-side evaluations filter the lists
 // at r_f with their own positions.  The whole step is a fixed sequence of
 // launches on one stream (no host synchronisation), so it can be captured
-// in a CUDA graph.
+// in a CUDA graph.  Particles marked in params->frozen keep x and U.
 #include <cmath>
 
 #include "phb_internal.cuh"
@@ -16,39 +16,45 @@ namespace {
 constexpr int kThreads = 256;
 
 // Y^p = Y^n + dt F(Y^n) in slot order; refresh the FP32 records; flag a
-// displacement above half the skin (the lists would then miss pairs).
+// displacement above half the skin (the lists would then miss pairs).  A
+// frozen particle (mask in caller order) keeps Y^n.
 __global__ void k_predict(Grid g, double dt, const double* __restrict__ y0,
-                          const double* __restrict__ f0, double* __restrict__ spos,
+                          const double* __restrict__ f0, const int32_t* __restrict__ perm,
+                          const uint8_t* __restrict__ frozen, double* __restrict__ spos,
                           double* __restrict__ sU, float* __restrict__ rec, int32_t* status_word) {
   const int n = g.n;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int64_t N = n;
+  const double h = (frozen && frozen[perm[s]]) ? 0.0 : dt;
   double x[3], u[8];
   double disp2 = 0.0;
   for (int a = 0; a < 3; ++a) {
-    const double d = dt * y0[(3 + 1 + a) * N + s];  // dt * V^n
+    const double d = h * y0[(3 + 1 + a) * N + s];  // dt * V^n
     x[a] = y0[a * N + s] + d;
     spos[a * N + s] = x[a];
     disp2 += d * d;
   }
   for (int f = 0; f < 8; ++f) {
-    u[f] = y0[(3 + f) * N + s] + dt * f0[f * N + s];
+    u[f] = y0[(3 + f) * N + s] + h * f0[f * N + s];
     sU[f * N + s] = u[f];
   }
   if (4.0 * disp2 > g.skin * g.skin) raise_flag(status_word, PHB_FLAG_SKIN);
   write_record(rec, s, x, u);
 }
 
-// Y^{n+1} = Y^n + dt/2 (F(Y^n) + F(Y^p)), written to the caller's arrays.
+// Y^{n+1} = Y^n + dt/2 (F(Y^n) + F(Y^p)), written to the caller's arrays;
+// a frozen particle's entries are left as they are.
 __global__ void k_correct(int n, double dt, const int32_t* __restrict__ perm,
-                          const double* __restrict__ y0, const double* __restrict__ sU_p,
-                          const double* __restrict__ f0, const double* __restrict__ f1,
-                          double* __restrict__ pos, double* __restrict__ U) {
+                          const uint8_t* __restrict__ frozen, const double* __restrict__ y0,
+                          const double* __restrict__ sU_p, const double* __restrict__ f0,
+                          const double* __restrict__ f1, double* __restrict__ pos,
+                          double* __restrict__ U) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int64_t N = n;
   const int i = perm[s];
+  if (frozen && frozen[i]) return;
   const double h = 0.5 * dt;
   for (int a = 0; a < 3; ++a)
     pos[a * N + i] = y0[a * N + s] + h * (y0[(3 + 1 + a) * N + s] + sU_p[(1 + a) * N + s]);
@@ -87,14 +93,14 @@ extern "C" phb_status phb_pc_step(const phb_plan* plan, const phb_params* prm, d
   if ((e = run_fit(plan, prm, ws, FitMode::kRHS, nullptr, f0, nullptr, nullptr, nullptr,
                    status_word, st)))
     return launch_status(e);
-  k_predict<<<blocks, kThreads, 0, st>>>(g, dt, y0, f0, spos, sU, region<float>(plan, ws, R_REC),
-                                         status_word);
+  const int32_t* perm = region<int32_t>(plan, ws, R_PERM);
+  k_predict<<<blocks, kThreads, 0, st>>>(g, dt, y0, f0, perm, prm->frozen, spos, sU,
+                                         region<float>(plan, ws, R_REC), status_word);
   note_launch();
   if ((e = run_fit(plan, prm, ws, FitMode::kRHS, nullptr, f1, nullptr, nullptr, nullptr,
                    status_word, st)))
     return launch_status(e);
-  k_correct<<<blocks, kThreads, 0, st>>>(n, dt, region<int32_t>(plan, ws, R_PERM), y0, sU, f0, f1,
-                                         pos, U);
+  k_correct<<<blocks, kThreads, 0, st>>>(n, dt, perm, prm->frozen, y0, sU, f0, f1, pos, U);
   note_launch();
   return launch_status(cudaSuccess);
 }

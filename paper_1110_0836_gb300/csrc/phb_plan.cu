@@ -294,6 +294,14 @@ extern "C" size_t phb_workspace_size(const phb_plan* p, int32_t op) {
   return p->ws_bytes;
 }
 
+extern "C" int phb_struct_sizes(int64_t* out, int32_t count) {
+  if (!out || count < 1 || count > 3) return 1;
+  const int64_t v[3] = {static_cast<int64_t>(sizeof(phb_box)), static_cast<int64_t>(sizeof(phb_params)),
+                        static_cast<int64_t>(sizeof(phb_plan))};
+  for (int k = 0; k < count; ++k) out[k] = v[k];
+  return 0;
+}
+
 extern "C" const char* phb_status_string(int32_t s) {
   switch (s) {
     case PHB_OK: return "ok";

@@ -112,3 +112,12 @@ def test_null_arguments_rejected_on_host(L):
     # null workspace / arrays are caught before any CUDA call
     assert L.phb_build_neighbors(C.byref(p), None, None, None, 0, None, None) in (1, 2)
     assert L.phb_mhd_rhs(C.byref(p), None, None, None, None, None, 0, None, None, None, None) == 1
+
+
+def test_struct_sizes_match_the_binding(L):
+    from paper_1110_0836_gb300 import _lib
+    out = (C.c_int64 * 3)()
+    assert L.phb_struct_sizes(out, 3) == 0
+    assert tuple(out) == (C.sizeof(_lib.Box), C.sizeof(_lib.Params), C.sizeof(_lib.Plan))
+    assert C.sizeof(_lib.Params) == 48    # gamma, kind, precision, threshold, zeta, eta, frozen
+    assert L.phb_struct_sizes(None, 3) == 1 and L.phb_struct_sizes(out, 4) == 1

@@ -46,6 +46,61 @@ def test_uniform_flow_advects_exactly():
     np.testing.assert_array_equal(pos, w.pos + dt * w.U[1:4])
 
 
+def test_frozen_particles_in_uniform_flow():
+    """Frozen particles keep x and U bit for bit; the others still advect by V dt
+    exactly (every right-hand side vanishes in a uniform state)."""
+    phb = need_gpu()
+    w = workloads.linear_wave(8, amplitude=0.0)
+    w.U[1:4] = np.array([[0.25], [-0.125], [0.5]])
+    frozen = np.random.default_rng(5).random(w.n) < 0.3
+    dt = 0.015625
+    plan = phb.Plan.for_workload(w, skin=0.05)
+    pos, lam, U = phb.tensors_of(w)
+    prm = phb.Params(gamma=w.gamma, frozen=torch.from_numpy(frozen).cuda())
+    phb.pc_step(plan, prm, pos, lam, U, dt)
+    assert plan.read_status() == 0
+    pos, U = pos.cpu().numpy(), U.cpu().numpy()
+    np.testing.assert_array_equal(U, w.U)
+    np.testing.assert_array_equal(pos[:, frozen], w.pos[:, frozen])
+    np.testing.assert_array_equal(pos[:, ~frozen], w.pos[:, ~frozen] + dt * w.U[1:4, ~frozen])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_mixed", 1e-5)])
+def test_frozen_mask_matches_oracle(prec, tol):
+    """A frozen shell around a moving interior (the fixed-value boundary of the
+    Sec. 3 tests): frozen particles keep their state exactly, the interior
+    matches the oracle's masked step, also when replayed from a CUDA graph."""
+    phb = need_gpu()
+    w = workloads.random_modes(10, seed=24, amp=0.05)
+    c = w.box_lo + 0.5 * w.box_len
+    r = np.sqrt(((w.pos - c[:, None]) ** 2).sum(0))
+    frozen = r > 0.4 * w.box_len.min()
+    dt, skin = 0.002, 0.01
+    box = oracle.box_of(w)
+    op, oU, ns = oracle.pc_step(box, w.pos, w.lam, w.U, dt, gamma=w.gamma, frozen=frozen)
+    assert ns == 0
+    g, h, _ = oracle.mls_derivs(box, w.pos, w.lam, w.U, oracle.neighbors(box, w.pos, w.lam),
+                                gamma=w.gamma)
+    sc = dt * rhs_term_scales(w.U, g, h, w.gamma)
+    mask = torch.from_numpy(frozen.astype(np.uint8)).cuda()
+    prm = phb.Params(gamma=w.gamma, precision=prec, frozen=mask)
+    for graph in (False, True):
+        plan = phb.Plan.for_workload(w, skin=skin)
+        pos, lam, U = phb.tensors_of(w)
+        if graph:
+            phb.build_neighbors(plan, pos, lam)
+            phb.StepGraph(plan, prm, pos, lam, U, dt, steps=1).replay()
+        else:
+            phb.pc_step(plan, prm, pos, lam, U, dt)
+        assert plan.read_status() == 0
+        pos, U = pos.cpu().numpy(), U.cpu().numpy()
+        assert np.array_equal(pos[:, frozen], w.pos[:, frozen])
+        assert np.array_equal(U[:, frozen], w.U[:, frozen])
+        m = ~frozen
+        assert rhs_err((U - w.U)[:, m], (oU - w.U)[:, m], sc).max() < tol
+        assert kind_err((pos - w.pos)[:, m], (op - w.pos)[:, m]).max() < tol
+
+
 def test_skin_violation_is_flagged():
     phb = need_gpu()
     from paper_1110_0836_gb300 import _lib
@@ -99,11 +154,22 @@ def test_autotune_returns_a_timed_candidate(tmp_path, monkeypatch):
     assert again == res   # served from the cache file
 
 
-def _evolve_wave(phb, n_side, prec, cfl=0.05, jitter=0.1):
-    """One period of the App. A fast magnetosonic wave (amplitude 1e-6) with
-    the predictor-corrector step; mean |U - U_exact| / amplitude summed over
-    the eight fields, against the travelling eigenmode sin(k x - omega t)."""
-    w = workloads.linear_wave(n_side, jitter=jitter)
+# Sec. 3.1 setups (rho = 1, P = 1 / gamma, gamma = 5/3, propagation along x)
+# and the oblique fast wave of the workload generator.
+WAVES = {
+    "magnetoacoustic": dict(mode="fast", B0=(0.0, 0.0, np.sqrt(3.0)), P0=0.6),
+    "alfven": dict(mode="alfven", B0=(1.0, 0.0, 0.0), P0=0.6),
+    "sound": dict(mode="fast", B0=(0.0, 0.0, 0.0), P0=0.6),
+    "oblique_fast": dict(mode="fast"),
+}
+
+
+def _evolve_wave(phb, n_side, prec, wave, cfl=0.05, jitter=0.1):
+    """One period of an App. A eigenmode (amplitude 1e-6) with the
+    predictor-corrector step; mean |U - U_exact| / amplitude summed over the
+    eight fields (the relative L1 error of Sec. 3.1), against the travelling
+    eigenmode sin(k x - omega t)."""
+    w = workloads.linear_wave(n_side, jitter=jitter, **WAVES[wave])
     m = w.meta
     om, k, A, vhat = m["omega"], m["k"], m["amplitude"], m["vhat"]
     T = 2 * np.pi / om
@@ -128,14 +194,16 @@ def _evolve_wave(phb, n_side, prec, cfl=0.05, jitter=0.1):
     return float((np.abs(U.cpu().numpy() - ex).mean(axis=1) / A).sum())
 
 
-def test_linear_wave_convergence_and_mixed_precision():
-    """Time-evolved linear wave (App. A; Sec. 3.1 shapes): the error after one
-    period falls at least second order from 16^3 to 32^3 jittered lattices,
-    and the FP32-mixed path tracks the FP64 path on the 1e-6 signal."""
+@pytest.mark.parametrize("wave", sorted(WAVES))
+def test_linear_wave_convergence_and_mixed_precision(wave):
+    """Time-evolved linear waves (Sec. 3.1, App. A): after one period the
+    relative L1 error falls at least second order from 16^3 to 32^3 jittered
+    lattices (CFL 0.05, so that the spatial error dominates), and the
+    FP32-mixed path tracks the FP64 path on the 1e-6 signal."""
     phb = need_gpu()
-    e16 = _evolve_wave(phb, 16, "fp64")
-    e32 = _evolve_wave(phb, 32, "fp64")
+    e16 = _evolve_wave(phb, 16, "fp64", wave)
+    e32 = _evolve_wave(phb, 32, "fp64", wave)
     order = np.log2(e16 / e32)
     assert order >= 2.0, (e16, e32, order)
-    m32 = _evolve_wave(phb, 32, "fp32_mixed")
+    m32 = _evolve_wave(phb, 32, "fp32_mixed", wave)
     assert abs(m32 - e32) <= 0.02 * e32, (m32, e32)
