@@ -400,7 +400,7 @@ def run_ours(args):
     # Graph replays cannot carry the library's per-launch event trace, so with a
     # graph the fused-fit launches are timed on an eager pass over the same
     # steps right after the timed region (same kernels, same inputs).
-    cap = 4 * args.steps + 16
+    cap = 8 * args.steps + 16
     tr_ms = (C.c_float * cap)()
     tr_id = (C.c_int32 * cap)()
     ms = []
@@ -437,6 +437,8 @@ def run_ours(args):
         eager_ms = ms
     ntr = L.phb_trace_stop(tr_ms, tr_id, cap)
     fit_ms = [tr_ms[k] for k in range(max(ntr, 0)) if tr_id[k] == 1]
+    search_ms = [tr_ms[k] for k in range(max(ntr, 0)) if tr_id[k] == 4]
+    compact_ms = [tr_ms[k] for k in range(max(ntr, 0)) if tr_id[k] == 5]
     clocks = clk.summary()
     status = plan.read_status()
     if status & ~_lib.FLAG_FIT_SINGULAR:
@@ -646,7 +648,9 @@ def run_ours(args):
                  "speedup_fp32_mixed_over_fp64": value / value64},
         "rhs_only": {"fp32_mixed_ms": rhs32_ms, "fp64_ms": rhs64_ms,
                      "fp32_mixed_value": n / (rhs32_ms * 1e-3), "fp64_value": n / (rhs64_ms * 1e-3),
-                     "neighbour_build_ms": build_ms},
+                     "neighbour_build_ms": build_ms,
+                     "search_ms_in_step": float(np.mean(search_ms)) if search_ms else None,
+                     "compaction_ms_in_step": float(np.mean(compact_ms)) if compact_ms else None},
         "adjoint": adjoint,
         "err_vs_oracle": err,
         "routed_to_fp64": routed,

@@ -27,15 +27,17 @@ int phb_fma_peak(int32_t precision, int32_t blocks, int32_t iters, void* sink, p
  * incremented at every launch site). */
 int64_t phb_launch_count(void);
 
-/* Event trace of the fused fit kernel.  phb_trace_start(capacity) creates
- * `capacity` CUDA event pairs (timing enabled) on the current device and arms
- * the trace; every later launch of the fused FP32-mixed or FP64 fit kernel
- * records one pair around itself on its own stream, until the pairs run out.
- * phb_trace_stop(ms, kernel_ids, capacity) synchronises on the last recorded
- * event, writes each launch's duration in milliseconds and kernel id (1 =
- * FP32-mixed fused fit, 2 = FP64 fused fit over all particles, 3 = FP64 fit of
- * the routed queue), destroys the events and returns the number of launches
- * recorded (or -1 on a CUDA error).  Not thread-safe; one trace at a time. */
+/* Event trace of the fused fit and the neighbour search kernels.
+ * phb_trace_start(capacity) creates `capacity` CUDA event pairs (timing
+ * enabled) on the current device and arms the trace; every later launch of a
+ * traced kernel records one pair around itself on its own stream, until the
+ * pairs run out.  phb_trace_stop(ms, kernel_ids, capacity) synchronises on
+ * the last recorded event, writes each launch's duration in milliseconds and
+ * kernel id (1 = FP32-mixed fused fit, 2 = FP64 fused fit over all particles,
+ * 3 = FP64 fit of the routed queue, 4 = neighbour search, 5 = list
+ * compaction and tile plans), destroys the events and returns the number of
+ * launches recorded (or -1 on a CUDA error).  Not thread-safe; one trace at a
+ * time. */
 int phb_trace_start(int32_t capacity);
 
 /* Copy diagnostic counters of the last operations on a workspace to the host

@@ -19,9 +19,9 @@ FLAG_BAD_INDEX = 0x40
 PHB_FP64, PHB_FP32_MIXED = 0, 1
 # ws_off index where the workspace part shared by neighbour build, fit and RHS ends
 # (position of R_END_COMMON in the library's region enumeration)
-WS_END_COMMON = 36
+WS_END_COMMON = 38
 # first and last adjoint regions (R_ADJ_EDGE, R_ADJ_SELF; the latter holds 11 doubles per particle)
-WS_ADJ_EDGE, WS_ADJ_SELF = 30, 35
+WS_ADJ_EDGE, WS_ADJ_SELF = 32, 37
 
 EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_check",
            "phb_build_neighbors", "phb_export_neighbors", "phb_neighbor_total", "phb_mls_derivs",

@@ -36,6 +36,8 @@ enum Region {
   R_LIDX,        // uint16 [capacity] neighbour index inside the tile's staged neighbourhood
   R_CELLC,       // int32 [n] packed cell coordinates of each slot (10 bits per axis)
   R_CLIN,        // int2 [cells] (first slot, count) per linear cell index (x-major)
+  R_LSTART,      // int32 [cells+1] first record of each cell in linear cell order
+  R_LSCR,        // float4 [n+4] screen records in linear cell order, slot in w (+ padding)
   R_TORDER,      // int32 [ntiles] tiles in descending cost class (persistent schedule)
   R_ELL,         // int32 [n][ell_width] first list entries of each slot (single-pass search)
   R_TPLAN,       // int2 [ntiles] (staged particles, 1 = not staged) of each tile's neighbourhood

@@ -12,6 +12,7 @@ namespace phb {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kOwnerCap = 8192;  // list entries of a tile mapped to their particle in shared memory
 
 inline unsigned blocks_for(int64_t n, int t = kThreads) { return static_cast<unsigned>((n + t - 1) / t); }
 
@@ -85,10 +86,14 @@ __global__ void k_gather_pos(Grid g, const int32_t* __restrict__ perm, const dou
   cellc[s] = pack_cell(c[0], c[1], c[2]);
 }
 
-// (first slot, count) of every cell by linear index, for the tile planner.
-__global__ void k_cell_lin(Grid g, const int32_t* __restrict__ cell_start, int2* __restrict__ clin) {
+// (first slot, count) of every cell by linear index, for the tile planner and
+// the search; the counts also go to lcnt[k] (lcnt[total] = 0), whose
+// exclusive scan places the cells in linear order for the run search.
+__global__ void k_cell_lin(Grid g, const int32_t* __restrict__ cell_start, int2* __restrict__ clin,
+                           int32_t* __restrict__ lcnt) {
   const int64_t total = static_cast<int64_t>(g.ncell[0]) * g.ncell[1] * g.ncell[2];
   const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k == total) lcnt[k] = 0;
   if (k >= total) return;
   const int cz = static_cast<int>(k % g.ncell[2]);
   const int cy = static_cast<int>((k / g.ncell[2]) % g.ncell[1]);
@@ -96,6 +101,24 @@ __global__ void k_cell_lin(Grid g, const int32_t* __restrict__ cell_start, int2*
   const int32_t key = cell_key(g, cx, cy, cz);
   const int a = cell_start[key];
   clin[k] = make_int2(a, cell_start[key + 1] - a);
+  lcnt[k] = cell_start[key + 1] - a;
+}
+
+// Screen records in linear cell order (z fastest; slot order inside a cell),
+// with the slot in w, plus four padding records: the cells of one (x, y) row
+// of a reach box are then one contiguous run.  lstart: exclusive scan of the
+// linear-order counts.
+__global__ void k_fill_lin(Grid g, const int32_t* __restrict__ cellc, const int2* __restrict__ clin,
+                           const int32_t* __restrict__ lstart, const float4* __restrict__ scr,
+                           float4* __restrict__ lscr) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.n) return;
+  int cx, cy, cz;
+  unpack_cell(cellc[s], cx, cy, cz);
+  const int64_t k = (static_cast<int64_t>(cx) * g.ncell[1] + cy) * g.ncell[2] + cz;
+  const float4 o = scr[s];
+  lscr[lstart[k] + (s - clin[k].x)] = make_float4(o.x, o.y, o.z, __int_as_float(s));
+  if (s < 4) lscr[g.n + s] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));  // batch padding
 }
 
 struct Reach {
@@ -152,6 +175,19 @@ __device__ __forceinline__ Screen make_screen(const Grid& g, double r) {
     q.invlf[a] = g.periodic[a] ? static_cast<float>(1.0 / g.len[a]) : 0.f;
   }
   return q;
+}
+
+// FP32 screen distance squared (the same arithmetic as is_neighbour): below
+// q.in2 a neighbour, above q.out2 not, in between the exact test decides.
+template <bool kWrap>
+__device__ __forceinline__ float screen_d2(const Screen& q, float4 me, float4 o) {
+  float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
+  if (kWrap) {
+    dx = fmaf(-q.lenf[0], rintf(dx * q.invlf[0]), dx);
+    dy = fmaf(-q.lenf[1], rintf(dy * q.invlf[1]), dy);
+    dz = fmaf(-q.lenf[2], rintf(dz * q.invlf[2]), dz);
+  }
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
 template <bool kWrap>
@@ -277,8 +313,112 @@ __device__ int search_one(const Grid& g, const int2* __restrict__ clin, const fl
   return count;
 }
 
+// Candidate records in linear cell order (k_fill_lin) and the cells' starts.
+struct Lin {
+  const float4* __restrict__ rec;
+  const int32_t* __restrict__ start;
+};
+
+// The same list as search_one (cells in x, y, z order of the reach box,
+// slot order inside a cell), for reaches that do not cover a whole periodic
+// axis: the z cells of one (x, y) row are read as one run of the linear-order
+// records (two where the row wraps a periodic z boundary), four candidates
+// per batch so that their loads overlap.
+template <int OUT, bool kWrap>
+__device__ int search_runs(const Grid& g, const Lin& lin, const double* __restrict__ spos,
+                           const Screen& q, const Cull& cu, const Reach& qx, const Reach& qy,
+                           const Reach& qz, float4 me, int s, int64_t base, int64_t end,
+                           int32_t* __restrict__ out) {
+  const int Rx = qx.count / 2, Ry = qy.count / 2, Rz = qz.count / 2;
+  const int ncz = g.ncell[2];
+  int count = 0;
+  auto take = [&](int t) {
+    if (OUT == kFillCsr) {
+      const int64_t e = base + count;
+      if (e < g.capacity && e < end) out[e] = t;
+    } else if (OUT == kFillEll) {
+      if (count < g.ell) out[count] = t;
+    }
+    ++count;
+  };
+  for (int kx = 0; kx < qx.count; ++kx) {
+    bool okx;
+    const int cx = axis_cell(g, 0, qx, kx, okx);
+    if (!okx) continue;
+    const float dx = cull_d(cu, 0, kx - Rx);
+    const float rx = cu.rr - dx * dx;
+    if (rx < 0.f) continue;
+    for (int ky = 0; ky < qy.count; ++ky) {
+      bool oky;
+      const int cy = axis_cell(g, 1, qy, ky, oky);
+      if (!oky) continue;
+      const float dy = cull_d(cu, 1, ky - Ry);
+      const float ry = rx - dy * dy;
+      if (ry < 0.f) continue;
+      const float sz = sqrtf(ry) / cu.cell[2];
+      const int hi = static_cast<int>(floorf(sz + cu.f[2]));
+      const int lo = -static_cast<int>(floorf(sz + 1.f - cu.f[2]));
+      int za = qz.start + max(0, lo + Rz), zb = qz.start + min(qz.count - 1, hi + Rz);
+      // up to two runs of cells [a0, b0], [a1, b1], in the order of the reach offsets
+      int a0 = za, b0 = zb, a1 = 0, b1 = -1;
+      if (!qz.wrap) {
+        a0 = max(za, 0);
+        b0 = min(zb, ncz - 1);
+      } else if (za < 0) {  // wraps below: cells ncz + za .., then 0 .. zb
+        a0 = za + ncz;
+        b0 = zb < 0 ? zb + ncz : ncz - 1;
+        b1 = zb < 0 ? -1 : zb;
+      } else if (zb >= ncz) {  // wraps above: cells za .. ncz - 1, then 0 .. zb - ncz
+        a0 = za < ncz ? za : za - ncz;
+        b0 = za < ncz ? ncz - 1 : zb - ncz;
+        b1 = za < ncz ? zb - ncz : -1;
+      }
+      const int nseg = (a0 <= b0 ? 1 : 0) + (a1 <= b1 ? 1 : 0);
+      if (a0 > b0) { a0 = a1; b0 = b1; }
+      const int64_t row = (static_cast<int64_t>(cx) * g.ncell[1] + cy) * ncz;
+      for (int k = 0; k < nseg; ++k) {
+        const int t0 = lin.start[row + (k == 0 ? a0 : a1)];
+        const int t1 = lin.start[row + (k == 0 ? b0 : b1) + 1];
+        // batches of four (the records array is padded by four, so a batch
+        // may read past the run): the screen sets a hit bit (inside the
+        // inner radius) or an ambiguous bit (inside the band), the exact FP64
+        // test settles the rare ambiguous ones, hits are then taken in order
+        for (int t = t0; t < t1; t += 4) {
+          const float4* rp = lin.rec + t;
+          const float4 o0 = rp[0], o1 = rp[1], o2 = rp[2], o3 = rp[3];
+          const unsigned live = t1 - t >= 4 ? 0xfu : (1u << (t1 - t)) - 1u;
+          const float d0 = screen_d2<kWrap>(q, me, o0), d1 = screen_d2<kWrap>(q, me, o1);
+          const float d2 = screen_d2<kWrap>(q, me, o2), d3 = screen_d2<kWrap>(q, me, o3);
+          const unsigned self = (__float_as_int(o0.w) == s ? 1u : 0u) | (__float_as_int(o1.w) == s ? 2u : 0u) |
+                                (__float_as_int(o2.w) == s ? 4u : 0u) | (__float_as_int(o3.w) == s ? 8u : 0u);
+          const unsigned in = (d0 < q.in2 ? 1u : 0u) | (d1 < q.in2 ? 2u : 0u) | (d2 < q.in2 ? 4u : 0u) |
+                              (d3 < q.in2 ? 8u : 0u);
+          const unsigned out = (d0 <= q.out2 ? 1u : 0u) | (d1 <= q.out2 ? 2u : 0u) |
+                               (d2 <= q.out2 ? 4u : 0u) | (d3 <= q.out2 ? 8u : 0u);
+          const unsigned keep = live & ~self;
+          unsigned hit = in & keep;
+          const unsigned amb = out & ~in & keep;
+          if (amb) {
+            if ((amb & 1u) && dist2_exact(g, spos, g.n, s, __float_as_int(o0.w)) < q.r2) hit |= 1u;
+            if ((amb & 2u) && dist2_exact(g, spos, g.n, s, __float_as_int(o1.w)) < q.r2) hit |= 2u;
+            if ((amb & 4u) && dist2_exact(g, spos, g.n, s, __float_as_int(o2.w)) < q.r2) hit |= 4u;
+            if ((amb & 8u) && dist2_exact(g, spos, g.n, s, __float_as_int(o3.w)) < q.r2) hit |= 8u;
+          }
+          if (hit) {
+            if (hit & 1u) take(__float_as_int(o0.w));
+            if (hit & 2u) take(__float_as_int(o1.w));
+            if (hit & 4u) take(__float_as_int(o2.w));
+            if (hit & 8u) take(__float_as_int(o3.w));
+          }
+        }
+      }
+    }
+  }
+  return count;
+}
+
 template <int OUT>
-__device__ int search_particle(const Grid& g, const int2* __restrict__ clin,
+__device__ int search_particle(const Grid& g, const int2* __restrict__ clin, const Lin& lin,
                                const int32_t* __restrict__ cellc, const float4* __restrict__ scr,
                                const double* __restrict__ spos, double r, int s, int64_t base,
                                int64_t end, int32_t* __restrict__ out) {
@@ -289,15 +429,32 @@ __device__ int search_particle(const Grid& g, const int2* __restrict__ clin,
   const Reach qy = axis_reach(g, 1, c[1], r);
   const Reach qz = axis_reach(g, 2, c[2], r);
   const Cull cu = make_cull(g, spos, s, c, qx, qy, qz, r);
-  if (plain_axis(g, 0, c[0], qx) && plain_axis(g, 1, c[1], qy) && plain_axis(g, 2, c[2], qz))
-    return search_one<OUT, false>(g, clin, scr, spos, q, cu, qx, qy, qz, s, base, end, out);
+  const bool plain =
+      plain_axis(g, 0, c[0], qx) && plain_axis(g, 1, c[1], qy) && plain_axis(g, 2, c[2], qz);
+  if (cu.on[0] && cu.on[1] && cu.on[2]) {
+    const float4 me = scr[s];
+    if (plain) return search_runs<OUT, false>(g, lin, spos, q, cu, qx, qy, qz, me, s, base, end, out);
+    return search_runs<OUT, true>(g, lin, spos, q, cu, qx, qy, qz, me, s, base, end, out);
+  }
+  // a reach covering a whole periodic axis: cell by cell
+  if (plain) return search_one<OUT, false>(g, clin, scr, spos, q, cu, qx, qy, qz, s, base, end, out);
   return search_one<OUT, true>(g, clin, scr, spos, q, cu, qx, qy, qz, s, base, end, out);
+}
+
+// The CSR fill of one list longer than the scratch rows (rare): kept out of
+// line so that it does not weigh on the compaction kernel's registers.
+__device__ __noinline__ void search_overflow(const Grid& g, const int2* __restrict__ clin, Lin lin,
+                                             const int32_t* __restrict__ cellc,
+                                             const float4* __restrict__ scr,
+                                             const double* __restrict__ spos, double r, int s,
+                                             int64_t base, int64_t end, int32_t* __restrict__ out) {
+  search_particle<kFillCsr>(g, clin, lin, cellc, scr, spos, r, s, base, end, out);
 }
 
 // Single pass, thread per particle (slot order): exact list lengths and the
 // first g.ell entries of every list.
 __global__ void __launch_bounds__(kThreads, 3) k_search_ell(Grid g, const int2* __restrict__ clin,
-                                                         const int32_t* __restrict__ cellc,
+                                                         Lin lin, const int32_t* __restrict__ cellc,
                                                          const float4* __restrict__ scr,
                                                          const double* __restrict__ spos,
                                                          const double* __restrict__ slam,
@@ -306,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_ell(Grid g, const int2* 
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.n) return;
   const double r = list_radius(g, slam[s]);
-  ncnt[s] = search_particle<kFillEll>(g, clin, cellc, scr, spos, r, s, 0, 0,
+  ncnt[s] = search_particle<kFillEll>(g, clin, lin, cellc, scr, spos, r, s, 0, 0,
                                       ell + static_cast<int64_t>(s) * g.ell);
 }
 
@@ -317,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_ell(Grid g, const int2* 
 // index, each tile particle's own staged index - and map every list entry to
 // its staged index.
 template <int T>
-__global__ void __launch_bounds__(T) k_compact(Grid g, const int2* __restrict__ clin,
+__global__ void __launch_bounds__(T, 768 / T) k_compact(Grid g, const int2* __restrict__ clin, Lin lin,
                                                const int32_t* __restrict__ cellc,
                                                const float4* __restrict__ scr,
                                                const double* __restrict__ spos,
@@ -337,6 +494,7 @@ __global__ void __launch_bounds__(T) k_compact(Grid g, const int2* __restrict__ 
   __shared__ int warp_tmp[T / 32 + 1];
   __shared__ int64_t toff[T + 1];
   __shared__ int tlen[T];
+  __shared__ uint8_t owner[kOwnerCap];
   const TileArrays tarr{bits, wpre, base, cstart, warp_tmp};
   const int n = g.n;
   const int tid = threadIdx.x;
@@ -361,7 +519,7 @@ __global__ void __launch_bounds__(T) k_compact(Grid g, const int2* __restrict__ 
     const int s = s0 + tid;
     if (toff[tid + 1] > g.capacity) raise_flag(status_word, PHB_FLAG_CAPACITY);
     if (ncnt[s] > g.ell)
-      search_particle<kFillCsr>(g, clin, cellc, scr, spos, list_radius(g, slam[s]), s, toff[tid],
+      search_overflow(g, clin, lin, cellc, scr, spos, list_radius(g, slam[s]), s, toff[tid],
                                 toff[tid + 1], idx);
   }
   tile_plan<T>(g, s0, cnt, cellc, slam, clin, ts, tarr);
@@ -382,29 +540,41 @@ __global__ void __launch_bounds__(T) k_compact(Grid g, const int2* __restrict__ 
       lself[s] = static_cast<uint16_t>(base[j] + (s - cstart[j]));
     }
   }
+  // the tile's entries [e0, e1) as one flat range over the block (each
+  // entry's tile particle from a byte map, or a binary search of the offsets
+  // when the tile has more entries than the map holds)
   const int64_t e0 = toff[0];
   const int64_t e1 = toff[cnt] < g.capacity ? toff[cnt] : g.capacity;
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int p = warp; p < cnt; p += T / 32) {
-    const int s = s0 + p;
-    const int m = tlen[p];
-    const bool over = m > g.ell;
-    const int64_t eb = toff[p];
-    const int64_t row = static_cast<int64_t>(s) * g.ell;
-    for (int k = lane; k < m; k += 32) {
-      const int64_t e = eb + k;
-      if (e >= e1) break;
-      int t;
-      if (over) {
-        t = idx[e];
-      } else {
-        t = ell[row + k];
-        idx[e] = t;
+  const bool mapped = e1 - e0 <= kOwnerCap;
+  if (mapped && tid < cnt) {
+    const int64_t a = toff[tid], b = toff[tid + 1] < e1 ? toff[tid + 1] : e1;
+    for (int64_t e = a; e < b; ++e) owner[e - e0] = static_cast<uint8_t>(tid);
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int64_t e = e0 + tid; e < e1; e += T) {
+    int p;
+    if (mapped) {
+      p = owner[e - e0];
+    } else {
+      int lo = 0, hi = cnt - 1;  // the last p with toff[p] <= e
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (toff[mid] <= e) lo = mid; else hi = mid - 1;
       }
-      if (staged) {
-        const int j = marked_index(tarr, box_index(g, ts, cellc[t]));
-        lidx[e] = static_cast<uint16_t>(base[j] + (t - cstart[j]));
-      }
+      p = lo;
+    }
+    const int k = static_cast<int>(e - toff[p]);
+    int t;
+    if (tlen[p] > g.ell) {
+      t = idx[e];
+    } else {
+      t = ell[static_cast<int64_t>(s0 + p) * g.ell + k];
+      idx[e] = t;
+    }
+    if (staged) {
+      const int j = marked_index(tarr, box_index(g, ts, cellc[t]));
+      lidx[e] = static_cast<uint16_t>(base[j] + (t - cstart[j]));
     }
   }
 }
@@ -508,11 +678,19 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   k_gather_pos<<<blocks_for(n), kThreads, 0, st>>>(g, perm, pos, lam, inv, spos, slam, scr, cellc);
   note_launch();
   const int64_t ncells = int64_t(p->ncell[0]) * p->ncell[1] * p->ncell[2];
-  k_cell_lin<<<blocks_for(ncells), kThreads, 0, st>>>(g, cell, clin);
+  int32_t* lstart = region<int32_t>(p, ws, R_LSTART);
+  float4* lscr = region<float4>(p, ws, R_LSCR);
+  k_cell_lin<<<blocks_for(ncells + 1), kThreads, 0, st>>>(g, cell, clin, lstart);
   note_launch();
+  if ((e = scan_exclusive_i32(lstart, ncells + 1, bsum, st))) return e;
+  k_fill_lin<<<blocks_for(n), kThreads, 0, st>>>(g, cellc, clin, lstart, scr, lscr);
+  note_launch();
+  const Lin lin{lscr, lstart};
   if ((e = cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), st))) return e;
   int32_t* ell = region<int32_t>(p, ws, R_ELL);
-  k_search_ell<<<blocks_for(n), kThreads, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, ell);
+  int tr = trace_begin(4, st);
+  k_search_ell<<<blocks_for(n), kThreads, 0, st>>>(g, clin, lin, cellc, scr, spos, slam, ncnt, ell);
+  trace_end(tr, st);
   note_launch();
   if ((e = cudaMemsetAsync(ncnt + n, 0, sizeof(int32_t), st))) return e;
   if ((e = scan_exclusive_i32_to_i64(ncnt, off, n + 1, bsum, st))) return e;
@@ -521,12 +699,14 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   int32_t* tslot = region<int32_t>(p, ws, R_TSLOT);
   uint16_t* lself = region<uint16_t>(p, ws, R_LSELF);
   uint8_t* tmap = region<uint8_t>(p, ws, R_TMAP);
+  tr = trace_begin(5, st);
   if (p->tile == 128)
-    k_compact<128><<<tiles, 128, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, ell, off, idx, lidx,
+    k_compact<128><<<tiles, 128, 0, st>>>(g, clin, lin, cellc, scr, spos, slam, ncnt, ell, off, idx, lidx,
                                           tplan, tslot, lself, tmap, misc + 1, status_word);
   else
-    k_compact<64><<<tiles, 64, 0, st>>>(g, clin, cellc, scr, spos, slam, ncnt, ell, off, idx, lidx,
+    k_compact<64><<<tiles, 64, 0, st>>>(g, clin, lin, cellc, scr, spos, slam, ncnt, ell, off, idx, lidx,
                                         tplan, tslot, lself, tmap, misc + 1, status_word);
+  trace_end(tr, st);
   note_launch();
   k_tile_order<<<1, 1024, 0, st>>>(n, p->tile, p->ntiles, p->nbr_capacity, off,
                                    region<int32_t>(p, ws, R_TORDER));

@@ -246,6 +246,8 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   sz[R_LIDX] = cap * 2;
   sz[R_CELLC] = n * 4;
   sz[R_CLIN] = size_t(p->ncell[0]) * p->ncell[1] * p->ncell[2] * 8;
+  sz[R_LSTART] = (size_t(p->ncell[0]) * p->ncell[1] * p->ncell[2] + 1) * 4;
+  sz[R_LSCR] = size_t(n + 4) * 16;
   sz[R_TORDER] = size_t(p->ntiles) * 4;
   sz[R_ELL] = size_t(n) * p->ell_width * 4;
   sz[R_TPLAN] = size_t(p->ntiles) * 8;

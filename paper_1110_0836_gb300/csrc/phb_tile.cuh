@@ -51,8 +51,12 @@ __device__ __forceinline__ int box_coord(const Grid& g, const TileShared& ts, in
   int d = c - ts.lo[a];
   if (g.periodic[a]) {
     const int nc = g.ncell[a];
-    d %= nc;
     if (d < 0) d += nc;
+    else if (d >= nc) d -= nc;
+    if (static_cast<unsigned>(d) >= static_cast<unsigned>(nc)) {  // only for reaches beyond a box length
+      d %= nc;
+      if (d < 0) d += nc;
+    }
   }
   return d;
 }
