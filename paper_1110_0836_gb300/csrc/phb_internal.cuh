@@ -73,7 +73,7 @@ __host__ __device__ inline const T* region(const phb_plan* p, const void* ws, Re
 
 // Plain-old-data view of the plan handed to kernels by value.
 struct Grid {
-  double lo[3], len[3], inv_cell[3], cell[3];
+  double lo[3], len[3], inv_cell[3], cell[3], inv_ncell[3];
   int32_t periodic[3], ncell[3], nbrick[3];
   int32_t hbits;      // Hilbert order of the brick curve
   int32_t tile;       // particles per tile
@@ -96,17 +96,36 @@ __device__ __forceinline__ void raise_flag(int32_t* status_word, int32_t bits) {
   if (status_word) atomicOr(status_word, bits);
 }
 
-// Cell coordinate on one axis: floor((x - lo) / cell), wrapped (periodic) or
-// clamped (open) into [0, ncell).
-__device__ __forceinline__ int cell_coord(const Grid& g, int a, double x) {
-  double u = floor((x - g.lo[a]) * g.inv_cell[a]);
-  int nc = g.ncell[a];
+// Cell coordinate on one axis and the matching wrap count k: with
+// u = floor((x - lo) / cell) (reciprocal cell edge), a periodic axis gives
+// c = u - k nc, k = floor(u / nc) in exact integer-valued FP64, and the
+// wrapped position x - k len lies in cell c up to the rounding of that
+// subtraction - the cell and the wrapped position never disagree by a box
+// length, also for a particle at lo + len exactly.  An open axis clamps c into
+// [0, ncell) with k = 0.  x must be finite.
+__device__ __forceinline__ int cell_wrap(const Grid& g, int a, double x, double& k_out) {
+  const double u = floor((x - g.lo[a]) * g.inv_cell[a]);
+  const int nc = g.ncell[a];
   if (g.periodic[a]) {
-    double w = u - nc * floor(u / nc);
-    int c = static_cast<int>(w);
-    return c >= nc ? nc - 1 : (c < 0 ? 0 : c);
+    double k = floor(u * g.inv_ncell[a]);
+    double c = u - k * nc;
+    if (c < 0) {
+      c += nc;
+      k -= 1;
+    } else if (c >= nc) {
+      c -= nc;
+      k += 1;
+    }
+    k_out = k;
+    return static_cast<int>(c);
   }
+  k_out = 0.0;
   return u < 0 ? 0 : (u >= nc ? nc - 1 : static_cast<int>(u));
+}
+
+__device__ __forceinline__ int cell_coord(const Grid& g, int a, double x) {
+  double k;
+  return cell_wrap(g, a, x, k);
 }
 
 // Index of brick (x, y, z) along a 3-D Hilbert curve of order b (2^b bricks per

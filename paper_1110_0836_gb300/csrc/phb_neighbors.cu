@@ -62,7 +62,7 @@ __global__ void k_rank_cells(int n, const int32_t* __restrict__ keys,
 }
 
 // Slot-order copies of positions and lambda, the inverse permutation and the
-// wrapped FP32 screen positions.
+// wrapped FP32 screen positions (wrapped by the same count as the cell).
 __global__ void k_gather_pos(Grid g, const int32_t* __restrict__ perm, const double* __restrict__ pos,
                              const double* __restrict__ lam, int32_t* __restrict__ inv,
                              double* __restrict__ spos, double* __restrict__ slam,
@@ -75,11 +75,11 @@ __global__ void k_gather_pos(Grid g, const int32_t* __restrict__ perm, const dou
   float w[3];
   int c[3];
   for (int a = 0; a < 3; ++a) {
-    double x = pos[a * n + i];
+    const double x = pos[a * n + i];
     spos[a * n + s] = x;
-    double xw = g.periodic[a] ? x - g.len[a] * floor((x - g.lo[a]) / g.len[a]) : x;
-    w[a] = static_cast<float>(xw);
-    c[a] = isfinite(x) ? cell_coord(g, a, x) : 0;
+    double k = 0.0;
+    c[a] = isfinite(x) ? cell_wrap(g, a, x, k) : 0;
+    w[a] = static_cast<float>(__dsub_rn(x, __dmul_rn(k, g.len[a])));
   }
   slam[s] = lam[i];
   scr[s] = make_float4(w[0], w[1], w[2], 0.f);

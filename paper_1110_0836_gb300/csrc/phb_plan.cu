@@ -23,6 +23,7 @@ Grid make_grid(const phb_plan* p) {
     g.lo[a] = p->box.lo[a];
     g.len[a] = p->box.len[a];
     g.inv_cell[a] = 1.0 / p->cell[a];
+    g.inv_ncell[a] = 1.0 / p->ncell[a];
     g.cell[a] = p->cell[a];
     g.periodic[a] = p->box.periodic[a] ? 1 : 0;
     g.ncell[a] = p->ncell[a];

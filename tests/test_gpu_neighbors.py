@@ -157,3 +157,30 @@ def test_full_size_density_sampled_sets(name, nq, skin):
     assert cnt.min() >= 5 and cnt.max() < 400 and 40 < cnt.mean() < 70
     del plan, pos, lam, off, idx
     torch.cuda.empty_cache()
+
+
+def test_particles_on_the_periodic_boundary():
+    """Particles at exactly lo + len and lo, and within a cell of them, on a
+    grid whose rounded reciprocal cell edge puts lo + len in the top cell
+    (93 cells per unit length): every set still equals the brute force."""
+    phb = need_gpu()
+    rng = np.random.default_rng(31)
+    n = 6000
+    lam = np.full(n, 1.0 / 215.0)
+    r = 2.3 / 215.0
+    assert int(np.floor(1.0 * (1.0 / (1.0 / 93.0)))) < 93   # the rounding this test is about
+    x = np.concatenate([np.ones(1500), np.zeros(1500), 1.0 - 2 * r * rng.random(1500),
+                        2 * r * rng.random(1500)])
+    y = 0.2 * rng.random(n)
+    z = rng.choice([0.0, 1.0, 0.5], n, p=[0.2, 0.2, 0.6])
+    mid = z == 0.5
+    z[mid] = np.where(rng.random(mid.sum()) < 0.5, 0.2 * rng.random(mid.sum()),
+                      1.0 - 0.2 * rng.random(mid.sum()))
+    pos = np.ascontiguousarray(np.stack([x, y, z]))
+    w = workloads.Workload("edge", np.zeros(3), np.ones(3), np.ones(3, np.int32), pos, lam,
+                           np.ones((8, n)), 5 / 3)
+    got, plan = gpu_sets(phb, w)
+    assert list(plan.c.ncell) == [93, 93, 93]
+    exp = oracle_sets(w)
+    assert sum(len(e) for e in exp) > 10 * n
+    assert_equal_sets(got, exp)
