@@ -39,6 +39,9 @@ __global__ void __launch_bounds__(kT, 1) k_fit_fp64(const FitArgs a, int routed,
   // uniform over the launch; an active subset in FP64 keeps one thread per
   // particle so that its results are bit-identical to the full evaluation
   const int lanes = (routed && list && total <= kWarpQueueMax) ? 32 : 1;
+  // fits routed from the FP32-mixed path need ~1e-5: FP64 normal equations
+  // meet that up to cond(M) ~ 1e9; the FP64 path itself targets ~1e-12
+  const double refine_above = routed ? 1e9 : 1e4;
   const int lane = threadIdx.x % lanes;
   const int groups = kT / lanes;
   const int grp = threadIdx.x / lanes;
@@ -110,43 +113,49 @@ __global__ void __launch_bounds__(kT, 1) k_fit_fp64(const FitArgs a, int routed,
     bool singular = cnt < kNB;
     bool refine = false;
     double invd[kNB];
-    if (lane == 0) {
-      if (!singular) {
-        mls_assemble(*reinterpret_cast<double(*)[kNM]>(hmom), M);
-        const double minpiv = mls_cholesky<double>(M, invd);
-        double rmin = 1e300;
+    if (lane == 0 && !singular) {
+      mls_assemble(*reinterpret_cast<double(*)[kNM]>(hmom), M);
+      const double minpiv = mls_cholesky<double>(M, invd);
+      double rmin = 1e300;
 #pragma unroll
-        for (int k = 0; k < kNB; ++k) {
-          const double r = 1.0 / (invd[k] * invd[k] * M[k * (k + 1) / 2 + k]);
-          rmin = r < rmin ? r : rmin;
-        }
-        // a Jacobi-scaled pivot below 1e-12 (cond(M) above ~1e12) is treated as singular
-        singular = !(minpiv > 0.0) || !(rmin > 1e-12);
-        // normal equations lose cond(M) * eps: above an estimate of 1e4 (n_b
-        // times the greedy ||M_s^-1||_inf estimate) take one corrected
-        // semi-normal-equations step (residuals recomputed from the data)
-        refine = !singular && kNB * mls_inv_norm_est<double>(M, invd) > 1e4;
+      for (int k = 0; k < kNB; ++k) {
+        const double r = 1.0 / (invd[k] * invd[k] * M[k * (k + 1) / 2 + k]);
+        rmin = r < rmin ? r : rmin;
       }
-      // coefficients of every field: the linear and quadratic ones, or all 19
-      // when the fit is refined; kept in the right-hand-side region
-      if (!singular) {
-        for (int f = f0; f < kNF; ++f) {
-          double b[kNB];
-#pragma unroll
-          for (int j = 0; j < kNB; ++j) b[j] = hbs[f * kNB + j];
-          mls_forward(M, invd, b);
-          if (refine) mls_back19(M, invd, b);
-          else mls_back9(M, invd, b);
-#pragma unroll
-          for (int j = 0; j < kNB; ++j) hbs[f * kNB + j] = b[j];
-        }
-      }
+      // a Jacobi-scaled pivot below 1e-12 (cond(M) above ~1e12) is treated as singular
+      singular = !(minpiv > 0.0) || !(rmin > 1e-12);
+      // normal equations lose cond(M) * eps: above an estimate of refine_above
+      // (n_b times the greedy ||M_s^-1||_inf estimate) take one corrected
+      // semi-normal-equations step (residuals recomputed from the data)
+      refine = !singular && kNB * mls_inv_norm_est<double>(M, invd) > refine_above;
+      if (lanes > 1)
+        for (int k = 0; k < kNB; ++k) head[kStride + k] = invd[k];  // lane 1's region is free here
     }
     if (lanes > 1) {
       singular = __shfl_sync(0xffffffffu, singular, 0);
       refine = __shfl_sync(0xffffffffu, refine, 0);
       __syncwarp();
+      if (lane > 0 && lane < kNF - f0 && !singular)
+        for (int k = 0; k < kNB; ++k) invd[k] = head[kStride + k];
+      __syncwarp();
     }
+    // coefficients of every field: the linear and quadratic ones, or all 19
+    // when the fit is refined; kept in the right-hand-side region.  One lane
+    // per field with a warp per particle, all fields in turn otherwise.
+    const int fstep = lanes > 1 ? kNF : 1;
+    if (!singular) {
+      for (int f = f0 + (lanes > 1 ? lane : 0); f < kNF; f += fstep) {
+        double b[kNB];
+#pragma unroll
+        for (int j = 0; j < kNB; ++j) b[j] = hbs[f * kNB + j];
+        mls_forward(M, invd, b);
+        if (refine) mls_back19(M, invd, b);
+        else mls_back9(M, invd, b);
+#pragma unroll
+        for (int j = 0; j < kNB; ++j) hbs[f * kNB + j] = b[j];
+      }
+    }
+    if (lanes > 1) __syncwarp();
     const int dst = a.perm_out ? a.perm_out[s] : s;
     if (refine) {
       // corrected semi-normal equations: one pass over the neighbours per
@@ -176,16 +185,14 @@ __global__ void __launch_bounds__(kT, 1) k_fit_fp64(const FitArgs a, int routed,
           }
         }
         reduce(0, 4 * kNB);
-        if (lane == 0) {
-          for (int f = g0; f < g1; ++f) {
-            double acc[kNB];
+        for (int f = g0 + (lanes > 1 ? lane : 0); f < g1; f += fstep) {
+          double acc[kNB];
 #pragma unroll
-            for (int k = 0; k < kNB; ++k) acc[k] = hmom[(f - g0) * kNB + k];
-            mls_forward(M, invd, acc);
-            mls_back9(M, invd, acc);
+          for (int k = 0; k < kNB; ++k) acc[k] = hmom[(f - g0) * kNB + k];
+          mls_forward(M, invd, acc);
+          mls_back9(M, invd, acc);
 #pragma unroll
-            for (int k = kQuad0; k < kNB; ++k) hbs[f * kNB + k] += acc[k];
-          }
+          for (int k = kQuad0; k < kNB; ++k) hbs[f * kNB + k] += acc[k];
         }
         if (lanes > 1) __syncwarp();
       }
