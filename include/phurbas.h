@@ -169,6 +169,23 @@ phb_status phb_build_neighbors(const phb_plan* plan, const double* pos, const do
                                void* ws, size_t ws_bytes, int32_t* status_word,
                                phb_stream_t stream);
 
+/* Put the caller's particle arrays into the library's storage order - the
+ * cells of the last build along their Hilbert curve, members of a cell by
+ * caller index - as a tree code keeps its particles in Peano-Hilbert order
+ * (Sec. 2.1).  After the call particle i of pos, lambda and U is the one the
+ * last build stored in slot i; the plan's lists already refer to the new
+ * numbering (no rebuild needed), and later builds keep the order up to the
+ * particles' drift, so the gathers from and scatters to the caller's arrays
+ * read and write contiguous runs.  pos [3][n] and lambda [n] must hold the
+ * values of the last phb_build_neighbors call (U [8][n] any); all three are
+ * permuted in place through the workspace.  perm_out (device int32 [n], may
+ * be NULL) receives the old index of each new index, for the caller's other
+ * per-particle arrays (zeta, eta, frozen).  PHB_ERR_INVALID_ARG for NULL
+ * arrays. */
+phb_status phb_reorder(const phb_plan* plan, double* pos, double* lambda, double* U,
+                       int32_t* perm_out, void* ws, size_t ws_bytes, int32_t* status_word,
+                       phb_stream_t stream);
+
 /* Copy the lists of the last phb_build_neighbors out in the caller's
  * numbering: off [n+1] (int64, device), idx [capacity] (int32, device) with
  * the neighbours of i at idx[off[i] .. off[i+1]) in increasing index order.

@@ -171,6 +171,19 @@ def build_neighbors(plan: Plan, pos: torch.Tensor, lam: torch.Tensor, check_capa
             raise PhbError(int(L.phb_check(w)), "phb_build_neighbors")
 
 
+def reorder(plan: Plan, pos, lam, U):
+    """Permute pos, lam and U in place into the storage order of the last build
+    (phb_reorder); returns the int32 [n] tensor of old indices, for the caller's
+    other per-particle arrays (x_new = x_old[perm])."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    perm = torch.empty(n, dtype=torch.int32, device=plan.device)
+    check(_lib.lib().phb_reorder(C.byref(plan.c), _ptr(pos), _ptr(lam), _ptr(U), _ptr(perm),
+                                 _ptr(plan.ws), plan.ws.numel(), _ptr(plan.status_word), _stream()),
+          "phb_reorder")
+    return perm
+
+
 def export_neighbors(plan: Plan):
     """(off int64 [n+1], idx int32 [total]) in caller numbering, ascending per list."""
     total = plan.neighbor_total()

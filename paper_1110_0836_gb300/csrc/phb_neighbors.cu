@@ -612,6 +612,14 @@ __global__ void __launch_bounds__(1024) k_tile_order(int n, int T, int ntiles, i
   }
 }
 
+// -------- storage order
+__global__ void k_identity(int n, int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  perm[s] = s;
+  inv[s] = s;
+}
+
 // -------- export in caller numbering
 __global__ void k_user_counts(int n, const int32_t* __restrict__ inv, const int64_t* __restrict__ off,
                               int32_t* __restrict__ ucnt) {
@@ -745,6 +753,35 @@ extern "C" phb_status phb_build_neighbors(const phb_plan* plan, const double* po
   if (!pos || !lambda) return PHB_ERR_INVALID_ARG;
   return launch_status(build_neighbors_impl(plan, pos, lambda, ws, status_word,
                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" phb_status phb_reorder(const phb_plan* plan, double* pos, double* lambda, double* U,
+                                  int32_t* perm_out, void* ws, size_t ws_bytes, int32_t* status_word,
+                                  phb_stream_t stream) {
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_END_COMMON] : 0);
+  if (s != PHB_OK) return s;
+  if (!pos || !lambda || !U) return PHB_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Grid g = make_grid(plan);
+  const int64_t N = plan->n;
+  int32_t* perm = region<int32_t>(plan, ws, R_PERM);
+  cudaError_t e;
+  // slot-order copies of all three arrays, then back over the caller's
+  if ((e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st))) return launch_status(e);
+  if (perm_out && (e = cudaMemcpyAsync(perm_out, perm, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, st)))
+    return launch_status(e);
+  if ((e = cudaMemcpyAsync(pos, region<double>(plan, ws, R_SPOS), 3 * N * sizeof(double),
+                           cudaMemcpyDeviceToDevice, st)))
+    return launch_status(e);
+  if ((e = cudaMemcpyAsync(lambda, region<double>(plan, ws, R_SLAM), N * sizeof(double),
+                           cudaMemcpyDeviceToDevice, st)))
+    return launch_status(e);
+  if ((e = cudaMemcpyAsync(U, region<double>(plan, ws, R_SU), 8 * N * sizeof(double),
+                           cudaMemcpyDeviceToDevice, st)))
+    return launch_status(e);
+  k_identity<<<blocks_for(N), kThreads, 0, st>>>(g.n, perm, region<int32_t>(plan, ws, R_INV));
+  note_launch();
+  return launch_status(cudaGetLastError());
 }
 
 extern "C" int64_t phb_neighbor_total(const phb_plan* plan, const void* ws, phb_stream_t stream) {
