@@ -551,30 +551,42 @@ __global__ void __launch_bounds__(T, 768 / T) k_compact(Grid g, const int2* __re
     for (int64_t e = a; e < b; ++e) owner[e - e0] = static_cast<uint8_t>(tid);
   }
   __syncthreads();
-#pragma unroll 4
-  for (int64_t e = e0 + tid; e < e1; e += T) {
-    int p;
-    if (mapped) {
-      p = owner[e - e0];
-    } else {
-      int lo = 0, hi = cnt - 1;  // the last p with toff[p] <= e
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (toff[mid] <= e) lo = mid; else hi = mid - 1;
+  // four entries per thread per round, their loads issued together (the
+  // list slot, then its cell) so that several global loads are in flight
+  auto owner_of = [&](int64_t e) {
+    if (mapped) return static_cast<int>(owner[e - e0]);
+    int lo = 0, hi = cnt - 1;  // the last p with toff[p] <= e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (toff[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  constexpr int kB = 4;
+  for (int64_t eb = e0 + tid; eb < e1; eb += kB * T) {
+    int t[kB], c[kB];
+    bool ok[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int64_t e = eb + static_cast<int64_t>(u) * T;
+      ok[u] = e < e1;
+      t[u] = 0;
+      if (ok[u]) {
+        const int p = owner_of(e);
+        t[u] = tlen[p] > g.ell ? idx[e] : ell[static_cast<int64_t>(s0 + p) * g.ell + (e - toff[p])];
       }
-      p = lo;
     }
-    const int k = static_cast<int>(e - toff[p]);
-    int t;
-    if (tlen[p] > g.ell) {
-      t = idx[e];
-    } else {
-      t = ell[static_cast<int64_t>(s0 + p) * g.ell + k];
-      idx[e] = t;
-    }
-    if (staged) {
-      const int j = marked_index(tarr, box_index(g, ts, cellc[t]));
-      lidx[e] = static_cast<uint16_t>(base[j] + (t - cstart[j]));
+#pragma unroll
+    for (int u = 0; u < kB; ++u) c[u] = (ok[u] && staged) ? cellc[t[u]] : 0;
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      if (!ok[u]) continue;
+      const int64_t e = eb + static_cast<int64_t>(u) * T;
+      idx[e] = t[u];
+      if (staged) {
+        const int j = marked_index(tarr, box_index(g, ts, c[u]));
+        lidx[e] = static_cast<uint16_t>(base[j] + (t[u] - cstart[j]));
+      }
     }
   }
 }
