@@ -2,7 +2,7 @@
 //
 // One CTA per tile of consecutive particles (cell order), one thread per
 // particle.  The tile's neighbourhood is staged in shared memory as 48-byte
-// records: position and the 8 fields relative to the tile's first particle,
+// records: position and the 8 fields relative to the tile's middle particle,
 // computed from FP32 hi/lo splits of the FP64 values (offsets with minimum
 // image), so differences between neighbours keep ~7 significant digits even
 // for a 1e-6 perturbation on an O(1) background.  Each thread accumulates the
@@ -251,8 +251,11 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   const int2 tp = listed ? make_int2(0, 1) : ta.tplan[tile];
   const bool fb = tp.y != 0;
   if (!fb) {
-    const float4 rh = rec[6 * s0], rl = rec[6 * s0 + 1];
-    const float4 fh = rec[6 * s0 + 2], fl = rec[6 * s0 + 3], gh = rec[6 * s0 + 4], gl = rec[6 * s0 + 5];
+    // records relative to the tile's middle particle: the staged FP32 offsets
+    // and field differences round to at most half the tile's extent
+    const int sr = s0 + (cnt_tile >> 1);
+    const float4 rh = rec[6 * sr], rl = rec[6 * sr + 1];
+    const float4 fh = rec[6 * sr + 2], fl = rec[6 * sr + 3], gh = rec[6 * sr + 4], gl = rec[6 * sr + 5];
     const int32_t* slots = ta.tslot + static_cast<int64_t>(tile) * a.g.stage_cap;
     // eight records per thread in flight: slots first, then all their loads
     constexpr int kB = 8;

@@ -217,7 +217,10 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   p->nkeys = nkeys;
   if (p->tile == 0) p->tile = 128;
   if (p->tile != 64 && p->tile != 128) return PHB_ERR_INVALID_ARG;
-  if (p->stage_cap == 0) p->stage_cap = p->tile == 128 ? 1500 : 768;
+  // default stage: the largest that keeps two 128-thread fit CTAs (254
+  // registers each) per SM: 2 x (29 KB parked right-hand sides + 48 B per
+  // record) within 227 KB; the 64-thread tiles run four CTAs per SM
+  if (p->stage_cap == 0) p->stage_cap = p->tile == 128 ? 1750 : 768;
   if (p->stage_cap < 64 || p->stage_cap > 2048) return PHB_ERR_INVALID_ARG;
   p->ntiles = static_cast<int32_t>((p->n + p->tile - 1) / p->tile);
   if (p->schedule != 0 && p->schedule != 1) return PHB_ERR_INVALID_ARG;
