@@ -41,7 +41,7 @@ FLOP_PER_NEIGHBOUR = 2 * (80 + 7 * 19)
 FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
 # DRAM bytes (read + write) per launch of the fused fit, from ncu captures of the
 # kernel as it is built now: (workload, kernel, tile) -> bytes.  Absent = null.
-FIT_TRAFFIC = {("random_modes_64^3", "k_fit_mixed", 128): 69.36e6 + 3.05e6}
+FIT_TRAFFIC = {("random_modes_64^3", "k_fit_mixed", 128): 68.63e6 + 3.02e6}
 
 
 def parse():
@@ -316,12 +316,16 @@ def run_profile(args):
     if args.profile == "fit":
         plan = phb.Plan.for_workload(w, device=dev, **shape)
         phb.build_neighbors(plan, pos, lam)
+        if args.particle_order == "storage":
+            phb.reorder(plan, pos, lam, U)
         out = torch.empty((8, w.n), dtype=torch.float64, device=dev)
         for _ in range(2):
             phb.mhd_rhs(plan, prm, pos, lam, U, out=out)
     else:
         plan = phb.Plan.for_workload(w, skin=skin, device=dev, **shape)
         phb.build_neighbors(plan, pos, lam)
+        if args.particle_order == "storage":
+            phb.reorder(plan, pos, lam, U)
         for _ in range(2):
             phb.pc_step(plan, prm, pos, lam, U, dt)
     torch.cuda.synchronize()
