@@ -30,7 +30,8 @@ class Box(C.Structure):
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("rf_factor", C.c_double), ("weight_kind", C.c_int32),
                 ("pad", C.c_int32), ("zeta", C.c_void_p), ("eta", C.c_void_p),
-                ("frozen", C.c_void_p)]
+                ("frozen", C.c_void_p), ("c_zeta_l", C.c_double), ("c_zeta_a", C.c_double),
+                ("c_eta", C.c_double)]
 
 
 _LIB = None
@@ -100,7 +101,8 @@ def box_of(w) -> Box:
 class _P:
     """Params plus the numpy arrays its pointers refer to (kept alive)."""
 
-    def __init__(self, gamma, rf_factor=2.3, weight_kind=0, zeta=None, eta=None, frozen=None):
+    def __init__(self, gamma, rf_factor=2.3, weight_kind=0, zeta=None, eta=None, frozen=None,
+                 laws=(0.0, 0.0, 0.0)):
         self.keep = []
         self.p = Params()
         self.p.gamma = float(gamma)
@@ -108,6 +110,7 @@ class _P:
         self.p.weight_kind = int(weight_kind)
         self.p.zeta = self._ptr(zeta)
         self.p.eta = self._ptr(eta)
+        self.p.c_zeta_l, self.p.c_zeta_a, self.p.c_eta = (float(x) for x in laws)
         self.p.frozen = None
         if frozen is not None:
             fz = np.ascontiguousarray(np.asarray(frozen) != 0, np.uint8)
@@ -164,8 +167,9 @@ def mls_derivs(box: Box, pos, lam, U, nbrs, query=None, gamma=5.0 / 3.0, rf_fact
 
 
 def mhd_rhs(box: Box, pos, lam, U, nbrs, query=None, gamma=5.0 / 3.0, rf_factor=2.3,
-            weight_kind=0, zeta=None, eta=None):
-    """dU/dt [8][nq] and status [nq] for the query particles."""
+            weight_kind=0, zeta=None, eta=None, laws=(0.0, 0.0, 0.0)):
+    """dU/dt [8][nq] and status [nq] for the query particles.  laws = (C_l, C_a,
+    C_eta) of the bulk-viscosity and div B diffusivity laws (0 = off)."""
     pos, lam, U = _c(pos), _c(lam), _c(U)
     n = lam.shape[0]
     q = _query(n, query)
@@ -173,14 +177,14 @@ def mhd_rhs(box: Box, pos, lam, U, nbrs, query=None, gamma=5.0 / 3.0, rf_factor=
     nq = q.shape[0]
     out = np.zeros((8, nq))
     st = np.zeros(nq, np.int32)
-    P = _P(gamma, rf_factor, weight_kind, zeta, eta)
+    P = _P(gamma, rf_factor, weight_kind, zeta, eta, laws=laws)
     lib().orc_mhd_rhs(C.byref(box), n, pos, lam, U, C.byref(P.p), nq, q, _c(off, np.int64),
                       _c(idx, np.int64) if len(idx) else np.zeros(1, np.int64), out, st)
     return out, st
 
 
 def rhs_jvp(box: Box, pos, lam, U, dpos, dU, nbrs, query=None, gamma=5.0 / 3.0, rf_factor=2.3,
-            weight_kind=0, zeta=None, eta=None):
+            weight_kind=0, zeta=None, eta=None, laws=(0.0, 0.0, 0.0)):
     """(dU/dt, its derivative along (dpos, dU)) for the query particles, sets frozen."""
     pos, lam, U = _c(pos), _c(lam), _c(U)
     n = lam.shape[0]
@@ -191,7 +195,7 @@ def rhs_jvp(box: Box, pos, lam, U, dpos, dU, nbrs, query=None, gamma=5.0 / 3.0, 
     dout = np.zeros((8, nq))
     dpos = None if dpos is None else _c(dpos)
     dU = None if dU is None else _c(dU)
-    P = _P(gamma, rf_factor, weight_kind, zeta, eta)
+    P = _P(gamma, rf_factor, weight_kind, zeta, eta, laws=laws)
     lib().orc_rhs_jvp(C.byref(box), n, pos, lam, U,
                       None if dpos is None else dpos.ctypes.data,
                       None if dU is None else dU.ctypes.data, C.byref(P.p), nq, q,
@@ -201,11 +205,11 @@ def rhs_jvp(box: Box, pos, lam, U, dpos, dU, nbrs, query=None, gamma=5.0 / 3.0, 
 
 
 def pc_step(box: Box, pos, lam, U, dt, gamma=5.0 / 3.0, rf_factor=2.3, weight_kind=0, zeta=None,
-            eta=None, frozen=None):
+            eta=None, frozen=None, laws=(0.0, 0.0, 0.0)):
     """One Heun step of all particles (O(n^2) brute force): returns new (pos, U).
     frozen: optional [n] mask of particles that keep x and U (fixed values)."""
     pos, lam, U = _c(pos).copy(), _c(lam), _c(U).copy()
-    P = _P(gamma, rf_factor, weight_kind, zeta, eta, frozen)
+    P = _P(gamma, rf_factor, weight_kind, zeta, eta, frozen, laws)
     nsing = lib().orc_pc_step(C.byref(box), lam.shape[0], pos, lam, U, float(dt), C.byref(P.p))
     return pos, U, nsing
 

@@ -32,7 +32,15 @@
 //   graded-lexicographic order x y z xx xy xz yy yz zz xxx xxy xxz xyy xyz xzz
 //   yyy yyz yzz zzz;
 //   P = (gamma - 1) sigma;  mu_0 = 1 units (V_A^2 = B^2 / rho, App. A);
-//   bulk viscosity zeta and div B diffusivity eta are per-particle inputs.
+//   bulk viscosity zeta and div B diffusivity eta are per-particle inputs,
+//   plus optional coefficient laws for the two bulk-viscosity fields and the
+//   div B diffusivity (Sec. 2 states only what they do; Paper I's forms are
+//   not available): with the fast-speed bound c = sqrt((gamma P + |B|^2)/rho)
+//     zeta = zeta_in + C_l lambda c + C_a lambda^2 max(0, -div V)
+//     eta  = eta_in  + C_eta lambda c
+//   (C_l: damping at the resolution scale at the signal speed; C_a: damping
+//   that grows with compression, as at shocks; C_eta: div B diffusion at the
+//   resolution scale).
 //
 // Build: g++ -O2 -std=c++17 -fopenmp -ffp-contract=off -fPIC -shared.
 #include <cmath>
@@ -60,6 +68,9 @@ struct Params {
   const double* zeta;   // [n] or null (0)
   const double* eta;    // [n] or null (0)
   const uint8_t* frozen;  // [n] or null: nonzero = no time evolution (pc_step only)
+  double c_zeta_l;        // coefficient laws (0 = off), see the header
+  double c_zeta_a;
+  double c_eta;
 };
 
 // ---------------------------------------------------------------- dual numbers
@@ -223,8 +234,8 @@ inline int hidx(int a, int b) {
 //   DB/Dt     = (B . grad) V - B div V + eta grad(div B)
 //   Dsigma/Dt = -gamma sigma div V + rho zeta (div V)^2
 template <class T>
-void mhd_rhs_point(const T u[NF], const T g[NF][3], const T h[NF][6], double gamma, double zeta,
-                   double eta, T out[NF]) {
+void mhd_rhs_point(const T u[NF], const T g[NF][3], const T h[NF][6], double gamma, T zeta,
+                   T eta, T out[NF]) {
   const T rho = u[0], sig = u[7];
   const T B[3] = {u[4], u[5], u[6]};
   T divV = g[1][0] + g[2][1] + g[3][2];
@@ -238,11 +249,11 @@ void mhd_rhs_point(const T u[NF], const T g[NF][3], const T h[NF][6], double gam
   T F[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
   out[0] = -rho * divV;
   for (int a = 0; a < 3; ++a) {
-    out[1 + a] = (T(-(gamma - 1.0)) * g[7][a] + F[a]) / rho + T(zeta) * gdivV[a];
+    out[1 + a] = (T(-(gamma - 1.0)) * g[7][a] + F[a]) / rho + zeta * gdivV[a];
     T adv = B[0] * g[1 + a][0] + B[1] * g[1 + a][1] + B[2] * g[1 + a][2];
-    out[4 + a] = adv - B[a] * divV + T(eta) * gdivB[a];
+    out[4 + a] = adv - B[a] * divV + eta * gdivB[a];
   }
-  out[7] = T(-gamma) * sig * divV + rho * T(zeta) * divV * divV;
+  out[7] = T(-gamma) * sig * divV + rho * zeta * divV * divV;
 }
 
 template <class T>
@@ -251,8 +262,18 @@ int rhs_particle(const Box& box, int64_t n, const T* pos, const double* lam, con
   T g[NF][3], h[NF][6], u[NF];
   int st = fit_particle<T>(box, n, pos, lam, U, prm, i, nb, nn, g, h);
   for (int f = 0; f < NF; ++f) u[f] = U[f * n + i];
-  double zeta = prm.zeta ? prm.zeta[i] : 0.0;
-  double eta = prm.eta ? prm.eta[i] : 0.0;
+  T zeta = T(prm.zeta ? prm.zeta[i] : 0.0);
+  T eta = T(prm.eta ? prm.eta[i] : 0.0);
+  if (prm.c_zeta_l != 0.0 || prm.c_zeta_a != 0.0 || prm.c_eta != 0.0) {
+    // coefficient laws (see the header): fast-speed bound and compression
+    const T P = T(prm.gamma - 1.0) * u[7];
+    const T c = sqrt((T(prm.gamma) * P + u[4] * u[4] + u[5] * u[5] + u[6] * u[6]) / u[0]);
+    const T divV = g[1][0] + g[2][1] + g[3][2];
+    const T l = T(lam[i]);
+    zeta = zeta + T(prm.c_zeta_l) * l * c;
+    if (val(divV) < 0.0) zeta = zeta - T(prm.c_zeta_a) * l * l * divV;
+    eta = eta + T(prm.c_eta) * l * c;
+  }
   mhd_rhs_point<T>(u, g, h, prm.gamma, zeta, eta, out);
   return st;
 }

@@ -27,9 +27,9 @@ MUTATIONS = {
     "lorentz_sign": ("J[1] * B[2] - J[2] * B[1]", "J[2] * B[1] - J[1] * B[2]"),
     "curl_sign": ("g[6][1] - g[5][2]", "g[6][1] + g[5][2]"),
     "no_pressure": ("T(-(gamma - 1.0)) * g[7][a]", "T(0.0) * g[7][a]"),
-    "zeta_sign": ("/ rho + T(zeta) * gdivV[a]", "/ rho - T(zeta) * gdivV[a]"),
-    "no_heating": ("+ rho * T(zeta) * divV * divV", "+ T(0.0) * divV"),
-    "eta_dropped": ("+ T(eta) * gdivB[a]", "+ T(0.0) * gdivB[a]"),
+    "zeta_sign": ("/ rho + zeta * gdivV[a]", "/ rho - zeta * gdivV[a]"),
+    "no_heating": ("+ rho * zeta * divV * divV", "+ T(0.0) * divV"),
+    "eta_dropped": ("+ eta * gdivB[a]", "+ T(0.0) * gdivB[a]"),
     "induction_compression": ("- B[a] * divV", "+ B[a] * divV"),
     "not_strict": ("return d2 < r * r;", "return d2 <= r * r;"),
     "no_min_image": ("if (periodic) d = d - len", "if (periodic < 0) d = d - len"),
@@ -37,6 +37,11 @@ MUTATIONS = {
                         "U[f * n + i] += dt * F0[f * n + i];"),
     "frozen_ignored": ("auto moving = [&](int64_t i) { return !(prm->frozen && prm->frozen[i]); };",
                        "auto moving = [&](int64_t i) { return i >= 0; };"),
+    "law_abs_divv": ("if (val(divV) < 0.0) zeta = zeta - T(prm.c_zeta_a) * l * l * divV;",
+                     "zeta = zeta + T(prm.c_zeta_a) * l * l * (val(divV) < 0.0 ? -divV : divV);"),
+    "law_speed_without_field": ("const T c = sqrt((T(prm.gamma) * P + u[4] * u[4] + u[5] * u[5] + u[6] * u[6]) / u[0]);",
+                                "const T c = sqrt((T(prm.gamma) * P) / u[0]);"),
+    "law_lambda_once": ("zeta = zeta - T(prm.c_zeta_a) * l * l * divV;", "zeta = zeta - T(prm.c_zeta_a) * l * divV;"),
     "basis_xyz_missing": ("p[13] = x * y * z;", "p[13] = x * y;"),
     "lambda_scale": ("grad[f][0] = C[0 * NF + f] * il;", "grad[f][0] = C[0 * NF + f] * il * il;"),
     "level_off_by_one": ("    int32_t L = 0;\n    while (L < max_level", "    int32_t L = 1;\n    while (L < max_level"),
@@ -62,6 +67,9 @@ PINS = [
     lambda: trhs.test_damped_sound_wave_bulk_viscosity(oracle),
     lambda: trhs.test_divb_diffusion(oracle),
     lambda: trhs.test_viscous_heating_linear_flow(oracle),
+    lambda: trhs.test_viscosity_laws_linear_flow(oracle, -1.0),
+    lambda: trhs.test_viscosity_laws_linear_flow(oracle, 1.0),
+    lambda: trhs.test_divb_diffusion_law(oracle),
     lambda: tstep.test_heun_is_second_order_in_time(oracle),
     lambda: tstep.test_frozen_particles_in_uniform_flow(oracle),
     lambda: tlev.test_golden_line(),
