@@ -97,6 +97,17 @@ typedef struct {
                             fixed-value boundaries of the Sec. 3 tests); its
                             right-hand side is still evaluated and it stays a
                             neighbour of the others.  Read by no other call. */
+  /* Coefficient laws added to zeta and eta (0 = off).  Sec. 2 says what the
+   * two bulk-viscosity fields and the div B diffusion do, not their form; the
+   * forms read here, with the fast-speed bound c = sqrt((gamma P + |B|^2)/rho):
+   *   zeta_i += c_zeta_l lambda_i c_i + c_zeta_a lambda_i^2 max(0, -div V_i)
+   *   eta_i  += c_eta lambda_i c_i
+   * (grid-scale damping at the signal speed; damping that grows with
+   * compression, as at shocks; div B diffusion at the resolution scale).
+   * Every right-hand-side, adjoint and step call applies them. */
+  double c_zeta_l;
+  double c_zeta_a;
+  double c_eta;
 } phb_params;
 
 /* A plan fixes the particle count, box, radius law and the cell grid.  The

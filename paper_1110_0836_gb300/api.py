@@ -45,6 +45,11 @@ class Params:
     zeta: torch.Tensor | None = None  # bulk viscosity [n] (caller order) or None
     eta: torch.Tensor | None = None   # div B diffusivity [n] or None
     frozen: torch.Tensor | None = None  # pc_step: bool/uint8 [n], nonzero = keep x and U
+    # coefficient laws added to zeta / eta (0 = off): zeta += c_zeta_l lambda c +
+    # c_zeta_a lambda^2 max(0, -div V), eta += c_eta lambda c, c the fast-speed bound
+    c_zeta_l: float = 0.0
+    c_zeta_a: float = 0.0
+    c_eta: float = 0.0
 
     def c(self) -> _lib.Params:
         p = _lib.Params()
@@ -60,6 +65,7 @@ class Params:
                                         or not self.frozen.is_contiguous()):
             raise ValueError("frozen must be a contiguous bool or uint8 tensor")
         p.frozen = None if self.frozen is None else self.frozen.data_ptr()
+        p.c_zeta_l, p.c_zeta_a, p.c_eta = float(self.c_zeta_l), float(self.c_zeta_a), float(self.c_eta)
         return p
 
 

@@ -66,6 +66,7 @@ struct AdjArgs {
   int32_t weight_kind;
   const double* zeta;    // caller order or null
   const double* eta;
+  double c_zeta_l, c_zeta_a, c_eta;  // coefficient laws (phb_params), 0 = off
   double* scr;           // [266][n]: c_f (7 x 19) then bbar_f (7 x 19)
   double* edge;          // [capacity][10]
   double* self;          // [11][n] slot order
@@ -93,15 +94,27 @@ __device__ __forceinline__ Geo geometry(const AdjArgs& a, int t, double xs, doub
 }
 
 // Adjoint of the right-hand side at one particle.  In: point values u, the
-// derivatives D, coefficients, output adjoint o.  Out: ubar (point values)
-// and the adjoints of each fitted field's gradient gb[f][3] and packed
-// Hessian hb[f][6] (f = 0..6 for U indices 1..7).
+// derivatives D, the input coefficients zeta / eta and the coefficient laws
+// (lam, cl, ca, ce as in mhd_laws), output adjoint o.  Out: ubar (point
+// values) and the adjoints of each fitted field's gradient gb[f][3] and
+// packed Hessian hb[f][6] (f = 0..6 for U indices 1..7).
 __device__ void rhs_adjoint_point(const double (&u)[8], const MhdDerivs<double>& D, double gamma,
-                                  double zeta, double eta, const double (&o)[8], double (&ubar)[8],
+                                  double zeta, double eta, double lam, double cl, double ca,
+                                  double ce, const double (&o)[8], double (&ubar)[8],
                                   double (&gb)[kNFit][3], double (&hb)[kNFit][6]) {
   const double rho = u[0], sig = u[7];
   const double B[3] = {u[4], u[5], u[6]};
   const double divV = D.gV[0][0] + D.gV[1][1] + D.gV[2][2];
+  // the laws' totals (forward as mhd_laws): c = sqrt(q), q = (gamma P + |B|^2) / rho
+  const bool laws = cl != 0.0 || ca != 0.0 || ce != 0.0;
+  double q = 0.0, c = 0.0;
+  if (laws) {
+    q = (gamma * ((gamma - 1.0) * sig) + B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho;
+    c = sqrt(q);
+    zeta += cl * lam * c;
+    if (divV < 0.0) zeta -= ca * lam * lam * divV;
+    eta += ce * lam * c;
+  }
   const double J[3] = {D.gB[2][1] - D.gB[1][2], D.gB[0][2] - D.gB[2][0], D.gB[1][0] - D.gB[0][1]};
   const double F[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2], J[0] * B[1] - J[1] * B[0]};
   for (int k = 0; k < 8; ++k) ubar[k] = 0.0;
@@ -138,6 +151,23 @@ __device__ void rhs_adjoint_point(const double (&u)[8], const MhdDerivs<double>&
   ubar[7] += -o[7] * gamma * divV;
   ubar[0] += o[7] * zeta * divV * divV;
   divVb += o[7] * (-gamma * sig + 2.0 * rho * zeta * divV);
+  if (laws) {
+    // zeta_bar and eta_bar, then through zeta = .. + cl lam c + ca lam^2
+    // max(0, -div V) and eta = .. + ce lam c
+    double zb = o[7] * rho * divV * divV, eb = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      zb += o[1 + a] * D.gdivV[a];
+      eb += o[4 + a] * D.gdivB[a];
+    }
+    if (divV < 0.0) divVb += -zb * ca * lam * lam;
+    const double cb = (zb * cl + eb * ce) * lam;
+    if (c > 0.0) {
+      const double qb = cb / (2.0 * c);
+      ubar[7] += qb * gamma * (gamma - 1.0) / rho;
+      for (int b = 0; b < 3; ++b) ubar[4 + b] += qb * 2.0 * B[b] / rho;
+      ubar[0] += -qb * q / rho;
+    }
+  }
   for (int a = 0; a < 3; ++a) gb[a][a] += divVb;
   // F = J x B:  Bbar += Fbar x J,  Jbar = B x Fbar
   ubar[4] += Fb[1] * J[2] - Fb[2] * J[1];
@@ -280,7 +310,8 @@ __global__ void __launch_bounds__(kT, 1) k_adjoint(const AdjArgs a) {
       mhd_collect(D, fi + 1, g, h);
     }
     double gb[kNFit][3], hb[kNFit][6];
-    rhs_adjoint_point(u, D, a.gamma, zeta, eta, o, selfu, gb, hb);
+    rhs_adjoint_point(u, D, a.gamma, zeta, eta, lam, a.c_zeta_l, a.c_zeta_a, a.c_eta, o, selfu,
+                      gb, hb);
     for (int fi = 0; fi < kNFit; ++fi) {
       double cb[kNB];
       for (int k = 0; k < kQuad0; ++k) cb[k] = 0.0;
@@ -453,6 +484,9 @@ phb_status adjoint_impl(int mode, const phb_plan* plan, const phb_params* prm, c
   a.weight_kind = prm->weight_kind;
   a.zeta = prm->zeta;
   a.eta = prm->eta;
+  a.c_zeta_l = prm->c_zeta_l;
+  a.c_zeta_a = prm->c_zeta_a;
+  a.c_eta = prm->c_eta;
   a.scr = region<double>(plan, ws, R_ADJ_SCR);
   a.edge = region<double>(plan, ws, R_ADJ_EDGE);
   a.self = region<double>(plan, ws, R_ADJ_SELF);

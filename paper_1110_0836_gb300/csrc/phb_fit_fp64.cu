@@ -221,8 +221,10 @@ __global__ void __launch_bounds__(kT, 1) k_fit_fp64(const FitArgs a, int routed,
       }
       if (MODE == FitMode::kRHS) {
         const int src = a.perm_in ? a.perm_in[s] : s;
-        const double zeta = a.zeta ? a.zeta[src] : 0.0;
-        const double eta = a.eta ? a.eta[src] : 0.0;
+        double zeta = a.zeta ? a.zeta[src] : 0.0;
+        double eta = a.eta ? a.eta[src] : 0.0;
+        if (a.c_zeta_l != 0.0 || a.c_zeta_a != 0.0 || a.c_eta != 0.0)
+          mhd_laws(u, D, a.gamma, lam, a.c_zeta_l, a.c_zeta_a, a.c_eta, zeta, eta);
         double out[8];
         mhd_rhs(u, D, a.gamma, zeta, eta, out);
         bool finite = true;

@@ -396,8 +396,12 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
         const float u[8] = {o2.x + o3.x, o2.z + o3.z, o2.w + o3.w, o4.x + o5.x,
                             o4.y + o5.y, o4.z + o5.z, o4.w + o5.w, o2.y + o3.y};
         const int src = a.perm_in ? a.perm_in[s] : s;
-        const float zeta = a.zeta ? static_cast<float>(a.zeta[src]) : 0.f;
-        const float eta = a.eta ? static_cast<float>(a.eta[src]) : 0.f;
+        float zeta = a.zeta ? static_cast<float>(a.zeta[src]) : 0.f;
+        float eta = a.eta ? static_cast<float>(a.eta[src]) : 0.f;
+        if (a.c_zeta_l != 0.0 || a.c_zeta_a != 0.0 || a.c_eta != 0.0)
+          mhd_laws(u, D, static_cast<float>(a.gamma), static_cast<float>(a.slam[s]),
+                   static_cast<float>(a.c_zeta_l), static_cast<float>(a.c_zeta_a),
+                   static_cast<float>(a.c_eta), zeta, eta);
         float out[8];
         mhd_rhs(u, D, static_cast<float>(a.gamma), zeta, eta, out);
         bool finite = true;

@@ -273,6 +273,7 @@ struct FitArgs {
   float cond_threshold;
   const double* zeta;          // caller order (indexed through perm_in) or null
   const double* eta;
+  double c_zeta_l, c_zeta_a, c_eta;  // coefficient laws (phb_params), 0 = off
   double* dudt;                // [8][n]
   double* grad;                // [8][3][n]
   double* hess;                // [8][6][n] or null

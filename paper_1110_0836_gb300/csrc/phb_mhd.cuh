@@ -56,6 +56,20 @@ __device__ __forceinline__ void mhd_zero(MhdDerivs<T>& D) {
   }
 }
 
+// Coefficient laws (readings of Sec. 2; see phb_params): with the fast-speed
+// bound c = sqrt((gamma P + |B|^2) / rho), P = (gamma - 1) sigma,
+//   zeta += cl lambda c + ca lambda^2 max(0, -div V),   eta += ce lambda c.
+template <typename T>
+__device__ __forceinline__ void mhd_laws(const T (&u)[8], const MhdDerivs<T>& D, T gamma, T lam,
+                                         T cl, T ca, T ce, T& zeta, T& eta) {
+  const T P = (gamma - T(1)) * u[7];
+  const T c = sqrt((gamma * P + u[4] * u[4] + u[5] * u[5] + u[6] * u[6]) / u[0]);
+  const T divV = D.gV[0][0] + D.gV[1][1] + D.gV[2][2];
+  zeta += cl * lam * c;
+  if (divV < T(0)) zeta -= ca * lam * lam * divV;
+  eta += ce * lam * c;
+}
+
 // u: point values (rho, Vx, Vy, Vz, Bx, By, Bz, sigma); out: time derivatives.
 template <typename T>
 __device__ __forceinline__ void mhd_rhs(const T (&u)[8], const MhdDerivs<T>& D, T gamma, T zeta,

@@ -93,6 +93,9 @@ cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMo
   a.cond_threshold = static_cast<float>(prm->cond_threshold > 0 ? prm->cond_threshold : 3e4);
   a.zeta = prm->zeta;
   a.eta = prm->eta;
+  a.c_zeta_l = prm->c_zeta_l;
+  a.c_zeta_a = prm->c_zeta_a;
+  a.c_eta = prm->c_eta;
   a.dudt = dudt;
   a.grad = grad;
   a.hess = hess;

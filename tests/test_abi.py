@@ -119,5 +119,5 @@ def test_struct_sizes_match_the_binding(L):
     out = (C.c_int64 * 3)()
     assert L.phb_struct_sizes(out, 3) == 0
     assert tuple(out) == (C.sizeof(_lib.Box), C.sizeof(_lib.Params), C.sizeof(_lib.Plan))
-    assert C.sizeof(_lib.Params) == 48    # gamma, kind, precision, threshold, zeta, eta, frozen
+    assert C.sizeof(_lib.Params) == 72    # gamma, kind, precision, threshold, zeta, eta, frozen, laws
     assert L.phb_struct_sizes(None, 3) == 1 and L.phb_struct_sizes(out, 4) == 1

@@ -17,19 +17,24 @@ def setup(phb, w, **prm):
     return plan, pos, lam, U, phb.Params(gamma=w.gamma, precision="fp64", **prm)
 
 
-@pytest.mark.parametrize("with_terms", [False, True])
+@pytest.mark.parametrize("with_terms", [False, True, "laws"])
 def test_dot_product_against_oracle_jvp(with_terms):
     """<gbar, J v> from the oracle's dual numbers equals <J^T gbar, v> from the
-    GPU adjoint (all particles, neighbour sets fixed)."""
+    GPU adjoint (all particles, neighbour sets fixed); with input zeta / eta,
+    and with the coefficient laws on top of them."""
     phb = need_gpu()
     w = workloads.random_modes(12, seed=41, amp=0.05)
     rng = np.random.default_rng(5)
     kw = {}
     zeta = eta = None
+    laws = (0.0, 0.0, 0.0)
     if with_terms:
         zeta = rng.uniform(0, 0.05, w.n)
         eta = rng.uniform(0, 0.02, w.n)
         kw = dict(zeta=torch.tensor(zeta, device="cuda"), eta=torch.tensor(eta, device="cuda"))
+    if with_terms == "laws":
+        laws = (0.8, 2.0, 1.5)
+        kw.update(c_zeta_l=laws[0], c_zeta_a=laws[1], c_eta=laws[2])
     plan, pos, lam, U, prm = setup(phb, w, **kw)
     gbar = rng.standard_normal((8, w.n))
     Ub, xb = phb.rhs_adjoint(plan, prm, pos, lam, U, torch.tensor(gbar, device="cuda"))
@@ -38,7 +43,8 @@ def test_dot_product_against_oracle_jvp(with_terms):
     vU = rng.standard_normal((8, w.n))
     box = oracle.box_of(w)
     nb = oracle.neighbors(box, w.pos, w.lam)
-    _, jv = oracle.rhs_jvp(box, w.pos, w.lam, w.U, vpos, vU, nb, gamma=w.gamma, zeta=zeta, eta=eta)
+    _, jv = oracle.rhs_jvp(box, w.pos, w.lam, w.U, vpos, vU, nb, gamma=w.gamma, zeta=zeta, eta=eta,
+                           laws=laws)
     lhs = float((gbar * jv).sum())
     rhs = float((Ub * vU).sum() + (xb * vpos).sum())
     assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), 1.0), (lhs, rhs)

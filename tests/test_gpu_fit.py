@@ -116,6 +116,35 @@ def test_viscosity_and_divb_terms_fp64():
     assert rhs_err(out, exp, sc).max() < 1e-5
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_mixed", 1e-5)])
+def test_coefficient_laws(prec, tol):
+    """zeta += C_l lambda c + C_a lambda^2 max(0, -div V), eta += C_eta lambda c on
+    top of input coefficients, against the oracle; term scales with each
+    particle's resulting coefficients."""
+    phb = need_gpu()
+    w = workloads.random_modes(14, seed=7, amp=0.05)
+    rng = np.random.default_rng(3)
+    zeta = rng.uniform(0.0, 0.02, w.n)
+    eta = rng.uniform(0.0, 0.01, w.n)
+    laws = (0.8, 2.0, 1.5)
+    prm = phb.Params(gamma=w.gamma, precision=prec, zeta=torch.tensor(zeta, device="cuda"),
+                     eta=torch.tensor(eta, device="cuda"), c_zeta_l=laws[0], c_zeta_a=laws[1],
+                     c_eta=laws[2])
+    out, st, _ = gpu_run(phb, w, prm)
+    exp, _ = oracle_run(w, zeta=zeta, eta=eta, laws=laws)
+    base, _ = oracle_run(w, zeta=zeta, eta=eta)
+    (g, h), _ = oracle_run(w, "derivs")
+    divV = g[1, 0] + g[2, 1] + g[3, 2]
+    P = (w.gamma - 1.0) * w.U[7]
+    c = np.sqrt((w.gamma * P + (w.U[4:7] ** 2).sum(0)) / w.U[0])
+    zt = zeta + laws[0] * w.lam * c + laws[1] * w.lam ** 2 * np.maximum(0.0, -divV)
+    et = eta + laws[2] * w.lam * c
+    assert (divV < 0).any() and (divV > 0).any()
+    sc = term_scales(w, zeta=zt, eta=et)
+    assert rhs_err(out, exp, sc).max() < tol
+    assert rhs_err(base, exp, sc).max() > 100 * tol     # the laws change the result
+
+
 def test_unweighted_fit():
     phb = need_gpu()
     w = workloads.random_modes(14, seed=6)
