@@ -60,6 +60,9 @@ def load(path: str):
                               C.POINTER(Params)]
     L.orc_timestep_levels.argtypes = [C.c_int64, _f64p, _f64p, C.c_double, C.c_double, C.c_double,
                                       C.c_int32, _i64p, _i64p, _i32p]
+    L.orc_adapt_scan.argtypes = [C.POINTER(Box), C.c_int64, _f64p, _f64p, C.c_double, C.c_double,
+                                 C.c_double, _i64p, _i64p, _i32p, _i32p, _f64p, _i32p]
+    L.orc_adapt_scan.restype = C.c_int64
     for f in ("orc_neighbors", "orc_mls_derivs", "orc_mhd_rhs", "orc_rhs_jvp", "orc_pc_step",
               "orc_timestep_levels"):
         getattr(L, f).restype = C.c_int
@@ -214,6 +217,23 @@ def pc_step(box: Box, pos, lam, U, dt, gamma=5.0 / 3.0, rf_factor=2.3, weight_ki
     return pos, U, nsing
 
 
+def adapt_scan(box: Box, pos, lam, nbrs, rf_factor=2.3, void_factor=1.0, clump_factor=0.25):
+    """Void and clump scan (see orc_adapt_scan); nbrs = CSR lists of all
+    particles at r_f.  Returns (void_count [n], best [n], cand [3][n], clump [n])."""
+    pos, lam = _c(pos), _c(lam)
+    n = lam.shape[0]
+    off, idx = nbrs
+    vc = np.zeros(n, np.int32)
+    best = np.zeros(n, np.int32)
+    cand = np.zeros((3, n))
+    clump = np.zeros(n, np.int32)
+    lib().orc_adapt_scan(C.byref(box), n, pos, lam, float(rf_factor), float(void_factor),
+                         float(clump_factor), _c(off, np.int64),
+                         _c(idx, np.int64) if len(idx) else np.zeros(1, np.int64), vc, best, cand,
+                         clump)
+    return vc, best, cand, clump
+
+
 def timestep_levels(lam, U, nbrs, gamma=5.0 / 3.0, cfl=0.1, dt_max=1.0, max_level=20):
     """Individual power-of-two time-step levels with the spatial limiter
     (see orc_timestep_levels); nbrs = CSR lists of all particles."""
@@ -244,7 +264,7 @@ def available() -> bool:
         return False
 
 
-__all__ = ["Box", "Params", "lib", "load", "using", "make_box", "box_of", "neighbors", "mls_derivs", "mhd_rhs",
+__all__ = ["Box", "Params", "lib", "load", "using", "make_box", "box_of", "neighbors", "mls_derivs", "mhd_rhs", "adapt_scan",
            "rhs_jvp", "pc_step", "timestep_levels", "workload_rhs", "available"]
 
 if os.environ.get("PHB_ORACLE_EAGER"):

@@ -24,7 +24,10 @@
 //   * individual power-of-two time-step levels with the spatial limiter
 //     (Sec. 2: steps independent of the bulk velocity, spatial variation
 //     limited; Sec. 2.1: rounded down to powers of two, information flows
-//     from a particle to its neighbours).
+//     from a particle to its neighbours);
+//   * the particle adaptivity scan: voids found on a 9^3 grid of test points
+//     around each particle and clumps of too-close particles (Sec. 2,
+//     Sec. 2.1), with thresholds that are readings.
 //
 // Readings where the paper defers to Paper I:
 //   weight w = (1 - s^2)^2 with s = |d| / r_f,i (or w = 1);
@@ -459,6 +462,91 @@ int orc_timestep_levels(int64_t n, const double* lam, const double* U, double ga
       if (L0[i] - 1 > levels[j]) levels[j] = L0[i] - 1;
     }
   return bad;
+}
+
+// Particle adaptivity scan (Sec. 2: particles are added in voids and deleted
+// in clumps so that every sphere of radius r_f stays well sampled; Sec. 2.1:
+// the void search measures distances from the points of a 9^3 grid to the
+// neighbour particles and drops every point found close to one; the
+// thresholds are Paper I's and are readings here).  For every particle i
+// with lists N(i) of the strict r_f sets (CSR over all particles):
+//   grid: o_k = h (kx, ky, kz), kx, ky, kz in -4..4, h = (rf_factor lambda_i) / 4,
+//     grid index k = ((kx + 4) * 9 + (ky + 4)) * 9 + (kz + 4);
+//   test points: those with |o_k|^2 < (r_f - d_v)^2, d_v = void_factor
+//     lambda_i, so that every particle within d_v of a test point is i or in
+//     N(i) (triangle inequality);
+//   a test point is covered when some j in {i} + N(i) has
+//     |(x_j - x_i) - o_k|^2 < d_v^2  (minimum image, FP64, this order);
+//   void_count[i] = number of uncovered test points; best[i] = the uncovered
+//     point whose smallest squared distance to {i} + N(i) is largest (lowest
+//     k on ties), -1 when none; cand[3][n] = x_i + o_best (unwrapped);
+//   clump[i] = 1 when some j in N(i) with j < i has |x_j - x_i|^2 <
+//     (clump_factor lambda_i)^2: of two particles closer than that the one
+//     with the larger index is marked for deletion.
+// Returns the number of particles with a void.
+int64_t orc_adapt_scan(const Box* box, int64_t n, const double* pos, const double* lam,
+                       double rf_factor, double void_factor, double clump_factor,
+                       const int64_t* off, const int64_t* idx, int32_t* void_count, int32_t* best,
+                       double* cand, int32_t* clump) {
+  int64_t with_void = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : with_void)
+  for (int64_t i = 0; i < n; ++i) {
+    const double r = rf_factor * lam[i];
+    const double h = r * 0.25;
+    const double dv = void_factor * lam[i];
+    const double dv2 = dv * dv;
+    const double rin = r - dv;
+    const double dc = clump_factor * lam[i];
+    // offsets of the particle itself and its neighbours
+    std::vector<double> d;
+    d.reserve(3 * (off[i + 1] - off[i] + 1));
+    d.push_back(0.0); d.push_back(0.0); d.push_back(0.0);
+    int32_t cl = 0;
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+      const int64_t j = idx[e];
+      double o[3];
+      for (int a = 0; a < 3; ++a)
+        o[a] = min_image(pos[a * n + j] - pos[a * n + i], box->len[a], box->periodic[a]);
+      for (int a = 0; a < 3; ++a) d.push_back(o[a]);
+      const double dd = (o[0] * o[0] + o[1] * o[1]) + o[2] * o[2];
+      if (j < i && dd < dc * dc) cl = 1;
+    }
+    const int64_t m = static_cast<int64_t>(d.size() / 3);
+    int32_t cnt = 0, bk = -1;
+    double bclear = -1.0;
+    for (int kx = -4; kx <= 4; ++kx)
+      for (int ky = -4; ky <= 4; ++ky)
+        for (int kz = -4; kz <= 4; ++kz) {
+          const double ox = kx * h, oy = ky * h, oz = kz * h;
+          if (!((ox * ox + oy * oy) + oz * oz < rin * rin)) continue;
+          double mind = 1e300;
+          for (int64_t t = 0; t < m; ++t) {
+            const double ex = d[3 * t] - ox, ey = d[3 * t + 1] - oy, ez = d[3 * t + 2] - oz;
+            const double e2 = (ex * ex + ey * ey) + ez * ez;
+            if (e2 < mind) mind = e2;
+          }
+          if (mind < dv2) continue;
+          ++cnt;
+          const int32_t k = ((kx + 4) * 9 + (ky + 4)) * 9 + (kz + 4);
+          if (mind > bclear) {
+            bclear = mind;
+            bk = k;
+          }
+        }
+    void_count[i] = cnt;
+    best[i] = bk;
+    clump[i] = cl;
+    if (bk >= 0) {
+      const int kx = bk / 81 - 4, ky = (bk / 9) % 9 - 4, kz = bk % 9 - 4;
+      cand[i] = pos[i] + kx * h;
+      cand[n + i] = pos[n + i] + ky * h;
+      cand[2 * n + i] = pos[2 * n + i] + kz * h;
+      ++with_void;
+    } else {
+      cand[i] = cand[n + i] = cand[2 * n + i] = 0.0;
+    }
+  }
+  return with_void;
 }
 
 }  // extern "C"

@@ -1,0 +1,80 @@
+"""Pins of the oracle's particle-adaptivity scan (Paper II Sec. 2: particles
+are added in voids and deleted in clumps; Sec. 2.1: void search on a 9^3 grid
+of test points).  Thresholds are readings: test points within r_f - d_v of
+the particle, covered by a particle closer than d_v = lambda, clumps closer
+than lambda / 4 (the larger index is marked)."""
+import numpy as np
+
+import workloads
+
+
+def _scan(orc, pos, lam, box, **kw):
+    nb = orc.neighbors(box, pos, lam)
+    return orc.adapt_scan(box, pos, lam, nb, **kw)
+
+
+def test_isolated_particle_counts_the_shell(orc):
+    """One particle alone: the uncovered test points are the grid points h k
+    (h = r_f / 4 = 0.575 lambda) with lambda <= |h k| < 1.3 lambda, i.e.
+    |k|^2 in {4, 5}: 6 + 24 = 30 points (|k|^2 = 3 lies at 0.996 lambda and is
+    covered by the particle itself).  The farthest are the |k|^2 = 5 points;
+    the first of them in grid order is k = (-2, -1, 0)."""
+    pos = np.array([[0.5], [0.5], [0.5]])
+    lam = np.array([0.01])
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    vc, best, cand, clump = _scan(orc, pos, lam, box)
+    assert vc[0] == 30
+    assert best[0] == ((-2 + 4) * 9 + (-1 + 4)) * 9 + (0 + 4)
+    h = 2.3 * 0.01 / 4
+    np.testing.assert_array_equal(cand[:, 0], [0.5 - 2 * h, 0.5 - h, 0.5])
+    assert clump[0] == 0
+
+
+def test_lattice_has_no_voids_or_clumps(orc):
+    """Cubic lattice of spacing a = lambda: every point lies within
+    sqrt(3)/2 a < lambda of a site, and all those sites are neighbours."""
+    pos, h = workloads.lattice_positions(12, 1, jitter=0.0)
+    lam = np.full(pos.shape[1], h)
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    vc, best, cand, clump = _scan(orc, pos, lam, box)
+    assert not vc.any() and (best == -1).all() and not clump.any()
+
+
+def test_hole_in_a_lattice(orc):
+    """A 2x2x2 block of sites removed from the lattice leaves a void whose
+    centre is 1.66 a from the nearest site: only particles next to the hole
+    see it, and every void candidate lies inside the hole."""
+    a = 1.0 / 12
+    g = (np.arange(12) + 0.5) * a
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()])
+    c = np.array([6.0, 6.0, 6.0]) * a            # centre of the removed block
+    keep = ~np.all(np.abs(pos - c[:, None]) < a, axis=0)
+    pos = np.ascontiguousarray(pos[:, keep])
+    lam = np.full(pos.shape[1], a)
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    vc, best, cand, clump = _scan(orc, pos, lam, box)
+    dist = np.sqrt(((pos - c[:, None]) ** 2).sum(0))
+    assert vc.any() and not clump.any()
+    assert (dist[vc > 0] < 2.5 * a).all()              # only the hole's surroundings
+    assert (vc[dist > 3.0 * a] == 0).all()
+    cd = np.sqrt(((cand[:, vc > 0] - c[:, None]) ** 2).sum(0))
+    assert (cd < 0.8 * a).all()                        # candidates inside the hole
+
+
+def test_clump_marks_the_larger_index(orc):
+    """Two particles 0.1 lambda apart in an otherwise empty box: the one with
+    the larger index is marked; a third one at 0.2 lambda from both marks
+    itself too; at 0.3 lambda nothing is marked."""
+    lam0 = 0.02
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    pos = np.array([[0.5, 0.5 + 0.1 * lam0], [0.5, 0.5], [0.5, 0.5]])
+    _, _, _, clump = _scan(orc, pos, np.full(2, lam0), box)
+    assert clump.tolist() == [0, 1]
+    pos3 = np.array([[0.5, 0.5 + 0.1 * lam0, 0.5 + 0.05 * lam0],
+                     [0.5, 0.5, 0.5 + 0.19 * lam0], [0.5, 0.5, 0.5]])
+    _, _, _, clump = _scan(orc, pos3, np.full(3, lam0), box)
+    assert clump.tolist() == [0, 1, 1]
+    pos = np.array([[0.5, 0.5 + 0.3 * lam0], [0.5, 0.5], [0.5, 0.5]])
+    _, _, _, clump = _scan(orc, pos, np.full(2, lam0), box)
+    assert clump.tolist() == [0, 0]

@@ -13,6 +13,7 @@ import pytest
 import oracle
 from oracle import build as obuild
 
+import test_oracle_adapt as tadapt
 import test_oracle_fit as tfit
 import test_oracle_levels as tlev
 import test_oracle_neighbors as tnb
@@ -42,6 +43,11 @@ MUTATIONS = {
     "law_speed_without_field": ("const T c = sqrt((T(prm.gamma) * P + u[4] * u[4] + u[5] * u[5] + u[6] * u[6]) / u[0]);",
                                 "const T c = sqrt((T(prm.gamma) * P) / u[0]);"),
     "law_lambda_once": ("zeta = zeta - T(prm.c_zeta_a) * l * l * divV;", "zeta = zeta - T(prm.c_zeta_a) * l * divV;"),
+    "adapt_region_rf": ("if (!((ox * ox + oy * oy) + oz * oz < rin * rin)) continue;",
+                        "if (!((ox * ox + oy * oy) + oz * oz < r * r)) continue;"),
+    "adapt_clump_order": ("if (j < i && dd < dc * dc) cl = 1;", "if (j > i && dd < dc * dc) cl = 1;"),
+    "adapt_grid_step": ("const double h = r * 0.25;", "const double h = r * 0.2;"),
+    "adapt_best_first": ("if (mind > bclear) {", "if (mind >= bclear) {"),
     "basis_xyz_missing": ("p[13] = x * y * z;", "p[13] = x * y;"),
     "lambda_scale": ("grad[f][0] = C[0 * NF + f] * il;", "grad[f][0] = C[0 * NF + f] * il * il;"),
     "level_off_by_one": ("    int32_t L = 0;\n    while (L < max_level", "    int32_t L = 1;\n    while (L < max_level"),
@@ -56,6 +62,10 @@ MUTATIONS = {
 }
 
 PINS = [
+    lambda: tadapt.test_isolated_particle_counts_the_shell(oracle),
+    lambda: tadapt.test_lattice_has_no_voids_or_clumps(oracle),
+    lambda: tadapt.test_hole_in_a_lattice(oracle),
+    lambda: tadapt.test_clump_marks_the_larger_index(oracle),
     lambda: tnb.test_golden_ties_strict_periodic_nonmutual(oracle),
     lambda: tnb.test_exact_rational_bruteforce_tiny(oracle),
     lambda: tfit.test_cubic_reproduction(oracle, 0),
