@@ -61,7 +61,8 @@ def load(path: str):
     L.orc_timestep_levels.argtypes = [C.c_int64, _f64p, _f64p, C.c_double, C.c_double, C.c_double,
                                       C.c_int32, _i64p, _i64p, _i32p]
     L.orc_adapt_scan.argtypes = [C.POINTER(Box), C.c_int64, _f64p, _f64p, C.c_double, C.c_double,
-                                 C.c_double, _i64p, _i64p, _i32p, _i32p, _f64p, _i32p]
+                                 C.c_double, C.c_int64, _i64p, _i64p, _i64p, _i32p, _i32p, _f64p,
+                                 _i32p]
     L.orc_adapt_scan.restype = C.c_int64
     for f in ("orc_neighbors", "orc_mls_derivs", "orc_mhd_rhs", "orc_rhs_jvp", "orc_pc_step",
               "orc_timestep_levels"):
@@ -217,18 +218,22 @@ def pc_step(box: Box, pos, lam, U, dt, gamma=5.0 / 3.0, rf_factor=2.3, weight_ki
     return pos, U, nsing
 
 
-def adapt_scan(box: Box, pos, lam, nbrs, rf_factor=2.3, void_factor=1.0, clump_factor=0.25):
-    """Void and clump scan (see orc_adapt_scan); nbrs = CSR lists of all
-    particles at r_f.  Returns (void_count [n], best [n], cand [3][n], clump [n])."""
+def adapt_scan(box: Box, pos, lam, nbrs, query=None, rf_factor=2.3, void_factor=1.0,
+               clump_factor=0.25):
+    """Void and clump scan (see orc_adapt_scan) of the query particles; nbrs =
+    their CSR lists at r_f (as from neighbors(..., query)).  Returns
+    (void_count [nq], best [nq], cand [3][nq], clump [nq])."""
     pos, lam = _c(pos), _c(lam)
     n = lam.shape[0]
+    q = _query(n, query)
+    nq = q.shape[0]
     off, idx = nbrs
-    vc = np.zeros(n, np.int32)
-    best = np.zeros(n, np.int32)
-    cand = np.zeros((3, n))
-    clump = np.zeros(n, np.int32)
+    vc = np.zeros(nq, np.int32)
+    best = np.zeros(nq, np.int32)
+    cand = np.zeros((3, nq))
+    clump = np.zeros(nq, np.int32)
     lib().orc_adapt_scan(C.byref(box), n, pos, lam, float(rf_factor), float(void_factor),
-                         float(clump_factor), _c(off, np.int64),
+                         float(clump_factor), nq, q, _c(off, np.int64),
                          _c(idx, np.int64) if len(idx) else np.zeros(1, np.int64), vc, best, cand,
                          clump)
     return vc, best, cand, clump

@@ -483,14 +483,16 @@ int orc_timestep_levels(int64_t n, const double* lam, const double* U, double ga
 //   clump[i] = 1 when some j in N(i) with j < i has |x_j - x_i|^2 <
 //     (clump_factor lambda_i)^2: of two particles closer than that the one
 //     with the larger index is marked for deletion.
-// Returns the number of particles with a void.
+// For the query particles q[0..nq) with their lists at off[a]..off[a+1];
+// outputs indexed by a (cand [3][nq]).  Returns the number with a void.
 int64_t orc_adapt_scan(const Box* box, int64_t n, const double* pos, const double* lam,
-                       double rf_factor, double void_factor, double clump_factor,
-                       const int64_t* off, const int64_t* idx, int32_t* void_count, int32_t* best,
-                       double* cand, int32_t* clump) {
+                       double rf_factor, double void_factor, double clump_factor, int64_t nq,
+                       const int64_t* q, const int64_t* off, const int64_t* idx,
+                       int32_t* void_count, int32_t* best, double* cand, int32_t* clump) {
   int64_t with_void = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : with_void)
-  for (int64_t i = 0; i < n; ++i) {
+  for (int64_t a = 0; a < nq; ++a) {
+    const int64_t i = q[a];
     const double r = rf_factor * lam[i];
     const double h = r * 0.25;
     const double dv = void_factor * lam[i];
@@ -502,7 +504,7 @@ int64_t orc_adapt_scan(const Box* box, int64_t n, const double* pos, const doubl
     d.reserve(3 * (off[i + 1] - off[i] + 1));
     d.push_back(0.0); d.push_back(0.0); d.push_back(0.0);
     int32_t cl = 0;
-    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+    for (int64_t e = off[a]; e < off[a + 1]; ++e) {
       const int64_t j = idx[e];
       double o[3];
       for (int a = 0; a < 3; ++a)
@@ -533,17 +535,17 @@ int64_t orc_adapt_scan(const Box* box, int64_t n, const double* pos, const doubl
             bk = k;
           }
         }
-    void_count[i] = cnt;
-    best[i] = bk;
-    clump[i] = cl;
+    void_count[a] = cnt;
+    best[a] = bk;
+    clump[a] = cl;
     if (bk >= 0) {
       const int kx = bk / 81 - 4, ky = (bk / 9) % 9 - 4, kz = bk % 9 - 4;
-      cand[i] = pos[i] + kx * h;
-      cand[n + i] = pos[n + i] + ky * h;
-      cand[2 * n + i] = pos[2 * n + i] + kz * h;
+      cand[a] = pos[i] + kx * h;
+      cand[nq + a] = pos[n + i] + ky * h;
+      cand[2 * nq + a] = pos[2 * n + i] + kz * h;
       ++with_void;
     } else {
-      cand[i] = cand[n + i] = cand[2 * n + i] = 0.0;
+      cand[a] = cand[nq + a] = cand[2 * nq + a] = 0.0;
     }
   }
   return with_void;
