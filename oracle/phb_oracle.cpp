@@ -501,7 +501,7 @@ int64_t orc_adapt_scan(const Box* box, int64_t n, const double* pos, const doubl
     const double dc = clump_factor * lam[i];
     // offsets of the particle itself and its neighbours
     std::vector<double> d;
-    d.reserve(3 * (off[i + 1] - off[i] + 1));
+    d.reserve(3 * (off[a + 1] - off[a] + 1));
     d.push_back(0.0); d.push_back(0.0); d.push_back(0.0);
     int32_t cl = 0;
     for (int64_t e = off[a]; e < off[a + 1]; ++e) {

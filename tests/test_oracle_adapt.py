@@ -78,3 +78,18 @@ def test_clump_marks_the_larger_index(orc):
     pos = np.array([[0.5, 0.5 + 0.3 * lam0], [0.5, 0.5], [0.5, 0.5]])
     _, _, _, clump = _scan(orc, pos, np.full(2, lam0), box)
     assert clump.tolist() == [0, 0]
+
+
+def test_query_subset_matches_the_full_scan(orc):
+    """The sampled form (lists of the query particles only) gives the full
+    scan's values at those particles."""
+    rng = np.random.default_rng(8)
+    pos = rng.random((3, 3000))
+    lam = np.full(3000, 0.04)
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    full = _scan(orc, pos, lam, box)
+    q = np.sort(rng.choice(3000, 200, replace=False)).astype(np.int64)
+    sub = orc.adapt_scan(box, pos, lam, orc.neighbors(box, pos, lam, q), q)
+    assert full[0].any() and full[3].any()
+    for a, b in zip(full, sub):
+        np.testing.assert_array_equal(a[..., q], b)
