@@ -180,6 +180,31 @@ phb_status phb_build_neighbors(const phb_plan* plan, const double* pos, const do
                                void* ws, size_t ws_bytes, int32_t* status_word,
                                phb_stream_t stream);
 
+/* Particle adaptivity scan (Sec. 2: particles are added to voids and deleted
+ * from clumps so that every sphere of radius r_f stays well sampled; Sec.
+ * 2.1: the void search measures distances from the points of a 9^3 grid to
+ * the neighbour particles and drops every point found close to one).  The
+ * thresholds are Paper I's and are readings here.  With the lists of the
+ * last build (pos and lambda may have moved since, within the skin), for
+ * every particle i, r = rf_factor lambda_i, h = r / 4, d_v = void_factor
+ * lambda_i, d_c = clump_factor lambda_i:
+ *   test points o_k = h (kx, ky, kz), kx, ky, kz in -4..4, grid index
+ *   k = ((kx+4) 9 + (ky+4)) 9 + (kz+4), those with |o_k| < r - d_v; a point
+ *   is covered when i or a particle of its r_f set lies closer than d_v;
+ *   void_count[i] = uncovered points; best[i] = the uncovered point whose
+ *   nearest particle is farthest (lowest k on ties), -1 if none;
+ *   cand [3][n] = x_i + o_best (0 if none), the place for a new particle;
+ *   clump[i] = 1 when a neighbour with a smaller index lies closer than d_c
+ *   (of a too-close pair the larger index is the one to delete).
+ * Distances that decide an output are FP64 in the order written, so the
+ * outputs are exact.  All outputs device arrays in caller order, each may be
+ * NULL.  0 < void_factor < rf_factor and 0 <= clump_factor < rf_factor, else
+ * PHB_ERR_INVALID_ARG. */
+phb_status phb_adapt_scan(const phb_plan* plan, const double* pos, const double* lambda,
+                          double void_factor, double clump_factor, void* ws, size_t ws_bytes,
+                          int32_t* void_count, int32_t* best, double* cand, int32_t* clump,
+                          int32_t* status_word, phb_stream_t stream);
+
 /* Put the caller's particle arrays into the library's storage order - the
  * cells of the last build along their Hilbert curve, members of a cell by
  * caller index - as a tree code keeps its particles in Peano-Hilbert order

@@ -177,6 +177,22 @@ def build_neighbors(plan: Plan, pos: torch.Tensor, lam: torch.Tensor, check_capa
             raise PhbError(int(L.phb_check(w)), "phb_build_neighbors")
 
 
+def adapt_scan(plan: Plan, pos, lam, void_factor: float = 1.0, clump_factor: float = 0.25):
+    """Particle adaptivity scan (phb_adapt_scan) with the lists of the last build:
+    returns (void_count int32 [n], best int32 [n], cand float64 [3, n], clump int32 [n])."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam")
+    vc = torch.empty(n, dtype=torch.int32, device=plan.device)
+    best = torch.empty(n, dtype=torch.int32, device=plan.device)
+    cand = torch.empty((3, n), dtype=torch.float64, device=plan.device)
+    clump = torch.empty(n, dtype=torch.int32, device=plan.device)
+    check(_lib.lib().phb_adapt_scan(C.byref(plan.c), _ptr(pos), _ptr(lam), float(void_factor),
+                                    float(clump_factor), _ptr(plan.ws), plan.ws.numel(), _ptr(vc),
+                                    _ptr(best), _ptr(cand), _ptr(clump), _ptr(plan.status_word),
+                                    _stream()), "phb_adapt_scan")
+    return vc, best, cand, clump
+
+
 def reorder(plan: Plan, pos, lam, U):
     """Permute pos, lam and U in place into the storage order of the last build
     (phb_reorder); returns the int32 [n] tensor of old indices, for the caller's

@@ -624,6 +624,177 @@ __global__ void __launch_bounds__(1024) k_tile_order(int n, int T, int ntiles, i
   }
 }
 
+// -------- particle adaptivity scan (voids on a 9^3 grid of test points,
+// clumps of too-close particles; see phb_adapt_scan)
+
+// Slot-order copies of positions and lambda and wrapped FP32 screen
+// positions for positions that may have moved since the build (the cells
+// and tile plans of the build are left alone).
+__global__ void k_adapt_gather(Grid g, const int32_t* __restrict__ perm, const double* __restrict__ pos,
+                               const double* __restrict__ lam, double* __restrict__ spos,
+                               double* __restrict__ slam, float4* __restrict__ scr) {
+  const int n = g.n;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int i = perm[s];
+  float w[3];
+  for (int a = 0; a < 3; ++a) {
+    const double x = pos[a * n + i];
+    spos[a * n + s] = x;
+    double k = 0.0;
+    if (isfinite(x)) cell_wrap(g, a, x, k);
+    w[a] = static_cast<float>(__dsub_rn(x, __dmul_rn(k, g.len[a])));
+  }
+  slam[s] = lam[i];
+  scr[s] = make_float4(w[0], w[1], w[2], 0.f);
+}
+
+constexpr int kGrid = 9;                       // test points per axis
+constexpr int kGridPts = kGrid * kGrid * kGrid;
+
+// FP32 offset of record o from me, minimum image on periodic axes.
+__device__ __forceinline__ float3 offset32(const Screen& q, float4 me, float4 o) {
+  float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
+  dx = fmaf(-q.lenf[0], rintf(dx * q.invlf[0]), dx);
+  dy = fmaf(-q.lenf[1], rintf(dy * q.invlf[1]), dy);
+  dz = fmaf(-q.lenf[2], rintf(dz * q.invlf[2]), dz);
+  return make_float3(dx, dy, dz);
+}
+
+// Exact FP64 squared distance from neighbour t of slot s to the test point
+// at offset (ox, oy, oz): ((ex*ex + ey*ey) + ez*ez), e = min-image(x_t - x_s) - o.
+__device__ __forceinline__ double test_dist2(const Grid& g, const double* spos, int n, int s, int t,
+                                             double ox, double oy, double oz) {
+  const double ex = __dsub_rn(min_image64(__dsub_rn(spos[t], spos[s]), g.len[0], g.periodic[0]), ox);
+  const double ey =
+      __dsub_rn(min_image64(__dsub_rn(spos[n + t], spos[n + s]), g.len[1], g.periodic[1]), oy);
+  const double ez =
+      __dsub_rn(min_image64(__dsub_rn(spos[2 * n + t], spos[2 * n + s]), g.len[2], g.periodic[2]), oz);
+  return __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+}
+
+// Thread per slot.  Every FP64 quantity that decides an output is computed
+// with single IEEE-rounded operations in the order of the definition; FP32
+// screens with a margin only skip work whose outcome they prove.
+__global__ void __launch_bounds__(128) k_adapt_scan(Grid g, const int32_t* __restrict__ perm,
+                                                   const double* __restrict__ spos,
+                                                   const double* __restrict__ slam,
+                                                   const float4* __restrict__ scr,
+                                                   const int64_t* __restrict__ off,
+                                                   const int32_t* __restrict__ idx, double vf, double cf,
+                                                   int32_t* void_count, int32_t* best, double* cand,
+                                                   int32_t* clump) {
+  // candidate test points: every grid point that can lie inside r_f - d_v for
+  // some lambda (a superset; each particle applies the exact test), ascending
+  __shared__ int16_t pts[kGridPts];
+  __shared__ int npts;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const double q = (g.rf_factor - vf) / (0.25 * g.rf_factor);
+    const double lim = q > 0.0 ? q * q * (1.0 + 1e-6) : -1.0;
+    int base = 0;
+    for (int k0 = 0; k0 < kGridPts; k0 += 32) {
+      const int k = k0 + lane;
+      bool in = false;
+      if (k < kGridPts) {
+        const int kx = k / 81 - 4, ky = (k / 9) % 9 - 4, kz = k % 9 - 4;
+        in = static_cast<double>(kx * kx + ky * ky + kz * kz) <= lim;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (in) pts[base + __popc(m & ((1u << lane) - 1u))] = static_cast<int16_t>(k);
+      base += __popc(m);
+    }
+    if (lane == 0) npts = base;
+  }
+  __syncthreads();
+  const int n = g.n;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int64_t N = n;
+  const double lam = slam[s];
+  const double r = __dmul_rn(g.rf_factor, lam);
+  const double r2 = __dmul_rn(r, r);
+  const double h = __dmul_rn(r, 0.25);
+  const double dv = __dmul_rn(vf, lam);
+  const double dv2 = __dmul_rn(dv, dv);
+  const double rin = __dsub_rn(r, dv);
+  const double rin2 = __dmul_rn(rin, rin);
+  const double dc = __dmul_rn(cf, lam);
+  const double dc2 = __dmul_rn(dc, dc);
+  const Screen q = make_screen(g, r);
+  // FP32 screens: |d32 - d| is within the coordinate margin; offsets and
+  // squares add a few ulps of r
+  const double m = static_cast<double>(g.screen_margin) + 1e-6 * r;
+  const float v_in2 = static_cast<float>(dv > m ? (dv - m) * (dv - m) : 0.0);
+  const float v_out2 = static_cast<float>((dv + m) * (dv + m));
+  const float c_in2 = static_cast<float>(dc > m ? (dc - m) * (dc - m) : 0.0);
+  const float c_out2 = static_cast<float>((dc + m) * (dc + m));
+  const float4 me = scr[s];
+  const int me_caller = perm[s];
+  const int64_t beg = off[s];
+  const int64_t end = off[s + 1] < g.capacity ? off[s + 1] : g.capacity;
+
+  // clumps: a neighbour with a smaller caller index closer than d_c
+  int32_t cl = 0;
+  for (int64_t e = beg; e < end && !cl; ++e) {
+    const int t = idx[e];
+    if (perm[t] >= me_caller) continue;
+    const float3 d = offset32(q, me, scr[t]);
+    const float dd = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+    if (dd < c_in2) cl = 1;
+    else if (dd <= c_out2 && dist2_exact(g, spos, n, s, t) < dc2) cl = 1;
+  }
+
+  // voids: test points not within d_v of the particle or a neighbour
+  int32_t cnt = 0, bk = -1;
+  double bclear = -1.0;
+  for (int p = 0; p < npts; ++p) {
+    const int k = pts[p];
+    const int kx = k / 81 - 4, ky = (k / 9) % 9 - 4, kz = k % 9 - 4;
+    const double ox = __dmul_rn(static_cast<double>(kx), h);
+    const double oy = __dmul_rn(static_cast<double>(ky), h);
+    const double oz = __dmul_rn(static_cast<double>(kz), h);
+    const double o2 = __dadd_rn(__dadd_rn(__dmul_rn(ox, ox), __dmul_rn(oy, oy)), __dmul_rn(oz, oz));
+    if (!(o2 < rin2)) continue;  // outside r_f - d_v
+    if (o2 < dv2) continue;      // covered by the particle itself
+    const float fx = static_cast<float>(ox), fy = static_cast<float>(oy), fz = static_cast<float>(oz);
+    bool covered = false;
+    for (int64_t e = beg; e < end && !covered; ++e) {
+      const int t = idx[e];
+      const float3 d = offset32(q, me, scr[t]);
+      const float ex = d.x - fx, ey = d.y - fy, ez = d.z - fz;
+      const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+      if (e2 < v_in2) covered = true;
+      else if (e2 <= v_out2 && test_dist2(g, spos, n, s, t, ox, oy, oz) < dv2) covered = true;
+    }
+    if (covered) continue;
+    // uncovered: its clearance over the particle and its exact r_f set
+    double clear = o2;
+    for (int64_t e = beg; e < end; ++e) {
+      const int t = idx[e];
+      if (!(dist2_exact(g, spos, n, s, t) < r2)) continue;  // a skin entry, not in N(i)
+      const double e2 = test_dist2(g, spos, n, s, t, ox, oy, oz);
+      clear = e2 < clear ? e2 : clear;
+    }
+    ++cnt;
+    if (clear > bclear) {
+      bclear = clear;
+      bk = k;
+    }
+  }
+  if (void_count) void_count[me_caller] = cnt;
+  if (best) best[me_caller] = bk;
+  if (clump) clump[me_caller] = cl;
+  if (cand) {
+    double c[3] = {0.0, 0.0, 0.0};
+    if (bk >= 0) {
+      const int kk[3] = {bk / 81 - 4, (bk / 9) % 9 - 4, bk % 9 - 4};
+      for (int a = 0; a < 3; ++a) c[a] = __dadd_rn(spos[a * N + s], __dmul_rn(static_cast<double>(kk[a]), h));
+    }
+    for (int a = 0; a < 3; ++a) cand[a * N + me_caller] = c[a];
+  }
+}
+
 // -------- storage order
 __global__ void k_identity(int n, int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -765,6 +936,33 @@ extern "C" phb_status phb_build_neighbors(const phb_plan* plan, const double* po
   if (!pos || !lambda) return PHB_ERR_INVALID_ARG;
   return launch_status(build_neighbors_impl(plan, pos, lambda, ws, status_word,
                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" phb_status phb_adapt_scan(const phb_plan* plan, const double* pos, const double* lambda,
+                                     double void_factor, double clump_factor, void* ws, size_t ws_bytes,
+                                     int32_t* void_count, int32_t* best, double* cand, int32_t* clump,
+                                     int32_t* status_word, phb_stream_t stream) {
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_END_COMMON] : 0);
+  if (s != PHB_OK) return s;
+  if (!pos || !lambda) return PHB_ERR_INVALID_ARG;
+  if (!(void_factor > 0.0) || !(void_factor < plan->rf_factor) || !(clump_factor >= 0.0) ||
+      !(clump_factor < plan->rf_factor))
+    return PHB_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Grid g = make_grid(plan);
+  const int n = g.n;
+  const int32_t* perm = region<int32_t>(plan, ws, R_PERM);
+  double* spos = region<double>(plan, ws, R_SPOS);
+  double* slam = region<double>(plan, ws, R_SLAM);
+  float4* scr = region<float4>(plan, ws, R_SCREEN);
+  k_adapt_gather<<<blocks_for(n), kThreads, 0, st>>>(g, perm, pos, lambda, spos, slam, scr);
+  note_launch();
+  k_adapt_scan<<<blocks_for(n, 128), 128, 0, st>>>(g, perm, spos, slam, scr,
+                                                   region<int64_t>(plan, ws, R_OFF),
+                                                   region<int32_t>(plan, ws, R_IDX), void_factor,
+                                                   clump_factor, void_count, best, cand, clump);
+  note_launch();
+  return launch_status(cudaGetLastError());
 }
 
 extern "C" phb_status phb_reorder(const phb_plan* plan, double* pos, double* lambda, double* U,
