@@ -239,6 +239,70 @@ def adapt_scan(box: Box, pos, lam, nbrs, query=None, rf_factor=2.3, void_factor=
     return vc, best, cand, clump
 
 
+def adapt_apply(box: Box, pos, lam, U, nbrs, scan, grad, hess, rf_factor=2.3, void_factor=1.0):
+    """Particle deletion and creation from an adaptivity scan (Sec. 2: particles
+    are added in voids and deleted in clumps), readings where Paper I is not
+    available:
+      * a particle marked as a clump is deleted;
+      * a surviving particle i with a void creates one particle at its best
+        test point c_i if c_i lies inside the box on every open axis
+        ([lo, lo + len)), unless a surviving neighbour j in N(i) with j < i
+        creates one at a point closer than d_v = void_factor lambda_i to c_i;
+      * the new particle takes lambda_i and the second-order Taylor value of
+        i's fit at o = c_i - x_i: U_i + grad U_i . o + o^T (hess U_i) o / 2;
+      * survivors keep their order, new particles follow in parent order;
+        origin = old index for survivors, n + parent for new particles.
+    nbrs: CSR lists of all particles at r_f; scan = (void_count, best, cand,
+    clump) of all particles; grad [8][3][n], hess [8][6][n] (xx xy xz yy yz zz).
+    Returns (pos [3][m], lam [m], U [8][m], origin [m])."""
+    pos, lam, U = _c(pos), _c(lam), _c(U)
+    n = lam.shape[0]
+    off, idx = nbrs
+    _, best, cand, clump = scan
+    keep = clump == 0
+    length = np.array(box.len[:3])
+    lo = np.array(box.lo[:3])
+    per = np.array(box.periodic[:3]) != 0
+
+    def dist2(a, b):
+        d = a - b
+        for ax in range(3):
+            if per[ax]:
+                d[ax] = d[ax] - length[ax] * np.rint(d[ax] / length[ax])
+        return (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+
+    inside = np.ones(n, bool)
+    for ax in range(3):
+        if not per[ax]:
+            inside &= (cand[ax] >= lo[ax]) & (cand[ax] < lo[ax] + length[ax])
+    wants = keep & (best >= 0) & inside
+    create = np.zeros(n, bool)
+    for i in range(n):
+        if not wants[i]:
+            continue
+        dv = void_factor * lam[i]
+        create[i] = True
+        for j in idx[off[i]:off[i + 1]]:
+            if j < i and wants[j] and dist2(cand[:, j], cand[:, i]) < dv * dv:
+                create[i] = False
+                break
+    parents = np.nonzero(create)[0]
+    o = cand[:, parents] - pos[:, parents]
+    Unew = U[:, parents].copy()
+    hi = {(0, 0): 0, (0, 1): 1, (0, 2): 2, (1, 1): 3, (1, 2): 4, (2, 2): 5}
+    for f in range(8):
+        for a in range(3):
+            Unew[f] += grad[f, a, parents] * o[a]
+            for b in range(3):
+                Unew[f] += 0.5 * hess[f, hi[(min(a, b), max(a, b))], parents] * o[a] * o[b]
+    surv = np.nonzero(keep)[0]
+    pos_out = np.concatenate([pos[:, surv], cand[:, parents]], axis=1)
+    lam_out = np.concatenate([lam[surv], lam[parents]])
+    U_out = np.concatenate([U[:, surv], Unew], axis=1)
+    origin = np.concatenate([surv, n + parents]).astype(np.int64)
+    return pos_out, lam_out, U_out, origin
+
+
 def timestep_levels(lam, U, nbrs, gamma=5.0 / 3.0, cfl=0.1, dt_max=1.0, max_level=20):
     """Individual power-of-two time-step levels with the spatial limiter
     (see orc_timestep_levels); nbrs = CSR lists of all particles."""
@@ -269,7 +333,7 @@ def available() -> bool:
         return False
 
 
-__all__ = ["Box", "Params", "lib", "load", "using", "make_box", "box_of", "neighbors", "mls_derivs", "mhd_rhs", "adapt_scan",
+__all__ = ["Box", "Params", "lib", "load", "using", "make_box", "box_of", "neighbors", "mls_derivs", "mhd_rhs", "adapt_scan", "adapt_apply",
            "rhs_jvp", "pc_step", "timestep_levels", "workload_rhs", "available"]
 
 if os.environ.get("PHB_ORACLE_EAGER"):

@@ -93,3 +93,73 @@ def test_query_subset_matches_the_full_scan(orc):
     assert full[0].any() and full[3].any()
     for a, b in zip(full, sub):
         np.testing.assert_array_equal(a[..., q], b)
+
+
+def _hole_lattice(a, field):
+    g = (np.arange(12) + 0.5) * a
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()])
+    c = np.array([6.0, 6.0, 6.0]) * a
+    keep = ~np.all(np.abs(pos - c[:, None]) < a, axis=0)
+    pos = np.ascontiguousarray(pos[:, keep])
+    U = field(pos)
+    return pos, np.full(pos.shape[1], a), U, c
+
+
+def _quadratic(pos):
+    """Fields quadratic in x (reproduced exactly by the fit and by its
+    second-order Taylor value), positive density and energy."""
+    x, y, z = pos - 0.5
+    U = np.empty((8, pos.shape[1]))
+    U[0] = 1.0 + 0.3 * x + 0.2 * y * z
+    U[1] = 0.1 * x * x - 0.2 * y
+    U[2] = 0.05 * x * y + 0.3 * z
+    U[3] = -0.1 * z * z + 0.07 * x
+    U[4] = 0.5 + 0.1 * y
+    U[5] = 0.2 * x * z
+    U[6] = -0.3 + 0.04 * y * y
+    U[7] = 2.0 + 0.1 * x * y
+    return U
+
+
+def test_apply_fills_the_hole_with_exact_states(orc):
+    """New particles sit inside the hole, take the parent's lambda and the
+    field's exact value there (quadratic fields: the fit and its second-order
+    Taylor value are exact, in an open box to keep the fields smooth); the
+    lowest-index parent of a group of nearby points wins; a second scan sees
+    fewer voids."""
+    a = 1.0 / 12
+    pos, lam, U, c = _hole_lattice(a, _quadratic)
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (0, 0, 0))
+    nb = orc.neighbors(box, pos, lam)
+    scan = orc.adapt_scan(box, pos, lam, nb)
+    g, h, st = orc.mls_derivs(box, pos, lam, U, nb)
+    p2, l2, U2, origin = orc.adapt_apply(box, pos, lam, U, nb, scan, g, h)
+    n = pos.shape[1]
+    new = origin >= n
+    assert new.sum() >= 1 and new.sum() < (scan[0] > 0).sum()    # deduplicated and walls skipped
+    assert np.array_equal(origin[~new], np.arange(n))              # no clumps here
+    inside = np.all((p2[:, new] >= 0) & (p2[:, new] < 1), axis=0)
+    assert inside.all()                                            # none beyond the open walls
+    near = np.sqrt(((pos[:, origin[new] - n] - c[:, None]) ** 2).sum(0)) < 2.5 * a
+    assert near.any()
+    assert (np.sqrt(((p2[:, new][:, near] - c[:, None]) ** 2).sum(0)) < 0.8 * a).all()
+    np.testing.assert_allclose(U2[:, new], _quadratic(p2[:, new]), rtol=0, atol=1e-12)
+    assert (l2[new] == a).all()
+    nb2 = orc.neighbors(box, p2, l2)
+    vc2 = orc.adapt_scan(box, p2, l2, nb2)[0]
+    assert vc2.sum() < scan[0].sum()
+
+
+def test_apply_deletes_the_larger_index_of_a_pair(orc):
+    lam0 = 0.02
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    pos = np.array([[0.3, 0.5, 0.5 + 0.1 * lam0], [0.5, 0.5, 0.5], [0.5, 0.5, 0.5]])
+    lam = np.full(3, lam0)
+    U = np.ones((8, 3))
+    nb = orc.neighbors(box, pos, lam)
+    scan = orc.adapt_scan(box, pos, lam, nb)
+    z = np.zeros((8, 3, 3)), np.zeros((8, 6, 3))
+    p2, l2, U2, origin = orc.adapt_apply(box, pos, lam, U, nb, scan, *z)
+    survivors = origin[origin < 3]
+    assert survivors.tolist() == [0, 1]
