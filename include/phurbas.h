@@ -205,6 +205,28 @@ phb_status phb_adapt_scan(const phb_plan* plan, const double* pos, const double*
                           int32_t* void_count, int32_t* best, double* cand, int32_t* clump,
                           int32_t* status_word, phb_stream_t stream);
 
+/* Particle deletion and creation from a phb_adapt_scan of the same state and
+ * build (Sec. 2: particles are added in voids and deleted in clumps; how is
+ * Paper I's, the readings here): a particle marked as a clump is deleted; a
+ * surviving particle i with a void creates one particle at cand_i when that
+ * point lies inside the box on every open axis, unless a neighbour j < i of
+ * its r_f set creates one closer than void_factor lambda_i to it; the new
+ * particle takes lambda_i and the second-order Taylor value of i's fit at
+ * o = cand_i - x_i, U + sum_a (grad_a o_a + sum_b ((hess_ab / 2) o_a) o_b),
+ * from grad [8][3][n] and hess [8][6][n] of phb_mls_derivs.  Outputs of
+ * leading dimension cap (pos_out [3][cap], lambda_out [cap], U_out [8][cap],
+ * origin [cap]): survivors in order (origin = old index), then the new
+ * particles in parent order (origin = n + parent); m_out (device int64) is
+ * the new count - above cap nothing past cap is written and
+ * PHB_FLAG_CAPACITY is raised.  Inputs and outputs are device arrays in
+ * caller order; the plan and its lists stay those of the old set. */
+phb_status phb_adapt_apply(const phb_plan* plan, const double* pos, const double* lambda,
+                           const double* U, const int32_t* best, const double* cand,
+                           const int32_t* clump, const double* grad, const double* hess,
+                           double void_factor, int64_t cap, double* pos_out, double* lambda_out,
+                           double* U_out, int64_t* origin, int64_t* m_out, void* ws,
+                           size_t ws_bytes, int32_t* status_word, phb_stream_t stream);
+
 /* Put the caller's particle arrays into the library's storage order - the
  * cells of the last build along their Hilbert curve, members of a cell by
  * caller index - as a tree code keeps its particles in Peano-Hilbert order

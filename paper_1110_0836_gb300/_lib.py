@@ -29,7 +29,7 @@ EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_chec
            "phb_trace_start", "phb_trace_stop", "phb_trace_read", "phb_workspace_stats", "phb_mhd_rhs_noalloc",
            "phb_noalloc_scratch_bytes", "phb_adjoint_record_bytes", "phb_adjoint_record",
            "phb_rhs_adjoint_stored", "phb_mhd_rhs_active", "phb_timestep_levels",
-           "phb_struct_sizes", "phb_reorder", "phb_adapt_scan"]
+           "phb_struct_sizes", "phb_reorder", "phb_adapt_scan", "phb_adapt_apply"]
 
 
 class Box(C.Structure):
@@ -125,6 +125,9 @@ def lib(path: str | None = None) -> C.CDLL:
     L.phb_adapt_scan.argtypes = [P(Plan), _vp, _vp, C.c_double, C.c_double, _vp, C.c_size_t, _vp,
                                  _vp, _vp, _vp, _vp, _vp]
     L.phb_adapt_scan.restype = C.c_int
+    L.phb_adapt_apply.argtypes = [P(Plan), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_double,
+                                  C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp, _vp]
+    L.phb_adapt_apply.restype = C.c_int
     L.phb_reorder.restype = C.c_int
     L.phb_struct_sizes.argtypes = [_vp, C.c_int32]
     L.phb_struct_sizes.restype = C.c_int

@@ -193,6 +193,42 @@ def adapt_scan(plan: Plan, pos, lam, void_factor: float = 1.0, clump_factor: flo
     return vc, best, cand, clump
 
 
+def adapt_apply(plan: Plan, pos, lam, U, scan, grad, hess, void_factor: float = 1.0,
+                capacity: int | None = None):
+    """Delete clump-marked particles and create one per void (phb_adapt_apply);
+    returns (pos [3, m], lam [m], U [8, m], origin int64 [m]) with origin = old
+    index for survivors and n + parent for new particles.  Synchronises to read m."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    _need(grad, (8, 3, n), "grad"), _need(hess, (8, 6, n), "hess")
+    _, best, cand, clump = scan
+    cap = 2 * n if capacity is None else int(capacity)
+    dev = plan.device
+    po = torch.empty((3, cap), dtype=torch.float64, device=dev)
+    lo = torch.empty(cap, dtype=torch.float64, device=dev)
+    Uo = torch.empty((8, cap), dtype=torch.float64, device=dev)
+    org = torch.empty(cap, dtype=torch.int64, device=dev)
+    m = torch.zeros(1, dtype=torch.int64, device=dev)
+    check(_lib.lib().phb_adapt_apply(C.byref(plan.c), _ptr(pos), _ptr(lam), _ptr(U), _ptr(best),
+                                     _ptr(cand), _ptr(clump), _ptr(grad), _ptr(hess),
+                                     float(void_factor), cap, _ptr(po), _ptr(lo), _ptr(Uo), _ptr(org),
+                                     _ptr(m), _ptr(plan.ws), plan.ws.numel(), _ptr(plan.status_word),
+                                     _stream()), "phb_adapt_apply")
+    k = int(m.item())
+    if k > cap:
+        raise PhbError(int(_lib.PHB_ERR_CAPACITY), f"phb_adapt_apply: {k} particles > capacity {cap}")
+    return po[:, :k].contiguous(), lo[:k].clone(), Uo[:, :k].contiguous(), org[:k].clone()
+
+
+def adapt(plan: Plan, params: Params, pos, lam, U, void_factor: float = 1.0,
+          clump_factor: float = 0.25):
+    """One adaptivity pass with the lists of the last build: scan, fit
+    derivatives, deletion and creation.  Returns the new (pos, lam, U, origin)."""
+    scan = adapt_scan(plan, pos, lam, void_factor, clump_factor)
+    g, h, _ = mls_derivs(plan, params, pos, lam, U)
+    return adapt_apply(plan, pos, lam, U, scan, g, h, void_factor)
+
+
 def reorder(plan: Plan, pos, lam, U):
     """Permute pos, lam and U in place into the storage order of the last build
     (phb_reorder); returns the int32 [n] tensor of old indices, for the caller's

@@ -795,6 +795,125 @@ __global__ void __launch_bounds__(128) k_adapt_scan(Grid g, const int32_t* __res
   }
 }
 
+// Deletion and creation flags (caller order) from a scan: wants = survives
+// (no clump mark), has a void and its point lies inside the box on every open
+// axis; keep = survives.
+__global__ void k_apply_wants(Grid g, const int32_t* __restrict__ best, const double* __restrict__ cand,
+                              const int32_t* __restrict__ clump, int32_t* __restrict__ wants,
+                              int32_t* __restrict__ keep) {
+  const int n = g.n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  if (i == n) {  // scan sentinels
+    keep[n] = 0;
+    return;
+  }
+  const int64_t N = n;
+  bool in = true;
+  for (int a = 0; a < 3; ++a) {
+    const double c = cand[a * N + i];
+    if (!g.periodic[a]) in = in && c >= g.lo[a] && c < __dadd_rn(g.lo[a], g.len[a]);
+  }
+  keep[i] = clump[i] == 0 ? 1 : 0;
+  wants[i] = (clump[i] == 0 && best[i] >= 0 && in) ? 1 : 0;
+}
+
+// create[i]: i wants a particle and no neighbour j of its exact r_f set with
+// j < i wants one at a point closer than d_v = vf lambda_i (FP64, minimum
+// image, in the order ((dx*dx + dy*dy) + dz*dz)).  Thread per slot.
+__global__ void k_apply_create(Grid g, const int32_t* __restrict__ perm, const double* __restrict__ spos,
+                               const double* __restrict__ slam, const int64_t* __restrict__ off,
+                               const int32_t* __restrict__ idx, const double* __restrict__ cand,
+                               const int32_t* __restrict__ wants, double vf,
+                               int32_t* __restrict__ create) {
+  const int n = g.n;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > n) return;
+  if (s == n) {
+    create[n] = 0;
+    return;
+  }
+  const int64_t N = n;
+  const int i = perm[s];
+  int32_t c = wants[i];
+  if (c) {
+    const double lam = slam[s];
+    const double r = __dmul_rn(g.rf_factor, lam);
+    const double r2 = __dmul_rn(r, r);
+    const double dv = __dmul_rn(vf, lam);
+    const double dv2 = __dmul_rn(dv, dv);
+    const double ci[3] = {cand[i], cand[N + i], cand[2 * N + i]};
+    const int64_t end = off[s + 1] < g.capacity ? off[s + 1] : g.capacity;
+    for (int64_t e = off[s]; e < end && c; ++e) {
+      const int t = idx[e];
+      const int j = perm[t];
+      if (j >= i || !wants[j]) continue;
+      if (!(dist2_exact(g, spos, n, s, t) < r2)) continue;  // skin entry
+      double d2 = 0.0;
+      double dd[3];
+      for (int a = 0; a < 3; ++a) dd[a] = min_image64(__dsub_rn(cand[a * N + j], ci[a]), g.len[a], g.periodic[a]);
+      d2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])), __dmul_rn(dd[2], dd[2]));
+      if (d2 < dv2) c = 0;
+    }
+  }
+  create[i] = c;
+}
+
+// Survivors (in order) then new particles (in parent order) into the output
+// arrays of leading dimension cap; ks / cs: exclusive scans of keep / create
+// (their totals at n).  New particles: lambda of the parent and its
+// second-order Taylor value at o = c - x, accumulated as
+// U + sum_a (g_a o_a + sum_b ((h_ab / 2) o_a) o_b).
+__global__ void k_apply_write(int n, int64_t cap, const double* __restrict__ pos,
+                              const double* __restrict__ lam, const double* __restrict__ U,
+                              const double* __restrict__ cand, const double* __restrict__ grad,
+                              const double* __restrict__ hess, const int32_t* __restrict__ ks,
+                              const int32_t* __restrict__ cs, double* __restrict__ pos_out,
+                              double* __restrict__ lam_out, double* __restrict__ U_out,
+                              int64_t* __restrict__ origin, int64_t* m_out, int32_t* status_word) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t N = n;
+  const int64_t nk = ks[n];
+  if (i == 0) {
+    const int64_t m = nk + cs[n];
+    *m_out = m;
+    if (m > cap) raise_flag(status_word, PHB_FLAG_CAPACITY);
+  }
+  if (ks[i + 1] != ks[i]) {
+    const int64_t k = ks[i];
+    if (k < cap) {
+      for (int a = 0; a < 3; ++a) pos_out[a * cap + k] = pos[a * N + i];
+      lam_out[k] = lam[i];
+      for (int f = 0; f < 8; ++f) U_out[f * cap + k] = U[f * N + i];
+      origin[k] = i;
+    }
+  }
+  if (cs[i + 1] != cs[i]) {
+    const int64_t k = nk + cs[i];
+    if (k < cap) {
+      double o[3];
+      for (int a = 0; a < 3; ++a) {
+        const double c = cand[a * N + i];
+        pos_out[a * cap + k] = c;
+        o[a] = __dsub_rn(c, pos[a * N + i]);
+      }
+      lam_out[k] = lam[i];
+      const int hx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+      for (int f = 0; f < 8; ++f) {
+        double u = U[f * N + i];
+        for (int a = 0; a < 3; ++a) {
+          u = __dadd_rn(u, __dmul_rn(grad[(f * 3 + a) * N + i], o[a]));
+          for (int b = 0; b < 3; ++b)
+            u = __dadd_rn(u, __dmul_rn(__dmul_rn(__dmul_rn(0.5, hess[(f * 6 + hx[a][b]) * N + i]), o[a]), o[b]));
+        }
+        U_out[f * cap + k] = u;
+      }
+      origin[k] = N + i;
+    }
+  }
+}
+
 // -------- storage order
 __global__ void k_identity(int n, int32_t* __restrict__ perm, int32_t* __restrict__ inv) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -961,6 +1080,49 @@ extern "C" phb_status phb_adapt_scan(const phb_plan* plan, const double* pos, co
                                                    region<int64_t>(plan, ws, R_OFF),
                                                    region<int32_t>(plan, ws, R_IDX), void_factor,
                                                    clump_factor, void_count, best, cand, clump);
+  note_launch();
+  return launch_status(cudaGetLastError());
+}
+
+extern "C" phb_status phb_adapt_apply(const phb_plan* plan, const double* pos, const double* lambda,
+                                      const double* U, const int32_t* best, const double* cand,
+                                      const int32_t* clump, const double* grad, const double* hess,
+                                      double void_factor, int64_t cap, double* pos_out,
+                                      double* lambda_out, double* U_out, int64_t* origin,
+                                      int64_t* m_out, void* ws, size_t ws_bytes, int32_t* status_word,
+                                      phb_stream_t stream) {
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_END_COMMON] : 0);
+  if (s != PHB_OK) return s;
+  if (!pos || !lambda || !U || !best || !cand || !clump || !grad || !hess || !pos_out ||
+      !lambda_out || !U_out || !origin || !m_out || cap < 0)
+    return PHB_ERR_INVALID_ARG;
+  if (!(void_factor > 0.0) || !(void_factor < plan->rf_factor)) return PHB_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Grid g = make_grid(plan);
+  const int n = g.n;
+  const int32_t* perm = region<int32_t>(plan, ws, R_PERM);
+  double* spos = region<double>(plan, ws, R_SPOS);
+  double* slam = region<double>(plan, ws, R_SLAM);
+  float4* scr = region<float4>(plan, ws, R_SCREEN);
+  int32_t* wants = region<int32_t>(plan, ws, R_QUEUE);
+  int32_t* keep = region<int32_t>(plan, ws, R_AFLAG);
+  int32_t* create = region<int32_t>(plan, ws, R_ALIST);
+  int64_t* bsum = region<int64_t>(plan, ws, R_SCAN);
+  cudaError_t e;
+  k_adapt_gather<<<blocks_for(n), kThreads, 0, st>>>(g, perm, pos, lambda, spos, slam, scr);
+  note_launch();
+  k_apply_wants<<<blocks_for(n + 1), kThreads, 0, st>>>(g, best, cand, clump, wants, keep);
+  note_launch();
+  k_apply_create<<<blocks_for(n + 1), kThreads, 0, st>>>(g, perm, spos, slam,
+                                                         region<int64_t>(plan, ws, R_OFF),
+                                                         region<int32_t>(plan, ws, R_IDX), cand, wants,
+                                                         void_factor, create);
+  note_launch();
+  if ((e = scan_exclusive_i32(keep, n + 1, bsum, st))) return launch_status(e);
+  if ((e = scan_exclusive_i32(create, n + 1, bsum, st))) return launch_status(e);
+  k_apply_write<<<blocks_for(n), kThreads, 0, st>>>(n, cap, pos, lambda, U, cand, grad, hess, keep, create,
+                                                    pos_out, lambda_out, U_out, origin, m_out,
+                                                    status_word);
   note_launch();
   return launch_status(cudaGetLastError());
 }
