@@ -729,6 +729,8 @@ __global__ void __launch_bounds__(128) k_adapt_scan(Grid g, const int32_t* __res
   const float v_out2 = static_cast<float>((dv + m) * (dv + m));
   const float c_in2 = static_cast<float>(dc > m ? (dc - m) * (dc - m) : 0.0);
   const float c_out2 = static_cast<float>((dc + m) * (dc + m));
+  const float r_in2 = static_cast<float>(r > m ? (r - m) * (r - m) : 0.0);
+  const float r_out2 = static_cast<float>((r + m) * (r + m));
   const float4 me = scr[s];
   const int me_caller = perm[s];
   const int64_t beg = off[s];
@@ -768,10 +770,29 @@ __global__ void __launch_bounds__(128) k_adapt_scan(Grid g, const int32_t* __res
       else if (e2 <= v_out2 && test_dist2(g, spos, n, s, t, ox, oy, oz) < dv2) covered = true;
     }
     if (covered) continue;
-    // uncovered: its clearance over the particle and its exact r_f set
+    // uncovered: its clearance, the smallest exact squared distance over the
+    // particle (o2) and its exact r_f set.  An FP32 pass finds the smallest
+    // screened distance over the entries proved (or, in the band, tested) to
+    // be in the r_f set; only entries within twice the screen error of it
+    // can hold the exact minimum, and only those are evaluated in FP64.
+    float min32 = static_cast<float>(o2);
+    for (int64_t e = beg; e < end; ++e) {
+      const int t = idx[e];
+      const float3 d = offset32(q, me, scr[t]);
+      const float dd = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+      if (dd > r_out2 || (dd >= r_in2 && !(dist2_exact(g, spos, n, s, t) < r2))) continue;
+      const float ex = d.x - fx, ey = d.y - fy, ez = d.z - fz;
+      const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+      min32 = e2 < min32 ? e2 : min32;
+    }
+    const double band = sqrt(static_cast<double>(min32)) + 2.0 * m;
+    const float band2 = static_cast<float>(band * band);
     double clear = o2;
     for (int64_t e = beg; e < end; ++e) {
       const int t = idx[e];
+      const float3 d = offset32(q, me, scr[t]);
+      const float ex = d.x - fx, ey = d.y - fy, ez = d.z - fz;
+      if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > band2) continue;
       if (!(dist2_exact(g, spos, n, s, t) < r2)) continue;  // a skin entry, not in N(i)
       const double e2 = test_dist2(g, spos, n, s, t, ox, oy, oz);
       clear = e2 < clear ? e2 : clear;
@@ -848,12 +869,12 @@ __global__ void k_apply_create(Grid g, const int32_t* __restrict__ perm, const d
       const int t = idx[e];
       const int j = perm[t];
       if (j >= i || !wants[j]) continue;
-      if (!(dist2_exact(g, spos, n, s, t) < r2)) continue;  // skin entry
-      double d2 = 0.0;
       double dd[3];
       for (int a = 0; a < 3; ++a) dd[a] = min_image64(__dsub_rn(cand[a * N + j], ci[a]), g.len[a], g.periodic[a]);
-      d2 = __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])), __dmul_rn(dd[2], dd[2]));
-      if (d2 < dv2) c = 0;
+      const double d2 =
+          __dadd_rn(__dadd_rn(__dmul_rn(dd[0], dd[0]), __dmul_rn(dd[1], dd[1])), __dmul_rn(dd[2], dd[2]));
+      if (!(d2 < dv2)) continue;
+      if (dist2_exact(g, spos, n, s, t) < r2) c = 0;  // not a skin entry
     }
   }
   create[i] = c;
