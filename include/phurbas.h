@@ -128,7 +128,8 @@ typedef struct {
   int32_t schedule;      /* fused fit: 0 = one CTA per tile in cell order; 1 = persistent CTAs
                             taking tiles from a queue in descending-cost order */
   int32_t ell_width;     /* neighbour search: list entries kept per particle in the
-                            single-pass scratch (0 = default 128; longer lists are
+                            single-pass scratch (0 = default: 128, or 256 when
+                            lambda_max > 1.26 lambda_min; longer lists are
                             searched again); 8 .. 1024 */
   /* filled by phb_plan_init */
   double cell[3];        /* cell edge per axis */

@@ -224,7 +224,12 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   if (p->stage_cap < 64 || p->stage_cap > 2048) return PHB_ERR_INVALID_ARG;
   p->ntiles = static_cast<int32_t>((p->n + p->tile - 1) / p->tile);
   if (p->schedule != 0 && p->schedule != 1) return PHB_ERR_INVALID_ARG;
-  if (p->ell_width == 0) p->ell_width = 128;
+  // default scratch row: ~51 neighbours at r_f = 2.3 lambda and uniform
+  // density; where lambda varies, a coarse particle next to a refined region
+  // gathers up to (lambda_max / lambda_min)^3 times more (275 at a 2x jump):
+  // rows too short send those lists through a second search in the
+  // compaction, so varying-lambda plans get 256 slots
+  if (p->ell_width == 0) p->ell_width = p->lambda_max > 1.26 * p->lambda_min ? 256 : 128;
   if (p->ell_width < 8 || p->ell_width > 1024) return PHB_ERR_INVALID_ARG;
   // FP32 screen: bound of |d32 - d| per component is 2^-24 (2X + 3L); two
   // components' worth of safety on top, times sqrt(3) for the norm.

@@ -121,3 +121,10 @@ def test_struct_sizes_match_the_binding(L):
     assert tuple(out) == (C.sizeof(_lib.Box), C.sizeof(_lib.Params), C.sizeof(_lib.Plan))
     assert C.sizeof(_lib.Params) == 72    # gamma, kind, precision, threshold, zeta, eta, frozen, laws
     assert L.phb_struct_sizes(None, 3) == 1 and L.phb_struct_sizes(out, 4) == 1
+
+
+def test_default_row_width_follows_the_lambda_range(L):
+    p = _plan()
+    assert L.phb_plan_init(C.byref(p)) == 0 and p.ell_width == 128
+    p = _plan(lmin=1 / 32, lmax=1 / 16)
+    assert L.phb_plan_init(C.byref(p)) == 0 and p.ell_width == 256
