@@ -143,9 +143,42 @@ __global__ void k_scan_add(TOut* out, int64_t count, const int64_t* bsum) {
   if (i < count) out[i] += static_cast<TOut>(bsum[i / kScanTile]);
 }
 
+// Whole scan in one block for short arrays (one launch instead of three):
+// 4096 consecutive elements per round, coalesced, with a running carry.  In
+// place is fine (each element is read before it is written).
+constexpr int64_t kScanSingleMax = 65536;
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(1024) k_scan_single(const TIn* in, TOut* out, int64_t count) {
+  __shared__ int64_t sw[33];
+  int64_t carry = 0;
+  for (int64_t c0 = 0; c0 < count; c0 += 4 * 1024) {
+    const int64_t b = c0 + 4 * threadIdx.x;
+    int64_t v[4];
+    int64_t run = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = b + k < count ? static_cast<int64_t>(in[b + k]) : 0;
+      run += v[k];
+    }
+    int64_t total;
+    int64_t pre = block_excl_scan<int64_t>(run, sw, total) + carry;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (b + k < count) out[b + k] = static_cast<TOut>(pre);
+      pre += v[k];
+    }
+    carry += total;
+  }
+}
+
 template <typename TIn, typename TOut>
 cudaError_t scan_impl(const TIn* in, TOut* out, int64_t count, int64_t* bsum, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
+  if (count <= kScanSingleMax) {
+    k_scan_single<TIn, TOut><<<1, 1024, 0, st>>>(in, out, count);
+    note_launch();
+    return cudaGetLastError();
+  }
   const int64_t nb = scan_blocks(count);
   k_scan_tile<TIn, TOut><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, count, bsum);
   note_launch();
