@@ -1039,9 +1039,11 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
                                         tplan, tslot, lself, tmap, misc + 1, status_word);
   trace_end(tr, st);
   note_launch();
-  k_tile_order<<<1, 1024, 0, st>>>(n, p->tile, p->ntiles, p->nbr_capacity, off,
-                                   region<int32_t>(p, ws, R_TORDER));
-  note_launch();
+  if (p->schedule == 1) {  // only the persistent fit reads the tile order
+    k_tile_order<<<1, 1024, 0, st>>>(n, p->tile, p->ntiles, p->nbr_capacity, off,
+                                     region<int32_t>(p, ws, R_TORDER));
+    note_launch();
+  }
   return cudaGetLastError();
 }
 
