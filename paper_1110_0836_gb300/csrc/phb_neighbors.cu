@@ -90,10 +90,13 @@ __global__ void k_gather_pos(Grid g, const int32_t* __restrict__ perm, const dou
 // the search; the counts also go to lcnt[k] (lcnt[total] = 0), whose
 // exclusive scan places the cells in linear order for the run search.
 __global__ void k_cell_lin(Grid g, const int32_t* __restrict__ cell_start, int2* __restrict__ clin,
-                           int32_t* __restrict__ lcnt) {
+                           int32_t* __restrict__ lcnt, int32_t* __restrict__ misc) {
   const int64_t total = static_cast<int64_t>(g.ncell[0]) * g.ncell[1] * g.ncell[2];
   const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k == total) lcnt[k] = 0;
+  if (k == total) {
+    lcnt[k] = 0;
+    misc[1] = 0;  // the compaction's count of unstaged tiles
+  }
   if (k >= total) return;
   const int cz = static_cast<int>(k % g.ncell[2]);
   const int cy = static_cast<int>((k / g.ncell[2]) % g.ncell[1]);
@@ -462,6 +465,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_search_ell(Grid g, const int2* 
                                                          int32_t* __restrict__ ell) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.n) return;
+  if (s == g.n - 1) ncnt[g.n] = 0;  // the offsets scan's sentinel
   const double r = list_radius(g, slam[s]);
   ncnt[s] = search_particle<kFillEll>(g, clin, lin, cellc, scr, spos, r, s, 0, 0,
                                       ell + static_cast<int64_t>(s) * g.ell);
@@ -995,8 +999,9 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   int2* clin = region<int2>(p, ws, R_CLIN);
   int32_t* misc = region<int32_t>(p, ws, R_MISC);
   cudaError_t e;
-  if ((e = cudaMemsetAsync(cell, 0, (p->nkeys + 1) * sizeof(int32_t), st))) return e;
-  if ((e = cudaMemsetAsync(cursor, 0, p->nkeys * sizeof(int32_t), st))) return e;
+  // cell counts and scatter cursors are adjacent regions: one clear
+  const size_t clear = p->ws_off[R_CURSOR] + p->nkeys * sizeof(int32_t) - p->ws_off[R_CELL];
+  if ((e = cudaMemsetAsync(cell, 0, clear, st))) return e;
   k_keys<<<blocks_for(n), kThreads, 0, st>>>(g, pos, lam, keys, cell, status_word);
   note_launch();
   if ((e = scan_exclusive_i32(cell, p->nkeys + 1, bsum, st))) return e;
@@ -1011,19 +1016,17 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   const int64_t ncells = int64_t(p->ncell[0]) * p->ncell[1] * p->ncell[2];
   int32_t* lstart = region<int32_t>(p, ws, R_LSTART);
   float4* lscr = region<float4>(p, ws, R_LSCR);
-  k_cell_lin<<<blocks_for(ncells + 1), kThreads, 0, st>>>(g, cell, clin, lstart);
+  k_cell_lin<<<blocks_for(ncells + 1), kThreads, 0, st>>>(g, cell, clin, lstart, misc);
   note_launch();
   if ((e = scan_exclusive_i32(lstart, ncells + 1, bsum, st))) return e;
   k_fill_lin<<<blocks_for(n), kThreads, 0, st>>>(g, cellc, clin, lstart, scr, lscr);
   note_launch();
   const Lin lin{lscr, lstart};
-  if ((e = cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), st))) return e;
   int32_t* ell = region<int32_t>(p, ws, R_ELL);
   int tr = trace_begin(4, st);
   k_search_ell<<<blocks_for(n), kThreads, 0, st>>>(g, clin, lin, cellc, scr, spos, slam, ncnt, ell);
   trace_end(tr, st);
   note_launch();
-  if ((e = cudaMemsetAsync(ncnt + n, 0, sizeof(int32_t), st))) return e;
   if ((e = scan_exclusive_i32_to_i64(ncnt, off, n + 1, bsum, st))) return e;
   const unsigned tiles = static_cast<unsigned>(p->ntiles);
   int2* tplan = region<int2>(p, ws, R_TPLAN);
