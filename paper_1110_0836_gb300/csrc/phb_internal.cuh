@@ -182,8 +182,10 @@ __host__ __device__ inline void unpack_cell(int32_t p, int& cx, int& cy, int& cz
 
 // Minimum-image FP64 offset, d - len * nearbyint(d / len), correctly rounded
 // at every step and without contraction (bit-identical to the definition).
+// Below a quarter box length the rounded quotient is 0 and d is returned as
+// it is, without the (slow) FP64 division.
 __device__ __forceinline__ double min_image64(double d, double len, int periodic) {
-  if (periodic) d = __dsub_rn(d, __dmul_rn(len, rint(__ddiv_rn(d, len))));
+  if (periodic && !(fabs(d) < 0.25 * len)) d = __dsub_rn(d, __dmul_rn(len, rint(__ddiv_rn(d, len))));
   return d;
 }
 

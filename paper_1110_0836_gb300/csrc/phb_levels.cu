@@ -50,7 +50,9 @@ __global__ void k_levels_limit(Grid g, const double* __restrict__ spos, const do
   const int64_t e1 = off[s + 1] < g.capacity ? off[s + 1] : g.capacity;
   for (int64_t e = off[s]; e < e1; ++e) {
     const int t = idx[e];
-    if (dist2_exact(g, spos, n, s, t) < r2) atomicMax(&L[t], send);
+    // only a neighbour below the level sent can change; the exact r_f test
+    // (FP64) decides the rest
+    if (send > L0[t] && dist2_exact(g, spos, n, s, t) < r2) atomicMax(&L[t], send);
   }
 }
 
