@@ -41,7 +41,7 @@ FLOP_PER_NEIGHBOUR = 2 * (80 + 7 * 19)
 FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
 # DRAM bytes (read + write) per launch of the fused fit, from ncu captures of the
 # kernel as it is built now: (workload, kernel, tile) -> bytes.  Absent = null.
-FIT_TRAFFIC = {("random_modes_64^3", "k_fit_mixed", 128): 68.63e6 + 3.02e6}
+FIT_TRAFFIC = {("random_modes_64^3", "k_fit_mixed", 128): 68.60e6 + 2.61e6}
 
 
 def parse():
