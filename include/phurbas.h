@@ -372,7 +372,7 @@ phb_status phb_rhs_adjoint_stored(const phb_plan* plan, const phb_params* params
  *     (32 MiB) that every GPU which loads the library holds until exit.  A
  *     plan whose build-and-fit workspace (everything before the
  *     predictor-corrector regions) is larger returns PHB_ERR_WORKSPACE and
- *     launches nothing; with constant lambda this allows roughly 33,000
+ *     launches nothing; with constant lambda this allows roughly 26,000
  *     particles.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
