@@ -239,24 +239,19 @@ __device__ void tile_plan(const Grid& g, int s0, int cnt, const int32_t* __restr
   }
   __syncthreads();
   if (ts.fallback) return;
-  // (first slot, count) of every marked cell, in box order
+  // (first slot, count) of every marked cell, in box order: a thread per box
+  // cell, so that the cell-table loads of a tile are issued in parallel
   const int d1 = ts.dim[1], d2 = ts.dim[2];
-  for (int w = tid; w < nw; w += T) {
-    unsigned bitsw = ta.bits[w];
-    int j = ta.wpre[w];
-    while (bitsw) {
-      const int b = __ffs(bitsw) - 1;
-      bitsw &= bitsw - 1;
-      const int k = (w << 5) + b;
-      const int bx = k / (d1 * d2), rr = k - bx * d1 * d2, by = rr / d2, bz = rr - by * d2;
-      const int cx = wrap_cell(g, 0, ts.lo[0] + bx);
-      const int cy = wrap_cell(g, 1, ts.lo[1] + by);
-      const int cz = wrap_cell(g, 2, ts.lo[2] + bz);
-      const int2 sc = clin[(static_cast<int64_t>(cx) * g.ncell[1] + cy) * g.ncell[2] + cz];
-      ta.cstart[j] = sc.x;
-      ta.base[j] = sc.y;
-      ++j;
-    }
+  for (int k = tid; k < ts.boxcells; k += T) {
+    if (!(ta.bits[k >> 5] >> (k & 31) & 1u)) continue;
+    const int j = marked_index(ta, k);
+    const int bx = k / (d1 * d2), rr = k - bx * d1 * d2, by = rr / d2, bz = rr - by * d2;
+    const int cx = wrap_cell(g, 0, ts.lo[0] + bx);
+    const int cy = wrap_cell(g, 1, ts.lo[1] + by);
+    const int cz = wrap_cell(g, 2, ts.lo[2] + bz);
+    const int2 sc = clin[(static_cast<int64_t>(cx) * g.ncell[1] + cy) * g.ncell[2] + cz];
+    ta.cstart[j] = sc.x;
+    ta.base[j] = sc.y;
   }
   __syncthreads();
   const int total = block_scan_excl<T>(ta.base, ncells, ta.warp_tmp);
