@@ -220,8 +220,10 @@ __device__ __forceinline__ bool plain_axis(const Grid& g, int a, int c, const Re
 
 enum SearchOut { kCount = 0, kFillCsr = 1, kFillEll = 2 };
 
-// Cell culling: the reach box of 2R+1 cells per axis is cut to the cells
-// that can hold a point within r of the particle.  With f the particle's
+// Cell culling for the cell-by-cell search of reaches that cover a whole
+// periodic axis (the run search does not cull): the reach box of 2R+1 cells
+// per axis is cut to the cells that can hold a point within r of the
+// particle.  With f the particle's
 // fractional position in its cell, the nearest point of the cell at offset i
 // is (i - f) cells away for i > 0, (-i - 1 + f) for i < 0 and 0 for i = 0.
 // Distances are taken with a margin of 1e-3 cells plus the screen margin, so
