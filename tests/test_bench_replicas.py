@@ -69,3 +69,23 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         workload, sample, steps, warmup, gpus = "C1", 64, 1, 1, 2
     assert bench.run_reference(A()) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_cpu():
+    """The reference arm (the FP64 oracle on the host cores) prints one JSON line
+    with the contract's keys; a small workload keeps it to a few seconds."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "C1", "--steps", "1", "--warmup", "1", "--sample", "256"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e",
+              "cpu_baseline"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert "workload" in line["config"]
