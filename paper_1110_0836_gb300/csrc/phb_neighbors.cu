@@ -453,7 +453,7 @@ __device__ __noinline__ void search_overflow(const Grid& g, const int2* __restri
 
 // Single pass, thread per particle (slot order): exact list lengths and the
 // first g.ell entries of every list.
-__global__ void __launch_bounds__(kThreads, 3) k_search_ell(Grid g, const int2* __restrict__ clin,
+__global__ void __launch_bounds__(kThreads, 4) k_search_ell(Grid g, const int2* __restrict__ clin,
                                                          Lin lin, const int32_t* __restrict__ cellc,
                                                          const float4* __restrict__ scr,
                                                          const double* __restrict__ spos,
