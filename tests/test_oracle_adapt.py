@@ -163,3 +163,19 @@ def test_apply_deletes_the_larger_index_of_a_pair(orc):
     p2, l2, U2, origin = orc.adapt_apply(box, pos, lam, U, nb, scan, *z)
     survivors = origin[origin < 3]
     assert survivors.tolist() == [0, 1]
+
+
+def test_void_scan_does_not_depend_on_particle_order(orc):
+    """Void counts, best test points and candidates belong to the particle,
+    not to its index (the clump mark, by design, does)."""
+    rng = np.random.default_rng(12)
+    pos = rng.random((3, 2500))
+    lam = np.full(2500, 0.045)
+    box = orc.make_box((0, 0, 0), (1, 1, 1), (1, 1, 1))
+    vc, best, cand, _ = _scan(orc, pos, lam, box)
+    p = rng.permutation(2500)
+    vc2, best2, cand2, _ = _scan(orc, np.ascontiguousarray(pos[:, p]), lam[p], box)
+    assert vc.any()
+    np.testing.assert_array_equal(vc2, vc[p])
+    np.testing.assert_array_equal(best2, best[p])
+    np.testing.assert_array_equal(cand2, cand[:, p])

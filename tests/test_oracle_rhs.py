@@ -216,3 +216,17 @@ def test_divb_diffusion_law(orc):
     exp = -eta * k * k * a * np.sin(k * pos[0, q])
     assert np.abs(out[4] - exp).max() < 1.5e-2 * np.abs(exp).max()
     assert not out[[0, 7]].any()
+
+
+def test_rhs_does_not_depend_on_particle_order(orc):
+    """Renumbering the particles permutes the right-hand side (the neighbour
+    order inside each fit changes, so equality holds to rounding)."""
+    w = workloads.random_modes(8, seed=13, amp=0.05)
+    box = orc.box_of(w)
+    out, st = orc.mhd_rhs(box, w.pos, w.lam, w.U, orc.neighbors(box, w.pos, w.lam), gamma=w.gamma)
+    p = np.random.default_rng(3).permutation(w.n)
+    pos, lam, U = np.ascontiguousarray(w.pos[:, p]), w.lam[p], np.ascontiguousarray(w.U[:, p])
+    out2, st2 = orc.mhd_rhs(box, pos, lam, U, orc.neighbors(box, pos, lam), gamma=w.gamma)
+    assert np.array_equal(st2, st[p])
+    scale = np.abs(out).max(axis=1, keepdims=True)
+    assert (np.abs(out2 - out[:, p]) <= 1e-12 * scale).all()
