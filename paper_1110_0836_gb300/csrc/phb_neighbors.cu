@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_search_ell(Grid g, const int2* 
 // index, each tile particle's own staged index - and map every list entry to
 // its staged index.
 template <int T>
-__global__ void __launch_bounds__(T, 768 / T) k_compact(Grid g, const int2* __restrict__ clin, Lin lin,
+__global__ void __launch_bounds__(T, 1024 / T) k_compact(Grid g, const int2* __restrict__ clin, Lin lin,
                                                const int32_t* __restrict__ cellc,
                                                const float4* __restrict__ scr,
                                                const double* __restrict__ spos,
