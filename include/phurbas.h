@@ -8,7 +8,12 @@
  *     B and sigma (Sec. 2; Acknowledgements: interpolating fits), its
  *     derivatives, and the ideal-MHD Lagrangian time derivatives with bulk
  *     viscosity and diffusive div B correction (Sec. 2; App. A);
- *   - the second-order predictor-corrector step (Sec. 2, Sec. 4.2);
+ *   - the second-order predictor-corrector step (Sec. 2, Sec. 4.2), with a
+ *     mask of fixed-value particles (Sec. 3);
+ *   - individual power-of-two time-step levels with the spatial limiter and
+ *     the right-hand side of an active subset (Sec. 2, Sec. 2.1);
+ *   - particle adaptivity: the void and clump scan and the deletion and
+ *     creation of particles (Sec. 2, Sec. 2.1);
  *   - a hand-written adjoint of the fit + right-hand side (not in the paper).
  *
  * Conventions for every entry point:
