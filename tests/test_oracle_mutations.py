@@ -113,3 +113,39 @@ def test_mutation_is_caught(name, tmp_path):
                 caught.append(i)
                 break
     assert caught, f"no pin caught mutation {name}"
+
+
+# Mistakes planted in the numpy part of the oracle (particle deletion and
+# creation): each must fail one of the adaptivity pins.
+APPLY_MUTATIONS = {
+    "apply_new_beyond_walls": ("inside &= (cand[ax] >= lo[ax]) & (cand[ax] < lo[ax] + length[ax])",
+                               "inside &= cand[ax] == cand[ax]"),
+    "apply_hessian_factor": ("Unew[f] += 0.5 * hess[", "Unew[f] += 1.0 * hess["),
+    "apply_no_gradient": ("Unew[f] += grad[f, a, parents] * o[a]", "Unew[f] += 0.0 * o[a]"),
+    "apply_keeps_clumps": ("keep = clump == 0", "keep = clump == clump"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(APPLY_MUTATIONS))
+def test_apply_mutation_is_caught(name, monkeypatch):
+    import inspect
+    import types
+    from oracle import oracle as omod
+    src = inspect.getsource(omod.adapt_apply)
+    old, new = APPLY_MUTATIONS[name]
+    assert src.count(old) == 1, f"mutation anchor not unique/found: {old!r}"
+    ns = dict(vars(omod))
+    exec(compile(src.replace(old, new), "<mutated adapt_apply>", "exec"), ns)
+    mutated = types.SimpleNamespace(**{k: getattr(oracle, k) for k in dir(oracle)
+                                       if not k.startswith("_")})
+    mutated.adapt_apply = ns["adapt_apply"]
+    caught = False
+    for pin in (tadapt.test_apply_fills_the_hole_with_exact_states,
+                tadapt.test_apply_deletes_the_larger_index_of_a_pair):
+        try:
+            pin(mutated)
+        except AssertionError:
+            caught = True
+            break
+    assert caught, f"no pin caught mutation {name}"
