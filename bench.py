@@ -32,16 +32,29 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-RHS evals/s (MLS fit + MHD RHS), FP32-mixed vs FP64 on 1 GB300, err vs oracle"
 UNIT = "particle-RHS/s"
 WORKLOAD = "C2"
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-# algorithmic flops of the fused RHS fit:
-#   per neighbour inside r_f: 80 moment FMAs + 7 fields x 19 RHS FMAs = 213 FMA
-#   per particle: Cholesky 1140 FMA + 7 forward solves 7x171 + 7 partial back
-#   solves 7x36 FMA, and ~100 flop of right-hand side
-FLOP_PER_NEIGHBOUR = 2 * (80 + 7 * 19)
-FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
-# DRAM bytes (read + write) per launch of the fused fit, from ncu captures of the
-# kernel as it is built now: (workload, kernel, tile) -> bytes.  Absent = null.
-FIT_TRAFFIC = {("random_modes_64^3", "k_fit_mixed", 128): 68.60e6 + 2.61e6}
+FP32_LANES = 128   # FP32 FMA lanes per SM (4 partitions x 32)
+# Algorithmic work of one particle-RHS, the method's count (Sec. 2 fit + RHS),
+# per neighbour inside r_f and per particle:
+#   per neighbour: 80 moment FMAs + 8 fields x 19 right-hand-side FMAs = 464
+#   flop, plus ~110 flop of offsets, hi/lo centring, weight and the degree 2..6
+#   monomial products = 575 flop;
+#   per particle: Jacobi scaling ~0.4 k, 19x19 Cholesky ~2.3 k, 8 full
+#   forward + back solves ~5.8 k, right-hand side ~0.2 k = 8.7 kflop;
+# about 38 kflop at 51 neighbours.
+FLOP_PER_NEIGHBOUR = 575
+FLOP_PER_PARTICLE = 8700
+# The fused kernel's own arithmetic, printed beside it: 7 fitted fields (the
+# right-hand side needs no density fit), 213 FMA per neighbour; per particle
+# Cholesky 1140 FMA + 7 forward solves (171 FMA) + 7 partial back solves (36
+# FMA) + ~100 flop; the corrected step of refined tiles adds ~2x this.
+KERNEL_FLOP_PER_NEIGHBOUR = 2 * (80 + 7 * 19)
+KERNEL_FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
+# DRAM bytes (read + write) per launch of the fused fit from one-kernel ncu
+# captures of the kernel as it is built now (profiles/fit_mixed_traffic.md):
+# workload name -> (bytes per launch, how).  Workloads too large to capture
+# under the size rule are captured on a smaller set of the same recipe and
+# scaled by the particles processed.  Absent = null.
+FIT_TRAFFIC = {}
 
 
 def parse():
@@ -191,11 +204,25 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
-def fma_peak_tflops(L, dev, precision: int) -> float:
-    """Best of 5 launches of the library's FMA probe (precision 1 = FP32, 0 = FP64)."""
+def sm_max_mhz(index: int, sampled: dict | None) -> float:
+    """Maximum SM clock of the GPU: from the clock samples of the timed region,
+    else one nvidia-smi query, else the GB300's documented 2070 MHz."""
+    if sampled and sampled.get("sm_max_mhz", 0) > 0:
+        return float(sampled["sm_max_mhz"])
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={index}", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=20).stdout.strip()
+        return float(out.splitlines()[0])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return 2070.0
+
+
+def fma_peak_tflops(L, dev, precision: int, sm_count: int) -> float:
+    """Best of 6 launches of the library's FMA probe (precision 1 = FP32, 0 = FP64)."""
     import ctypes as C
     import torch
-    blocks = SM_COUNT * 8
+    blocks = sm_count * 8
     iters = 20000 if precision == 1 else 1000
     sink = torch.empty(blocks * 256, dtype=torch.float32 if precision == 1 else torch.float64,
                        device=dev)
@@ -462,20 +489,29 @@ def run_ours(args):
     value = world * 2 * n / (step_ms_max * 1e-3)
 
     fit_avg = float(np.mean(fit_ms)) if fit_ms else float("nan")
+    sm_count = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    mhz = sm_max_mhz(local, clocks)
     flops = FLOP_PER_NEIGHBOUR * nbr_inside + FLOP_PER_PARTICLE * n
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    kflops = KERNEL_FLOP_PER_NEIGHBOUR * nbr_inside + KERNEL_FLOP_PER_PARTICLE * n
+    peak = sm_count * FP32_LANES * 2 * mhz * 1e6 / 1e12
     achieved = flops / (fit_avg * 1e-3) / 1e12
     kname = "k_fit_mixed_persistent" if plan.c.schedule == 1 else "k_fit_mixed"
-    traffic = FIT_TRAFFIC.get((w.name, kname, int(plan.c.tile)))
+    tr = FIT_TRAFFIC.get(w.name) if (kname == "k_fit_mixed" and int(plan.c.tile) == 128) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
+                "frac": achieved / peak, "traffic": None if tr is None else tr[0],
                 "traffic_unit": "DRAM bytes read + written per launch (ncu, profiles/)",
+                "traffic_how": None if tr is None else tr[1],
                 "kernel": f"{kname}<kRHS, {int(plan.c.tile)}> (fused FP32 MLS fit + MHD RHS)",
                 "launch_ms": fit_avg, "launches": len(fit_ms),
                 "timed_on": "eager pass over the timed steps (CUDA events on the launching stream)"
                             if graph is not None else "the timed steps (CUDA events on the launching stream)",
                 "algorithmic_flop_per_launch": flops,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts and max clock)"}
+                "flop_count": f"{FLOP_PER_NEIGHBOUR} flop per neighbour inside r_f + "
+                              f"{FLOP_PER_PARTICLE} per particle (the method's count)",
+                "kernel_flop_per_launch": kflops,
+                "kernel_count_achieved": kflops / (fit_avg * 1e-3) / 1e12,
+                "peak_basis": f"{sm_count} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz "
+                              "(SM count from the device, max SM clock from nvidia-smi)"}
     del graph
 
     # ---------------- FP64 path, same step (fewer steps: ~25x slower)
@@ -552,8 +588,8 @@ def run_ours(args):
         Ub2 = torch.empty_like(Ub)
         xb2 = torch.empty_like(xb)
         st_ms, _ = timed(lambda: phb.rhs_adjoint_stored(plan, fp64, pos0, lam, U0, gb, rec, Ub2, xb2))
-        ws_adj = (int(plan.c.ws_off[_lib.WS_ADJ_SELF]) + 11 * 8 * n
-                  - int(plan.c.ws_off[_lib.WS_ADJ_EDGE]))   # adjoint regions of the workspace
+        b_adj, e_adj = _lib.workspace_part(plan.c, _lib.PART_ADJOINT)
+        ws_adj = e_adj - b_adj                               # adjoint part of the workspace
         adjoint = {"ms": adj_ms, "value": n / (adj_ms * 1e-3), "unit": "particle-gradients/s",
                    "precision": "fp64", "factorisations": "recomputed",
                    "stored": {"record_ms": rec_ms, "adjoint_ms": st_ms,
@@ -628,8 +664,9 @@ def run_ours(args):
                    "each step with a synchronize on both sides"}
 
     # ---------------- measured FMA peaks (project probe) and the FP64 path's roofline
-    p32 = fma_peak_tflops(L, dev, 1)
-    p64 = fma_peak_tflops(L, dev, 0)
+    p32 = fma_peak_tflops(L, dev, 1, sm_count)
+    p64 = fma_peak_tflops(L, dev, 0, sm_count)
+    roofline["measured_fma_peak"] = p32
     roofline["frac_of_measured_fma"] = achieved / p32
     ach64 = flops / (rhs64_ms * 1e-3) / 1e12
     roofline_fp64 = {"bound": "alu", "achieved": ach64, "peak": 1.25, "unit": "TFLOP/s",
@@ -637,7 +674,8 @@ def run_ours(args):
                      "kernel": "k_fit_fp64<kRHS> (fused FP64 MLS fit + MHD RHS), whole RHS call",
                      "peak_basis": "nominal GB300 FP64 rate"}
     measured = {"fp32_fma_tflops": p32, "fp64_fma_tflops": p64,
-                "how": "phb_fma_peak: 1216 CTAs x 256 threads x 16 independent FMA chains, best of 6"}
+                "how": f"phb_fma_peak: {sm_count * 8} CTAs x 256 threads x 16 independent FMA "
+                       "chains, best of 6"}
 
     # ---------------- CPU oracle and accuracy (rank 0, one GPU)
     cpu = None

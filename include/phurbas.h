@@ -113,6 +113,21 @@ typedef struct {
   double c_zeta_l;
   double c_zeta_a;
   double c_eta;
+  /* FP32_MIXED only: one corrected semi-normal-equations step (Bjorck) after
+   * the FP32 solve: residuals r_j = (U_j - U_i) - p(q_j).c recomputed from the
+   * neighbour data, P^T W r accumulated and solved with the same factor, so
+   * the coefficient error follows cond(A) = cond(M_s)^(1/2) rather than
+   * cond(M_s).  It costs about one more fit.  The decision is per tile of
+   * particles: refine = 0 refines a tile when any of its fits has a
+   * conditioning estimate (as for cond_threshold) above refine_kappa (0 =
+   * default 500; the fits of a jittered lattice stay below ~330, about 40% of
+   * the fits of a density-sampled set lie above 500, and there even
+   * well-conditioned fits leak the large linear coefficients of a steep
+   * front into the quadratic ones); refine = 1 refines every tile; refine =
+   * -1 never refines. */
+  int32_t refine;
+  int32_t pad_;
+  double refine_kappa;
 } phb_params;
 
 /* A plan fixes the particle count, box, radius law and the cell grid.  The
@@ -158,6 +173,18 @@ phb_status phb_plan_init(phb_plan* plan);
 
 /* Workspace bytes needed by `op` under `plan` (0 for an invalid plan). */
 size_t phb_workspace_size(const phb_plan* plan, int32_t op);
+
+/* Parts of the workspace, for callers that size or inspect it by use. */
+#define PHB_PART_COMMON 0  /* neighbour lists, fits, right-hand sides, levels, adaptivity:
+                              every call other than the two below needs only this part */
+#define PHB_PART_STEP 1    /* phb_pc_step's state and right-hand sides (after the common part) */
+#define PHB_PART_ADJOINT 2 /* phb_rhs_adjoint's scratch (after the common part; overlays the
+                              step part, the two are never used at the same time) */
+
+/* Byte range [*begin, *end) of workspace part `part` under `plan`; a call that
+ * uses the part needs ws_bytes >= *end.  Host only.  Returns 0, or 1 for an
+ * invalid plan, part or NULL output. */
+int phb_workspace_part(const phb_plan* plan, int32_t part, size_t* begin, size_t* end);
 
 /* Text for a phb_status code (static storage). */
 const char* phb_status_string(int32_t status);

@@ -44,7 +44,9 @@ int phb_trace_start(int32_t capacity);
  * (synchronising on `stream`): out[0] = fits routed to FP64 by the last fused
  * fit, out[1] = tiles of the last neighbour build that read neighbours from
  * global memory (neighbourhood larger than the staging capacity), out[2] =
- * such tiles in the last fused fit, out[3] = number of tiles.  count <= 4.
+ * such tiles in the last fused fit, out[3] = number of tiles, out[4] = tiles
+ * of the last FP32-mixed fused fit that took the corrected
+ * semi-normal-equations step (phb_params.refine).  count <= 5.
  * Returns 0, 1 for invalid arguments, 3 on a CUDA error. */
 int phb_workspace_stats(const phb_plan* plan, const void* ws, int32_t* out, int32_t count,
                         phb_stream_t stream);

@@ -17,11 +17,8 @@ FLAG_CAPACITY, FLAG_SKIN, FLAG_FIT_SINGULAR, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_
     0x01, 0x02, 0x04, 0x08, 0x10, 0x20)
 FLAG_BAD_INDEX = 0x40
 PHB_FP64, PHB_FP32_MIXED = 0, 1
-# ws_off index where the workspace part shared by neighbour build, fit and RHS ends
-# (position of R_END_COMMON in the library's region enumeration)
-WS_END_COMMON = 38
-# first and last adjoint regions (R_ADJ_EDGE, R_ADJ_SELF; the latter holds 11 doubles per particle)
-WS_ADJ_EDGE, WS_ADJ_SELF = 32, 37
+# workspace parts (phb_workspace_part)
+PART_COMMON, PART_STEP, PART_ADJOINT = 0, 1, 2
 
 EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_check",
            "phb_build_neighbors", "phb_export_neighbors", "phb_neighbor_total", "phb_mls_derivs",
@@ -29,7 +26,8 @@ EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_chec
            "phb_trace_start", "phb_trace_stop", "phb_trace_read", "phb_workspace_stats", "phb_mhd_rhs_noalloc",
            "phb_noalloc_scratch_bytes", "phb_adjoint_record_bytes", "phb_adjoint_record",
            "phb_rhs_adjoint_stored", "phb_mhd_rhs_active", "phb_timestep_levels",
-           "phb_struct_sizes", "phb_reorder", "phb_adapt_scan", "phb_adapt_apply"]
+           "phb_struct_sizes", "phb_reorder", "phb_adapt_scan", "phb_adapt_apply",
+           "phb_workspace_part"]
 
 
 class Box(C.Structure):
@@ -41,7 +39,8 @@ class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("weight_kind", C.c_int32), ("precision", C.c_int32),
                 ("cond_threshold", C.c_double), ("zeta", C.c_void_p), ("eta", C.c_void_p),
                 ("frozen", C.c_void_p), ("c_zeta_l", C.c_double), ("c_zeta_a", C.c_double),
-                ("c_eta", C.c_double)]
+                ("c_eta", C.c_double), ("refine", C.c_int32), ("pad_", C.c_int32),
+                ("refine_kappa", C.c_double)]
 
 
 class Plan(C.Structure):
@@ -129,6 +128,8 @@ def lib(path: str | None = None) -> C.CDLL:
                                   C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp, _vp]
     L.phb_adapt_apply.restype = C.c_int
     L.phb_reorder.restype = C.c_int
+    L.phb_workspace_part.argtypes = [P(Plan), C.c_int32, _vp, _vp]
+    L.phb_workspace_part.restype = C.c_int
     L.phb_struct_sizes.argtypes = [_vp, C.c_int32]
     L.phb_struct_sizes.restype = C.c_int
     sizes = (C.c_int64 * 3)()
@@ -142,6 +143,14 @@ def lib(path: str | None = None) -> C.CDLL:
     if path is None:
         _LIB = L
     return L
+
+
+def workspace_part(plan: Plan, part: int) -> tuple[int, int]:
+    """Byte range (begin, end) of a workspace part of an initialised plan."""
+    b, e = C.c_size_t(0), C.c_size_t(0)
+    if lib().phb_workspace_part(C.byref(plan), int(part), C.byref(b), C.byref(e)) != 0:
+        raise ValueError(f"invalid plan or workspace part {part}")
+    return int(b.value), int(e.value)
 
 
 def status_string(code: int) -> str:

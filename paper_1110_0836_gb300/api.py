@@ -50,6 +50,11 @@ class Params:
     c_zeta_l: float = 0.0
     c_zeta_a: float = 0.0
     c_eta: float = 0.0
+    # FP32-mixed: one corrected semi-normal-equations step per tile: "auto"
+    # (tiles with a fit whose conditioning estimate exceeds refine_kappa),
+    # "on" (every tile) or "off"
+    refine: str = "auto"
+    refine_kappa: float = 500.0
 
     def c(self) -> _lib.Params:
         p = _lib.Params()
@@ -66,6 +71,11 @@ class Params:
             raise ValueError("frozen must be a contiguous bool or uint8 tensor")
         p.frozen = None if self.frozen is None else self.frozen.data_ptr()
         p.c_zeta_l, p.c_zeta_a, p.c_eta = float(self.c_zeta_l), float(self.c_zeta_a), float(self.c_eta)
+        modes = {"auto": 0, "on": 1, "off": -1}
+        if self.refine not in modes:
+            raise ValueError(f"refine must be 'auto', 'on' or 'off', not {self.refine!r}")
+        p.refine = modes[self.refine]
+        p.refine_kappa = float(self.refine_kappa)
         return p
 
 
@@ -143,11 +153,12 @@ class Plan:
 
     def stats(self) -> dict:
         """Diagnostic counters of the last build / fused fit (synchronises)."""
-        out = (C.c_int32 * 4)()
-        check(_lib.lib().phb_workspace_stats(C.byref(self.c), _ptr(self.ws), out, 4, _stream()),
+        out = (C.c_int32 * 5)()
+        check(_lib.lib().phb_workspace_stats(C.byref(self.c), _ptr(self.ws), out, 5, _stream()),
               "phb_workspace_stats")
         return {"routed_to_fp64": int(out[0]), "build_fallback_tiles": int(out[1]),
-                "fit_fallback_tiles": int(out[2]), "tiles": int(out[3])}
+                "fit_fallback_tiles": int(out[2]), "tiles": int(out[3]),
+                "refined_tiles": int(out[4])}
 
     def neighbor_total(self) -> int:
         return int(_lib.lib().phb_neighbor_total(C.byref(self.c), _ptr(self.ws), _stream()))

@@ -13,11 +13,13 @@
 //               wbar_j   = sum_a mbar_a q_j^a + sum_f dU_fj (p_j . bbar_f)
 //               qbar_j   = w_j grad_q[ sum_a mbar_a q^a + sum_f dU_fj p(q) . bbar_f ]
 //               dbar_j   = qbar_j / lambda_i + wbar_j dw/dd,
-//             contributions to U_j and x_j written per list entry and those
-//             to U_i and x_i kept by the particle.
-// A second kernel gathers every particle's own terms plus the entries that
-// name it through a reverse neighbour list sorted by entry id, so the result
-// does not depend on thread scheduling.  By default the factorisation is
+//             whose negatives are particle i's own terms (U_i, x_i).
+// The first kernel keeps, per particle, only its adjoint seeds bbar_f and
+// mbar (213 doubles) and its own terms; a second kernel gathers, for every
+// particle j, the contributions of each i that lists j - through a reverse
+// neighbour list in ascending order of i, recomputing q, w, p(q) and dw/dd
+// of the entry from the positions - so the result does not depend on thread
+// scheduling and no per-entry buffer is needed.  By default the factorisation is
 // recomputed here (nothing is stored by the forward call); the stored variant
 // records, per particle, the Cholesky factor, its Jacobi scaling and the
 // fitted coefficients once (kRecord) and the adjoint then starts from that
@@ -33,6 +35,10 @@ constexpr int kT = 64;
 constexpr int kThreads = 256;
 constexpr int kNFit = 7;                 // fitted fields: U indices 1..7 (V, B, sigma)
 constexpr int kSm = kNM + kNFit * kNB;   // 213 doubles per thread (the 190-entry M overlays it)
+// per-particle scratch record (contiguous per particle, read by the gather):
+// bbar_f (7 x 19), then the coefficients c_f (7 x 19) of the recomputing
+// form, whose first 80 words take mbar once c_f is no longer needed
+constexpr int kScrBbar = 0, kScrC = kNFit * kNB, kScrMbar = kScrC, kScr = 2 * kNFit * kNB;
 static_assert(kSm >= kNT, "shared region must hold the normal matrix");
 // record of one particle's forward fit, [k][n] layout: factor (190), Jacobi
 // scaling invd (19), coefficients c_f (7 x 19), then 1 = singular / 0 = regular
@@ -67,8 +73,7 @@ struct AdjArgs {
   const double* zeta;    // caller order or null
   const double* eta;
   double c_zeta_l, c_zeta_a, c_eta;  // coefficient laws (phb_params), 0 = off
-  double* scr;           // [266][n]: c_f (7 x 19) then bbar_f (7 x 19)
-  double* edge;          // [capacity][10]
+  double* scr;           // [n][kScr] slot order: bbar_f, then c_f / mbar
   double* self;          // [11][n] slot order
   double* rec;           // [kRecWords][n] slot order (stored variant) or null
   int32_t* status_word;
@@ -183,6 +188,55 @@ __device__ void rhs_adjoint_point(const double (&u)[8], const MhdDerivs<double>&
   gb[3 + 0][1] -= Jb[2];
 }
 
+// Adjoint contribution of one list entry (particle i at xs with fields u,
+// neighbour t) to the neighbour: ub[f] to U_t (fitted fields 1..7) and xb to
+// x_t, from i's seeds bbar_f (stride bs) and mbar (stride ms).  The entry's
+// offset, weight, monomials and dw/dd are recomputed from the positions.
+// Returns false (nothing written) for an entry beyond r_f,i (skin).
+__device__ __forceinline__ bool entry_adjoint(const AdjArgs& a, int t, double xs, double ys,
+                                              double zs, const double (&u)[8], double inv_rf2,
+                                              double inv_l, const double (&len)[3],
+                                              const double (&ilen)[3], const double* bb, int bs,
+                                              const double* mbar, int ms, double (&ub)[kNFit],
+                                              double (&xb)[3]) {
+  const int64_t N = a.n;
+  const Geo q = geometry(a, t, xs, ys, zs, len, ilen, inv_rf2);
+  if (!(q.s2 < 1.0)) return false;
+  const double sw = 1.0 - q.s2;
+  const double wt = a.weight_kind == 1 ? 1.0 : sw * sw;
+  double mono[kNMono];
+  mls_monos6(q.dx * inv_l, q.dy * inv_l, q.dz * inv_l, mono);
+  double p[kNB];
+  mls_basis_from_monos(mono, p);
+  double Bt[kNB];
+  for (int k = 0; k < kNB; ++k) Bt[k] = 0.0;
+  for (int fi = 0; fi < kNFit; ++fi) {
+    const double du = a.sU[(fi + 1) * N + t] - u[fi + 1];
+    double pb = 0.0;
+    for (int k = 0; k < kNB; ++k) {
+      const double bk = bb[(fi * kNB + k) * bs];
+      pb = fma(p[k], bk, pb);
+      Bt[k] = fma(du, bk, Bt[k]);
+    }
+    ub[fi] = wt * pb;
+  }
+  struct Strided {
+    const double* p;
+    int st;
+    __device__ __forceinline__ double operator[](int k) const { return p[k * st]; }
+  };
+  double V, Vx, Vy, Vz, P, Px, Py, Pz;
+  mls_eval_basis_poly(mono, Bt, V, Vx, Vy, Vz);
+  mls_eval_moment_poly(mono, Strided{mbar, ms}, P, Px, Py, Pz);
+  const double wbar = P + V;
+  const double dwd_c = a.weight_kind == 1 ? 0.0 : -4.0 * inv_rf2;
+  const double dw = wbar * dwd_c * sw;  // d w / d d = -4 (1 - s^2) d / r_f^2
+  xb[0] = wt * (Px + Vx) * inv_l + dw * q.dx;
+  xb[1] = wt * (Py + Vy) * inv_l + dw * q.dy;
+  xb[2] = wt * (Pz + Vz) * inv_l + dw * q.dz;
+  return true;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kT, 1) k_adjoint(const AdjArgs a) {
   extern __shared__ double sm[];
@@ -193,8 +247,10 @@ __global__ void __launch_bounds__(kT, 1) k_adjoint(const AdjArgs a) {
   const SCol MB{my};                // mbar [80]
   const int64_t N = a.n;
   // c_f, f = 0..6: [f * 19 + k] (in the record for the stored variant)
-  const GCol cf{MODE == kRecompute ? a.scr + s : a.rec + kRecCoef * N + s, N};
-  const GCol bbar{a.scr + s + 133 * N, N};        // bbar_f
+  double* my_scr = a.scr + static_cast<int64_t>(s) * kScr;
+  const GCol cf{MODE == kRecompute ? my_scr + kScrC : a.rec + kRecCoef * N + s,
+                MODE == kRecompute ? 1 : N};
+  const GCol bbar{my_scr + kScrBbar, 1};          // bbar_f
   double len[3], ilen[3];
   for (int c = 0; c < 3; ++c) {
     len[c] = a.g.len[c];
@@ -260,9 +316,10 @@ __global__ void __launch_bounds__(kT, 1) k_adjoint(const AdjArgs a) {
   }
   double selfu[8], selfx[3] = {0.0, 0.0, 0.0};
   if (singular) {
-    // the forward right-hand side is zero and does not depend on the inputs
-    for (int64_t e = beg; e < end; ++e)
-      for (int k = 0; k < kEdgeAdj; ++k) a.edge[e * kEdgeAdj + k] = 0.0;
+    // the forward right-hand side is zero and does not depend on the inputs:
+    // no own terms and zero seeds for the gather
+    for (int k = 0; k < kNFit * kNB; ++k) my_scr[kScrBbar + k] = 0.0;
+    for (int k = 0; k < kNM; ++k) my_scr[kScrMbar + k] = 0.0;
     for (int k = 0; k < 11; ++k) a.self[k * N + s] = 0.0;
     raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
     return;
@@ -330,6 +387,7 @@ __global__ void __launch_bounds__(kT, 1) k_adjoint(const AdjArgs a) {
     }
   }
   // ---- mbar = fold of -sum_f bbar_f c_f^T onto the moments; stage mbar, bbar
+  // in shared memory and keep mbar in the scratch record (over c_f) for the gather
   {
     double mb[kNM];
 #pragma unroll
@@ -343,81 +401,55 @@ __global__ void __launch_bounds__(kT, 1) k_adjoint(const AdjArgs a) {
       mls_accum_mbar(bb, cc, mb);
     }
 #pragma unroll
-    for (int k = 0; k < kNM; ++k) MB[k] = mb[k];
+    for (int k = 0; k < kNM; ++k) {
+      MB[k] = mb[k];
+      my_scr[kScrMbar + k] = mb[k];
+    }
     for (int k = 0; k < kNFit * kNB; ++k) M[kNM + k] = bbar[k];  // M is dead now
   }
-  // ---- backward pass over the neighbours
-  const double dwd_c = a.weight_kind == 1 ? 0.0 : -4.0 * inv_rf2;
+  // ---- backward pass over the neighbours: particle i's own terms
   for (int64_t e = beg; e < end; ++e) {
     const int t = a.idx[e];
-    const Geo q = geometry(a, t, xs, ys, zs, len, ilen, inv_rf2);
-    double* ed = a.edge + e * kEdgeAdj;
-    if (!(q.s2 < 1.0)) {
-      for (int k = 0; k < kEdgeAdj; ++k) ed[k] = 0.0;
+    double ub[kNFit], xb[3];
+    if (!entry_adjoint(a, t, xs, ys, zs, u, inv_rf2, inv_l, len, ilen, M.p + kNM * kT, kT,
+                       MB.p, kT, ub, xb))
       continue;
-    }
-    const double sw = 1.0 - q.s2;
-    const double wt = a.weight_kind == 1 ? 1.0 : sw * sw;
-    double mono[kNMono];
-    mls_monos6(q.dx * inv_l, q.dy * inv_l, q.dz * inv_l, mono);
-    double p[kNB];
-    mls_basis_from_monos(mono, p);
-    double Bt[kNB];
-    for (int k = 0; k < kNB; ++k) Bt[k] = 0.0;
-    for (int fi = 0; fi < kNFit; ++fi) {
-      const double du = a.sU[(fi + 1) * N + t] - u[fi + 1];
-      double pb = 0.0;
-      for (int k = 0; k < kNB; ++k) {
-        const double bk = M[kNM + fi * kNB + k];
-        pb = fma(p[k], bk, pb);
-        Bt[k] = fma(du, bk, Bt[k]);
-      }
-      const double dub = wt * pb;
-      ed[fi] = dub;
-      selfu[fi + 1] -= dub;
-    }
-    double V, Vx, Vy, Vz, P, Px, Py, Pz;
-    mls_eval_basis_poly(mono, Bt, V, Vx, Vy, Vz);
-    mls_eval_moment_poly(mono, MB, P, Px, Py, Pz);
-    const double wbar = P + V;
-    const double dw = wbar * dwd_c * sw;  // d w / d d = -4 (1 - s^2) d / r_f^2
-    const double db[3] = {wt * (Px + Vx) * inv_l + dw * q.dx, wt * (Py + Vy) * inv_l + dw * q.dy,
-                          wt * (Pz + Vz) * inv_l + dw * q.dz};
-    for (int c = 0; c < 3; ++c) {
-      ed[kNFit + c] = db[c];
-      selfx[c] -= db[c];
-    }
+    for (int fi = 0; fi < kNFit; ++fi) selfu[fi + 1] -= ub[fi];
+    for (int c = 0; c < 3; ++c) selfx[c] -= xb[c];
   }
   for (int k = 0; k < 8; ++k) a.self[k * N + s] = selfu[k];
   for (int c = 0; c < 3; ++c) a.self[(8 + c) * N + s] = selfx[c];
 }
 
-// ---- reverse neighbour lists (entry ids grouped by the neighbour they name)
-__global__ void k_rev_count(int64_t cap, const int64_t* __restrict__ off, int n,
+// ---- reverse neighbour lists: for every particle t, the particles i whose
+// list names t, in ascending order of i
+__global__ void k_rev_count(int n, int64_t cap, const int64_t* __restrict__ off,
                             const int32_t* __restrict__ idx, int32_t* __restrict__ rcnt) {
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t total = off[n] < cap ? off[n] : cap;
-  if (e >= total) return;
-  atomicAdd(&rcnt[idx[e]], 1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t end = off[i + 1] < cap ? off[i + 1] : cap;
+  for (int64_t e = off[i]; e < end; ++e) atomicAdd(&rcnt[idx[e]], 1);
 }
 
-__global__ void k_rev_fill(int64_t cap, const int64_t* __restrict__ off, int n,
+__global__ void k_rev_fill(int n, int64_t cap, const int64_t* __restrict__ off,
                            const int32_t* __restrict__ idx, const int64_t* __restrict__ roff,
-                           int32_t* __restrict__ rcur, int64_t* __restrict__ ridx) {
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t total = off[n] < cap ? off[n] : cap;
-  if (e >= total) return;
-  const int t = idx[e];
-  ridx[roff[t] + atomicAdd(&rcur[t], 1)] = e;
+                           int32_t* __restrict__ rcur, int32_t* __restrict__ rsrc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t end = off[i + 1] < cap ? off[i + 1] : cap;
+  for (int64_t e = off[i]; e < end; ++e) {
+    const int t = idx[e];
+    rsrc[roff[t] + atomicAdd(&rcur[t], 1)] = i;
+  }
 }
 
-__global__ void k_rev_sort(int n, const int64_t* __restrict__ roff, int64_t* __restrict__ ridx) {
+__global__ void k_rev_sort(int n, const int64_t* __restrict__ roff, int32_t* __restrict__ rsrc) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  int64_t* v = ridx + roff[t];
+  int32_t* v = rsrc + roff[t];
   const int m = static_cast<int>(roff[t + 1] - roff[t]);
   for (int i = 1; i < m; ++i) {
-    const int64_t x = v[i];
+    const int32_t x = v[i];
     int j = i - 1;
     while (j >= 0 && v[j] > x) {
       v[j + 1] = v[j];
@@ -427,22 +459,37 @@ __global__ void k_rev_sort(int n, const int64_t* __restrict__ roff, int64_t* __r
   }
 }
 
-// Own terms plus every entry naming the particle, in entry order; caller order out.
-__global__ void k_adj_gather(int n, const int32_t* __restrict__ perm, const double* __restrict__ self,
-                             const double* __restrict__ edge, const int64_t* __restrict__ roff,
-                             const int64_t* __restrict__ ridx, double* __restrict__ Ubar,
-                             double* __restrict__ xbar) {
+// Own terms plus the contribution of every particle i whose list names t,
+// recomputed from i's seeds in ascending order of i; caller order out.
+__global__ void __launch_bounds__(128) k_adj_gather(const AdjArgs a, const int64_t* __restrict__ roff,
+                                                    const int32_t* __restrict__ rsrc,
+                                                    double* __restrict__ Ubar,
+                                                    double* __restrict__ xbar) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const int64_t N = n;
-  double acc[11];
-  for (int k = 0; k < 11; ++k) acc[k] = self[k * N + t];
-  for (int64_t r = roff[t]; r < roff[t + 1]; ++r) {
-    const double* ed = edge + ridx[r] * kEdgeAdj;
-    for (int k = 0; k < kNFit; ++k) acc[1 + k] += ed[k];
-    for (int c = 0; c < 3; ++c) acc[8 + c] += ed[kNFit + c];
+  if (t >= a.n) return;
+  const int64_t N = a.n;
+  double len[3], ilen[3];
+  for (int c = 0; c < 3; ++c) {
+    len[c] = a.g.len[c];
+    ilen[c] = a.g.periodic[c] ? 1.0 / a.g.len[c] : 0.0;
   }
-  const int i = perm[t];
+  double acc[11];
+  for (int k = 0; k < 11; ++k) acc[k] = a.self[k * N + t];
+  for (int64_t r = roff[t]; r < roff[t + 1]; ++r) {
+    const int i = rsrc[r];
+    double u[8];
+    for (int f = 0; f < 8; ++f) u[f] = a.sU[f * N + i];
+    const double lam = a.slam[i];
+    const double rf = a.g.rf_factor * lam;
+    const double* bb = a.scr + static_cast<int64_t>(i) * kScr;
+    double ub[kNFit], xb[3];
+    if (!entry_adjoint(a, t, a.spos[i], a.spos[N + i], a.spos[2 * N + i], u, 1.0 / (rf * rf),
+                       1.0 / lam, len, ilen, bb + kScrBbar, 1, bb + kScrMbar, 1, ub, xb))
+      continue;
+    for (int k = 0; k < kNFit; ++k) acc[1 + k] += ub[k];
+    for (int c = 0; c < 3; ++c) acc[8 + c] += xb[c];
+  }
+  const int i = a.perm[t];
   for (int k = 0; k < 8; ++k) Ubar[k * N + i] = acc[k];
   for (int c = 0; c < 3; ++c) xbar[c * N + i] = acc[8 + c];
 }
@@ -458,7 +505,7 @@ phb_status adjoint_impl(int mode, const phb_plan* plan, const phb_params* prm, c
                         const double* lambda, const double* U, const double* gbar, void* ws,
                         size_t ws_bytes, double* rec, size_t rec_bytes, double* Ubar, double* xbar,
                         int32_t* status_word, cudaStream_t st) {
-  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_ADJ_SELF] + 11 * 8 * plan->n : 0);
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_END_ADJ] : 0);
   if (s != PHB_OK) return s;
   if (!prm || !pos || !lambda || !U) return PHB_ERR_INVALID_ARG;
   if (mode != kRecord && (!gbar || !Ubar || !xbar)) return PHB_ERR_INVALID_ARG;
@@ -488,7 +535,6 @@ phb_status adjoint_impl(int mode, const phb_plan* plan, const phb_params* prm, c
   a.c_zeta_a = prm->c_zeta_a;
   a.c_eta = prm->c_eta;
   a.scr = region<double>(plan, ws, R_ADJ_SCR);
-  a.edge = region<double>(plan, ws, R_ADJ_EDGE);
   a.self = region<double>(plan, ws, R_ADJ_SELF);
   a.rec = rec;
   a.status_word = status_word;
@@ -512,21 +558,20 @@ phb_status adjoint_impl(int mode, const phb_plan* plan, const phb_params* prm, c
   note_launch();
   int32_t* rcnt = region<int32_t>(plan, ws, R_ADJ_RCNT);
   int64_t* roff = region<int64_t>(plan, ws, R_ADJ_ROFF);
-  int64_t* ridx = region<int64_t>(plan, ws, R_ADJ_RIDX);
+  int32_t* rsrc = region<int32_t>(plan, ws, R_ADJ_RSRC);
   int64_t* bsum = region<int64_t>(plan, ws, R_SCAN);
   const int64_t cap = plan->nbr_capacity;
-  const unsigned eb = static_cast<unsigned>((cap + kThreads - 1) / kThreads);
   const unsigned nb = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   if ((e = cudaMemsetAsync(rcnt, 0, (n + 1) * sizeof(int32_t), st))) return launch_status(e);
-  k_rev_count<<<eb, kThreads, 0, st>>>(cap, a.off, n, a.idx, rcnt);
+  k_rev_count<<<nb, kThreads, 0, st>>>(n, cap, a.off, a.idx, rcnt);
   note_launch();
   if ((e = scan_exclusive_i32_to_i64(rcnt, roff, n + 1, bsum, st))) return launch_status(e);
   if ((e = cudaMemsetAsync(rcnt, 0, (n + 1) * sizeof(int32_t), st))) return launch_status(e);
-  k_rev_fill<<<eb, kThreads, 0, st>>>(cap, a.off, n, a.idx, roff, rcnt, ridx);
+  k_rev_fill<<<nb, kThreads, 0, st>>>(n, cap, a.off, a.idx, roff, rcnt, rsrc);
   note_launch();
-  k_rev_sort<<<nb, kThreads, 0, st>>>(n, roff, ridx);
+  k_rev_sort<<<nb, kThreads, 0, st>>>(n, roff, rsrc);
   note_launch();
-  k_adj_gather<<<nb, kThreads, 0, st>>>(n, a.perm, a.self, a.edge, roff, ridx, Ubar, xbar);
+  k_adj_gather<<<static_cast<unsigned>((n + 127) / 128), 128, 0, st>>>(a, roff, rsrc, Ubar, xbar);
   note_launch();
   return launch_status(cudaSuccess);
 }

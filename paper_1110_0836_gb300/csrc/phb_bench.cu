@@ -132,13 +132,13 @@ extern "C" int phb_fma_peak(int32_t precision, int32_t blocks, int32_t iters, vo
 
 extern "C" int phb_workspace_stats(const phb_plan* plan, const void* ws, int32_t* out, int32_t count,
                                    phb_stream_t stream) {
-  if (!plan || !ws || !out || count < 0 || count > 4 || plan->ws_bytes == 0) return 1;
-  int32_t tmp[3] = {0, 0, 0};
+  if (!plan || !ws || !out || count < 0 || count > 5 || plan->ws_bytes == 0) return 1;
+  int32_t tmp[6] = {0, 0, 0, 0, 0, 0};
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int32_t* misc = phb::region<int32_t>(plan, ws, phb::R_MISC);
   if (cudaMemcpyAsync(tmp, misc, sizeof(tmp), cudaMemcpyDeviceToHost, st) != cudaSuccess) return 3;
   if (cudaStreamSynchronize(st) != cudaSuccess) return 3;
-  const int32_t v[4] = {tmp[0], tmp[1], tmp[2], plan->ntiles};
+  const int32_t v[5] = {tmp[0], tmp[1], tmp[2], plan->ntiles, tmp[5]};
   for (int k = 0; k < count; ++k) out[k] = v[k];
   return 0;
 }

@@ -10,11 +10,26 @@
 // fitted fields in FP32 registers in two passes over its neighbour list
 // (moments + first field group, then the second group), factorises the
 // 19x19 normal matrix by an unrolled in-register Cholesky and back-substitutes
-// only the linear and quadratic coefficients.  Fits whose Jacobi-scaled
-// conditioning estimate (max L_kk / min L_kk)^2 exceeds the threshold, or
-// whose factorisation fails, are queued for the FP64 kernel.  Tiles whose
-// neighbourhood exceeds the staging capacity read neighbours from global
-// memory (FP32 hi/lo records) through the same code.
+// only the linear and quadratic coefficients.  Fits whose conditioning
+// estimate (19 x a greedy estimate of ||M_s^-1||_inf of the Jacobi-scaled
+// matrix M_s) exceeds the routing threshold, or whose factorisation fails,
+// are queued for the FP64 kernel.  Tiles whose neighbourhood exceeds the
+// staging capacity read neighbours from global memory (FP32 hi/lo records)
+// through the same code.
+//
+// Corrected semi-normal equations (Bjorck).  FP32 normal equations lose about
+// cond(M_s) x 2^-24 of the coefficient vector, and on density-sampled sets the
+// odd and even blocks of M_s couple, so the large linear coefficients of a
+// steep front leak into the quadratic ones (Hessian errors of 4e-4 of their
+// scale at the shear layer).  A tile whose largest estimate exceeds
+// refine_kappa (or every tile, by choice) therefore takes one corrected step
+// after the first solve: all 19 coefficients c0 of every field go to the
+// workspace, one more pass over the neighbours accumulates P^T W r with the
+// residuals r_j = (U_j - U_i) - p(q_j).c0 recomputed from the records, and the
+// same factor (re-formed from the moments kept in shared memory) solves for
+// the correction.  The error then follows cond(A) = cond(M_s)^(1/2) instead of
+// cond(M_s).  The decision is per tile, so the CTA's control flow and
+// barriers stay uniform.
 #include "phb_internal.cuh"
 #include "mls_gen.cuh"
 #include "phb_mhd.cuh"
@@ -208,6 +223,64 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
   return cnt;
 }
 
+// One corrected semi-normal-equations pass for the fields of parked slots
+// [k0, k0 + NFG): c0 (all 19 coefficients, slot order [k][19][n] in the
+// workspace) in registers, residuals r_j = du_j - p(q_j).c0 from the global
+// records, acc_k = sum_j w_j p(q_j) r_j parked in the slots' columns.
+// B selects the record half (false: rho, sigma, Vx, Vy; true: Vz, Bx, By, Bz);
+// du0 is the first du component used.
+template <int NFG, bool B, int T>
+__device__ __forceinline__ void csne_pass(const GlobalSrc& src, int64_t beg, int64_t end,
+                                          float inv_l, float inv_rf2, bool unweighted,
+                                          const float* c0, int64_t n, int s, int k0, int du0,
+                                          float* park, int col) {
+  float c[NFG][kNB], acc[NFG][kNB];
+#pragma unroll
+  for (int f = 0; f < NFG; ++f)
+#pragma unroll
+    for (int k = 0; k < kNB; ++k) {
+      c[f][k] = c0[((k0 + f) * kNB + k) * n + s];
+      acc[f][k] = 0.f;
+    }
+  for (int64_t e = beg; e < end; ++e) {
+    const int t = src.index(e);
+    float dx, dy, dz, du[4];
+    if (B) src.decode_b(src.fetch_b(t), dx, dy, dz, du);
+    else src.decode_a(src.fetch_a(t), dx, dy, dz, du);
+    const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
+    const float sw = 1.f - s2;
+    const float wt = s2 < 1.f ? (unweighted ? 1.f : sw * sw) : 0.f;
+    float qg[kNB];
+    mls_basis(dx * inv_l, dy * inv_l, dz * inv_l, qg);
+#pragma unroll
+    for (int f = 0; f < NFG; ++f) {
+      float r = du[du0 + f];
+#pragma unroll
+      for (int k = 0; k < kNB; ++k) r = fmaf(-qg[k], c[f][k], r);
+      mls_accum_rhs_basis(qg, wt * r, acc[f]);
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < NFG; ++f)
+#pragma unroll
+    for (int k = 0; k < kNB; ++k) park[((k0 + f) * kNB + k) * T + col] = acc[f][k];
+}
+
+// Linear and quadratic coefficients b[10..18] -> derivatives in the first
+// nine rows of the parked column (gradient, then the packed Hessian).
+template <int T>
+__device__ __forceinline__ void park_derivs(float* d, const float (&b)[kNB], float il, float il2) {
+  d[0 * T] = b[kLin0] * il;
+  d[1 * T] = b[kLin0 + 1] * il;
+  d[2 * T] = b[kLin0 + 2] * il;
+  d[3 * T] = 2.f * b[kQuad0] * il2;
+  d[4 * T] = b[kQuad0 + 1] * il2;
+  d[5 * T] = b[kQuad0 + 2] * il2;
+  d[6 * T] = 2.f * b[kQuad0 + 3] * il2;
+  d[7 * T] = b[kQuad0 + 4] * il2;
+  d[8 * T] = 2.f * b[kQuad0 + 5] * il2;
+}
+
 struct TileArgs {
   const int2* tplan;      // per tile: (staged particles, 1 = not staged)
   const int32_t* tslot;   // per tile: slot of every staged index (stage_cap stride)
@@ -291,15 +364,16 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
 
   float m[kNM], bB[4][kNB];
   int cnt = 0;
-  float inv_l = 1.f;
+  float inv_l = 1.f, inv_rf2 = 0.f;
+  int64_t beg = 0, end = 0;
+  const bool unweighted = a.weight_kind == 1;
   if (active) {
     const double lam = a.slam[s];
     const double rf = a.g.rf_factor * lam;
     inv_l = static_cast<float>(1.0 / lam);
-    const float inv_rf2 = static_cast<float>(1.0 / (rf * rf));
-    const int64_t beg = a.off[s];
-    const int64_t end = a.off[s + 1] < a.g.capacity ? a.off[s + 1] : a.g.capacity;
-    const bool unweighted = a.weight_kind == 1;
+    inv_rf2 = static_cast<float>(1.0 / (rf * rf));
+    beg = a.off[s];
+    end = a.off[s + 1] < a.g.capacity ? a.off[s + 1] : a.g.capacity;
     if (fb) {
       GlobalSrc src;
       src.rec = rec;
@@ -323,17 +397,21 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     }
   }
   __syncthreads();  // the staged records are dead from here on
+  // moments kept for the corrected step, after the parked right-hand sides
+  float* mstash = park + G::NF * kNB * T;
+  const bool may_refine = a.refine_mode >= 0;
+  const bool singular = !active || cnt < kNB;
+  bool routed = false, need = false;
+  float M[kNT], invd[kNB];
   if (active) {
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
       for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = bB[f][k];
-
-    const int dst = a.perm_out ? a.perm_out[s] : s;
-    bool singular = cnt < kNB;
-    bool routed = false;
     if (!singular) {
-      float M[kNT], invd[kNB];
+      if (may_refine)
+#pragma unroll
+        for (int k = 0; k < kNM; ++k) mstash[k * T + tid] = m[k];
       mls_assemble(m, M);
       const float minpiv = mls_cholesky<float>(M, invd);
       // conditioning estimate of the Jacobi-scaled matrix: n_b times the
@@ -344,31 +422,75 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
         a.queue[q] = s;
         routed = true;
       } else {
-        const float il = inv_l, il2 = inv_l * inv_l;
-#pragma unroll 1
-        for (int k = 0; k < G::NF; ++k) {
-          float b[kNB];
-#pragma unroll
-          for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
-          mls_forward(M, invd, b);
-          mls_back9(M, invd, b);
-          float* d = park + (k * kNB) * T + tid;
-          d[0 * T] = b[kLin0] * il;
-          d[1 * T] = b[kLin0 + 1] * il;
-          d[2 * T] = b[kLin0 + 2] * il;
-          d[3 * T] = 2.f * b[kQuad0] * il2;
-          d[4 * T] = b[kQuad0 + 1] * il2;
-          d[5 * T] = b[kQuad0 + 2] * il2;
-          d[6 * T] = 2.f * b[kQuad0 + 3] * il2;
-          d[7 * T] = b[kQuad0 + 4] * il2;
-          d[8 * T] = 2.f * b[kQuad0 + 5] * il2;
-        }
+        need = a.refine_mode == 1 || kappa > a.refine_kappa;
       }
-    } else {
-#pragma unroll 1
-      for (int k = 0; k < G::NF; ++k)
-        for (int j = 0; j < 9; ++j) park[(k * kNB + j) * T + tid] = 0.f;
     }
+  }
+  // one decision per tile keeps the CTA's control flow uniform
+  const bool refine = may_refine && __syncthreads_or(need);
+  if (refine && tid == 0) atomicAdd(a.refined_tiles, 1);
+  const bool solve = !singular && !routed;
+  const float il = inv_l, il2 = inv_l * inv_l;
+  if (solve && !refine) {
+#pragma unroll 1
+    for (int k = 0; k < G::NF; ++k) {
+      float b[kNB];
+#pragma unroll
+      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
+      mls_forward(M, invd, b);
+      mls_back9(M, invd, b);
+      park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
+    }
+  } else if (solve) {
+    // first solve: all 19 coefficients of every field to the workspace
+#pragma unroll 1
+    for (int k = 0; k < G::NF; ++k) {
+      float b[kNB];
+#pragma unroll
+      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
+      mls_forward(M, invd, b);
+      mls_back19(M, invd, b);
+#pragma unroll
+      for (int j = 0; j < kNB; ++j) a.csne[(k * kNB + j) * static_cast<int64_t>(n) + s] = b[j];
+    }
+    // residual passes over the neighbours (global records: the staged
+    // neighbourhood's storage now holds the parked columns and the moments)
+    GlobalSrc src;
+    src.rec = rec;
+    src.idx = a.idx;
+    for (int k = 0; k < 6; ++k) src.o[k] = rec[6 * s + k];
+    src.P = P;
+    csne_pass<G::NA, false, T>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, 0,
+                               4 - G::NA, park, tid);
+    csne_pass<4, true, T>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, G::NA, 0,
+                          park, tid);
+    // the same factor again from the kept moments; correction of the linear
+    // and quadratic coefficients
+    float mm[kNM];
+#pragma unroll
+    for (int k = 0; k < kNM; ++k) mm[k] = mstash[k * T + tid];
+    float M2[kNT], invd2[kNB];
+    mls_assemble(mm, M2);
+    mls_cholesky<float>(M2, invd2);
+#pragma unroll 1
+    for (int k = 0; k < G::NF; ++k) {
+      float b[kNB];
+#pragma unroll
+      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
+      mls_forward(M2, invd2, b);
+      mls_back9(M2, invd2, b);
+#pragma unroll
+      for (int j = kQuad0; j < kNB; ++j) b[j] += a.csne[(k * kNB + j) * static_cast<int64_t>(n) + s];
+      park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
+    }
+  }
+  if (active && singular) {
+#pragma unroll 1
+    for (int k = 0; k < G::NF; ++k)
+      for (int j = 0; j < 9; ++j) park[(k * kNB + j) * T + tid] = 0.f;
+  }
+  if (active) {
+    const int dst = a.perm_out ? a.perm_out[s] : s;
     if (!routed) {
       if (a.fit_status) a.fit_status[dst] = singular ? 1 : 0;
       if (singular) raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
@@ -467,7 +589,9 @@ cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, int64
   using G = Groups<MODE>;
   const size_t park_a = size_t(G::NA) * kNB * T * sizeof(float);
   const size_t staged = size_t(a.g.stage_cap) * 3 * sizeof(float4);
-  const size_t park_all = size_t(G::NF) * kNB * T * sizeof(float);
+  // after the accumulation: the parked columns of all fields, and the
+  // moments kept for the corrected step
+  const size_t park_all = size_t(G::NF * kNB + (a.refine_mode >= 0 ? kNM : 0)) * T * sizeof(float);
   const size_t smem = park_a + staged > park_all ? park_a + staged : park_all;
   const int64_t units = ta.list ? list_cap : a.n;
   const unsigned tiles = static_cast<unsigned>((units + T - 1) / T);

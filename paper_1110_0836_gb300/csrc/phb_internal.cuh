@@ -11,14 +11,14 @@ namespace phb {
 
 constexpr int kNF = 8;      // fields rho, Vx, Vy, Vz, Bx, By, Bz, sigma
 constexpr int kRec = 24;    // floats per FP32 particle record (6 x float4)
-constexpr int kEdgeAdj = 10;  // doubles per neighbour edge in the adjoint (7 fitted fields + 3 axes)
 
 // Workspace regions (byte offsets in plan->ws_off).  The PC-step and adjoint
 // regions share storage (never used at the same time).
 enum Region {
   R_MISC = 0,    // int32 [64]: 0 = FP64 route-queue length, 1 = tiles that fell back to
                  //   global gathers in the last neighbour build, 2 = same in the last
-                 //   fused fit, 3 = persistent tile-queue counter
+                 //   fused fit, 3 = persistent tile-queue counter, 4 = active-subset
+                 //   length, 5 = tiles refined by the last FP32-mixed fit
   R_KEYS,        // int32 [n]   cell key of each caller particle
   R_PERM,        // int32 [n]   slot -> caller index
   R_INV,         // int32 [n]   caller index -> slot
@@ -47,17 +47,19 @@ enum Region {
   R_ALIST,       // int32 [n+64] slots of an active subset (ascending)
   R_AFLAG,       // int32 [n+1]  active-subset marks / their exclusive scan
   R_QUEUE,       // int32 [n]    slots routed to FP64
+  R_CSNE,        // float [8][19][n] FP32 coefficients of refined fits (corrected step)
   R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
   R_PC_Y0,       // double [11][n] saved x^n, U^n (slot order) -- PC step
-  R_ADJ_EDGE,    // double [capacity][10] per-edge adjoint contributions -- adjoint
   R_ADJ_ROFF,    // int64 [n+1] reverse-list offsets                     -- adjoint
-  R_ADJ_RIDX,    // int64 [capacity] reverse-list edge ids               -- adjoint
+  R_ADJ_RSRC,    // int32 [capacity] reverse lists: the particles naming each particle -- adjoint
   R_ADJ_RCNT,    // int32 [n+1] reverse-list counts / cursors            -- adjoint
-  R_ADJ_SCR,     // double [266][n] per-particle coefficients c and bbar  -- adjoint
+  R_ADJ_SCR,     // double [n][266] per particle: seeds bbar, coefficients c then mbar -- adjoint
   R_ADJ_SELF,    // double [11][n] each particle's own adjoint terms      -- adjoint
   R_END_COMMON,  // end of the common part (prefix for RHS / derivs)
   R_END,         // end of everything
+  R_END_PC,      // end of the PC-step regions
+  R_END_ADJ,     // end of the adjoint regions
   R_COUNT
 };
 static_assert(R_COUNT <= 48, "ws_off has 48 entries");
@@ -283,6 +285,12 @@ struct FitArgs {
   int32_t* queue;              // FP64 route queue
   int32_t* queue_len;
   int32_t* status_word;
+  // FP32-mixed corrected semi-normal-equations step: -1 off, 0 tiles whose
+  // largest conditioning estimate exceeds refine_kappa, 1 every tile
+  int32_t refine_mode;
+  float refine_kappa;
+  float* csne;                 // [8][19][n] coefficients of the first solve (slot order)
+  int32_t* refined_tiles;      // count of refined tiles (zeroed before the launch)
 };
 
 // Fused FP32-mixed fit over all slots (list == null, staged tiles) or over

@@ -299,8 +299,9 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   sz[R_ALIST] = size_t(n + 64) * 4;
   sz[R_AFLAG] = size_t(n + 1) * 4;
   sz[R_QUEUE] = (n + 64) * 4;  // also the export's n+1 counts
+  sz[R_CSNE] = size_t(kNF) * 19 * n * 4;
   size_t off = 0;
-  for (int r = R_MISC; r <= R_QUEUE; ++r) {
+  for (int r = R_MISC; r <= R_CSNE; ++r) {
     p->ws_off[r] = off;
     off += align256(sz[r]);
   }
@@ -315,21 +316,31 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   pc += align256(size_t(11) * n * 8);
   // adjoint regions overlay the PC ones
   size_t ad = off;
-  p->ws_off[R_ADJ_EDGE] = ad;
-  ad += align256(size_t(kEdgeAdj) * cap * 8);
   p->ws_off[R_ADJ_ROFF] = ad;
   ad += align256(size_t(n + 1) * 8);
-  p->ws_off[R_ADJ_RIDX] = ad;
-  ad += align256(size_t(cap) * 8);
+  p->ws_off[R_ADJ_RSRC] = ad;
+  ad += align256(size_t(cap) * 4);
   p->ws_off[R_ADJ_RCNT] = ad;
   ad += align256(size_t(n + 1) * 4);
   p->ws_off[R_ADJ_SCR] = ad;
   ad += align256(size_t(266) * n * 8);
   p->ws_off[R_ADJ_SELF] = ad;
   ad += align256(size_t(11) * n * 8);
+  p->ws_off[R_END_PC] = pc;
+  p->ws_off[R_END_ADJ] = ad;
   p->ws_off[R_END] = std::max(pc, ad);
   p->ws_bytes = p->ws_off[R_END];
   return PHB_OK;
+}
+
+extern "C" int phb_workspace_part(const phb_plan* p, int32_t part, size_t* begin, size_t* end) {
+  if (!p || p->ws_bytes == 0 || !begin || !end) return 1;
+  switch (part) {
+    case PHB_PART_COMMON: *begin = 0; *end = p->ws_off[R_END_COMMON]; return 0;
+    case PHB_PART_STEP: *begin = p->ws_off[R_END_COMMON]; *end = p->ws_off[R_END_PC]; return 0;
+    case PHB_PART_ADJOINT: *begin = p->ws_off[R_END_COMMON]; *end = p->ws_off[R_END_ADJ]; return 0;
+    default: return 1;
+  }
 }
 
 extern "C" size_t phb_workspace_size(const phb_plan* p, int32_t op) {

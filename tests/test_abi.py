@@ -63,14 +63,31 @@ def test_plan_init_valid(L):
     assert p.nkeys == 64 * p.nbrick[0] * p.nbrick[1] * p.nbrick[2]
     offs = list(p.ws_off)[:10]
     assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
-    # the shared prefix ends where the predictor-corrector regions begin
+    # the shared prefix ends where the step and adjoint parts begin; both end
+    # inside the workspace and one of them ends it
     from paper_1110_0836_gb300 import _lib
-    end = p.ws_off[_lib.WS_END_COMMON]
-    assert end > offs[-1] and end == p.ws_off[_lib.WS_END_COMMON - 9]  # first predictor-corrector region
-    # adjoint regions: edge contributions (10 doubles per list entry) first, the
-    # per-particle self terms (11 doubles) last, ending the workspace
-    assert p.ws_off[_lib.WS_ADJ_SELF] - p.ws_off[_lib.WS_ADJ_EDGE] >= 10 * 8 * p.nbr_capacity
-    assert p.ws_off[_lib.WS_ADJ_SELF] + 11 * 8 * p.n <= p.ws_bytes
+    b0, end = _lib.workspace_part(p, _lib.PART_COMMON)
+    bs, es = _lib.workspace_part(p, _lib.PART_STEP)
+    ba, ea = _lib.workspace_part(p, _lib.PART_ADJOINT)
+    assert b0 == 0 and end > offs[-1] and bs == end and ba == end
+    assert es > bs and ea > ba and max(es, ea) == p.ws_bytes
+    # the step holds F(Y^n), F(Y^p) (8 doubles each) and Y^n (11 doubles) per particle
+    assert es - bs >= 27 * 8 * p.n
+    for bad in (-1, 3):
+        assert L.phb_workspace_part(C.byref(p), bad, C.byref(C.c_size_t()), C.byref(C.c_size_t())) == 1
+
+
+def test_recomputing_adjoint_needs_less_than_the_stored_record(L):
+    """The recomputing adjoint keeps per particle only its adjoint seeds and
+    own terms plus the reverse lists: its part of the workspace is smaller
+    than the stored-factorisation record it avoids (64^3 lattice plan)."""
+    from paper_1110_0836_gb300 import _lib
+    p = _plan(n=64 ** 3, lmin=1.0 / 64, lmax=1.0 / 64)
+    p.nbr_capacity = 72 * p.n + 1024        # the binding's default capacity
+    assert L.phb_plan_init(C.byref(p)) == 0
+    b, e = _lib.workspace_part(p, _lib.PART_ADJOINT)
+    L.phb_adjoint_record_bytes.restype = C.c_size_t
+    assert e - b < L.phb_adjoint_record_bytes(C.byref(p)), (e - b, L.phb_adjoint_record_bytes(C.byref(p)))
 
 
 @pytest.mark.parametrize("tile,schedule", [(64, 0), (128, 1)])
@@ -119,7 +136,7 @@ def test_struct_sizes_match_the_binding(L):
     out = (C.c_int64 * 3)()
     assert L.phb_struct_sizes(out, 3) == 0
     assert tuple(out) == (C.sizeof(_lib.Box), C.sizeof(_lib.Params), C.sizeof(_lib.Plan))
-    assert C.sizeof(_lib.Params) == 72    # gamma, kind, precision, threshold, zeta, eta, frozen, laws
+    assert C.sizeof(_lib.Params) == 88    # gamma, kind, precision, threshold, zeta, eta, frozen, laws, refine
     assert L.phb_struct_sizes(None, 3) == 1 and L.phb_struct_sizes(out, 4) == 1
 
 

@@ -148,3 +148,72 @@ def test_stored_record_too_small_is_rejected():
     rec = torch.empty(343 * w.n - 1, dtype=torch.float64, device="cuda")
     with pytest.raises(phb.PhbError):
         phb.adjoint_record(plan, prm, pos, lam, U, record=rec)
+
+
+def test_adjoint_workload_full_size():
+    """The adjoint workload at its stated size: 262,144 jittered-lattice
+    particles with random-mode fields, L = sum_ik r_ik (dU_k/dt)_i.
+    (1) 64 seeded gradient entries (positions and fields) against central
+    differences of the GPU FP64 forward (step 1e-6, neighbour sets held) at
+    1e-6, and against the oracle's exact directional derivatives (dual numbers
+    on the particles whose lists contain the perturbed one) at 1e-9;
+    (2) the dot-product identity <r_S, (J v)_S> = <J^T r_S, v> on a
+    4,096-particle subset S: the oracle's JVP at S along a random v against the
+    GPU adjoint of the loss restricted to S."""
+    phb = need_gpu()
+    w = workloads.config("C4")
+    n = w.n
+    plan, pos, lam, U, prm = setup(phb, w)
+    r = workloads.loss_weights(n)
+    Ub, xb = phb.rhs_adjoint(plan, prm, pos, lam, U, torch.tensor(r, device="cuda"))
+    Ub, xb = Ub.cpu().numpy(), xb.cpu().numpy()
+    box = oracle.box_of(w)
+    rng = np.random.default_rng(2024)
+    out_p = torch.empty((8, n), dtype=torch.float64, device="cuda")
+    out_m = torch.empty_like(out_p)
+    rg = torch.tensor(r, device="cuda")
+    scale_u = np.abs(Ub).max()
+    scale_x = np.abs(xb).max()
+    for k in range(64):
+        which = "x" if k % 3 == 0 else "U"
+        i = int(rng.integers(n))
+        c = int(rng.integers(3 if which == "x" else 8))
+        # particles whose right-hand side depends on particle i: i itself and
+        # every j that lists i (|x_i - x_j| < r_f,j)
+        d = w.pos - w.pos[:, i:i + 1]
+        d -= w.box_len[:, None] * np.rint(d / w.box_len[:, None])
+        q = np.flatnonzero(((d * d).sum(0) < (2.3 * w.lam) ** 2) | (np.arange(n) == i)).astype(np.int64)
+        nb = oracle.neighbors(box, w.pos, w.lam, q)
+        vpos = np.zeros((3, n))
+        vU = np.zeros((8, n))
+        (vpos if which == "x" else vU)[c, i] = 1.0
+        _, jv = oracle.rhs_jvp(box, w.pos, w.lam, w.U, vpos, vU, nb, q, gamma=w.gamma)
+        exact = float((r[:, q] * jv).sum())
+        got = float(xb[c, i] if which == "x" else Ub[c, i])
+        sc = scale_x if which == "x" else scale_u
+        assert abs(got - exact) <= 1e-9 * sc + 1e-9 * abs(exact), (which, c, i, got, exact)
+        h = 1e-6 * (w.lam[i] if which == "x" else 1.0)
+        p2, U2 = pos.clone(), U.clone()
+        (p2 if which == "x" else U2)[c, i] += h
+        phb.mhd_rhs(plan, prm, p2, lam, U2, out=out_p)
+        (p2 if which == "x" else U2)[c, i] -= 2 * h
+        phb.mhd_rhs(plan, prm, p2, lam, U2, out=out_m)
+        # the difference is nonzero only near i: summing it, not the two
+        # losses, keeps the rounding of the 2M-term sums out of the estimate
+        fd = float(((out_p - out_m) * rg).sum().item()) / (2 * h)
+        assert abs(fd - exact) <= 1e-6 * max(abs(exact), sc * (w.lam[i] if which == "x" else 1.0)), \
+            (which, c, i, fd, exact)
+    # dot-product identity on a 4,096-particle subset
+    S = sample(n, 4096, seed=11)
+    rS = np.zeros_like(r)
+    rS[:, S] = r[:, S]
+    UbS, xbS = phb.rhs_adjoint(plan, prm, pos, lam, U, torch.tensor(rS, device="cuda"))
+    vpos = rng.standard_normal((3, n)) * w.lam
+    vU = rng.standard_normal((8, n)) * 1e-2
+    nbS = oracle.neighbors(box, w.pos, w.lam, S)
+    _, jv = oracle.rhs_jvp(box, w.pos, w.lam, w.U, vpos, vU, nbS, S, gamma=w.gamma)
+    lhs = float((r[:, S] * jv).sum())
+    rhs = float((UbS.cpu().numpy() * vU).sum() + (xbS.cpu().numpy() * vpos).sum())
+    assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), 1.0), (lhs, rhs)
+    del plan
+    torch.cuda.empty_cache()

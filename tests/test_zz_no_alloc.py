@@ -33,7 +33,7 @@ def test_no_alloc_matches_workspace_path_twice(prec, tol):
     L = _lib.lib()
     w = workloads.random_modes(16, seed=77)
     plan = phb.Plan.for_workload(w)
-    assert plan.c.ws_off[_lib.WS_END_COMMON] <= L.phb_noalloc_scratch_bytes()
+    assert _lib.workspace_part(plan.c, _lib.PART_COMMON)[1] <= L.phb_noalloc_scratch_bytes()
     pos, lam, U = phb.tensors_of(w)
     prm = phb.Params(gamma=w.gamma, precision=prec)
     phb.build_neighbors(plan, pos, lam)
@@ -59,7 +59,7 @@ def test_no_alloc_rejects_plan_larger_than_scratch():
     L = _lib.lib()
     w = workloads.random_modes(40, seed=78)   # 64,000 particles: above the 32 MiB scratch
     plan = phb.Plan.for_workload(w)
-    assert plan.c.ws_off[_lib.WS_END_COMMON] > L.phb_noalloc_scratch_bytes()
+    assert _lib.workspace_part(plan.c, _lib.PART_COMMON)[1] > L.phb_noalloc_scratch_bytes()
     pos, lam, U = phb.tensors_of(w)
     out = torch.empty((8, w.n), dtype=torch.float64, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
