@@ -71,6 +71,9 @@ def parse():
                          "prebuilt lists, 'step' = two predictor-corrector steps")
     ap.add_argument("--precision", choices=["fp32_mixed", "fp64"], default="fp32_mixed",
                     help="precision of the --profile run")
+    ap.add_argument("--particles", type=int, default=0,
+                    help="--profile only: the workload's recipe at this particle count (a smaller "
+                         "set of the same recipe for captures that must stay small; 0 = as named)")
     ap.add_argument("--tile", type=int, default=0, help="fit tile (64 or 128; 0 = library default)")
     ap.add_argument("--schedule", type=int, default=0,
                     help="0 = one CTA per tile, 1 = persistent CTAs over a cost-ordered tile queue")
@@ -333,7 +336,13 @@ def run_profile(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     phb.build()
-    w = workloads.config(args.workload)
+    if args.particles > 0:
+        recipe = {"C3": workloads.shock_tube, "C5": workloads.shear_layer}
+        if args.workload not in recipe:
+            raise SystemExit("--particles applies to the density-sampled workloads C3 and C5")
+        w = recipe[args.workload](args.particles)
+    else:
+        w = workloads.config(args.workload)
     dt = cfl_dt(w)
     vmax = float(np.sqrt((w.U[1:4] ** 2).sum(0)).max())
     skin = max(4.0 * dt * vmax, 0.02 * 2.3 * float(w.lam.min()))

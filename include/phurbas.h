@@ -57,7 +57,8 @@ typedef enum {
   PHB_ERR_CAPACITY = 4,    /* neighbour list larger than plan.nbr_capacity */
   PHB_ERR_SKIN = 5,        /* predictor moved a particle by more than skin/2 */
   PHB_WARN_FIT = 6,        /* at least one fit was singular (its derivatives are 0) */
-  PHB_ERR_TIMEOUT = 7,     /* a bounded device wait gave up */
+  PHB_ERR_TIMEOUT = 7,     /* reserved for a bounded device wait that gave up (never
+                              returned: no kernel of this library waits on another) */
   PHB_ERR_NONFINITE = 8    /* a non-finite input or result was seen */
 } phb_status;
 
@@ -66,7 +67,8 @@ typedef enum {
 #define PHB_FLAG_SKIN 0x02
 #define PHB_FLAG_FIT_SINGULAR 0x04
 #define PHB_FLAG_NONFINITE 0x08
-#define PHB_FLAG_TIMEOUT 0x10
+#define PHB_FLAG_TIMEOUT 0x10 /* reserved: no kernel waits on another - the persistent
+                                 tile queue is a wait-free counter - so none sets it */
 #define PHB_FLAG_LAMBDA_RANGE 0x20 /* a lambda outside the plan's [lambda_min, lambda_max] */
 #define PHB_FLAG_BAD_INDEX 0x40    /* an active-subset index outside [0, n) (it was skipped) */
 
@@ -393,6 +395,22 @@ phb_status phb_rhs_adjoint_stored(const phb_plan* plan, const phb_params* params
                                   const double* record, size_t record_bytes, double* Ubar,
                                   double* xbar, int32_t* status_word, phb_stream_t stream);
 
+/* Mode-amplitude diagnostic of the Kelvin-Helmholtz test (Sec. 3.4: the
+ * growth of the unstable y-velocity mode measured by a discrete convolution
+ * over the particles instead of a Fourier transform of gridded values):
+ *   e_i = exp(-k |y~_i - y0|), y~ = y where y < ly / 2, ly - y elsewhere (a
+ *   layer at y0 and its mirror image at ly - y0),
+ *   s = sum_i Vy_i sin(k x_i) e_i,  c = sum_i Vy_i cos(k x_i) e_i,
+ *   d = sum_i e_i^2,  M = 2 [ (s / d)^2 + (c / d)^2 ]^(1/2),
+ * over all plan->n particles.  The paper's set-up: k = 4 pi, y0 = 1, ly = 4.
+ * pos [3][n] and U [8][n] device arrays (any particle order); out: device
+ * double [4] = (s, c, d, M).  FP64; the sums are formed in a fixed order, so
+ * repeated calls give identical results.  k > 0, ly > 0 and finite y0, else
+ * PHB_ERR_INVALID_ARG. */
+phb_status phb_kh_mode_amplitude(const phb_plan* plan, const double* pos, const double* U, double k,
+                                 double y0, double ly, void* ws, size_t ws_bytes, double* out,
+                                 phb_stream_t stream);
+
 /* Neighbour build + fused right-hand side (phb_build_neighbors followed by
  * phb_mhd_rhs) without any device allocation and without a caller workspace.
  * The paper has no counterpart: this exists for callers that cannot allocate
@@ -404,10 +422,13 @@ phb_status phb_rhs_adjoint_stored(const phb_plan* plan, const phb_params* params
  *     (32 MiB) that every GPU which loads the library holds until exit.  A
  *     plan whose build-and-fit workspace (everything before the
  *     predictor-corrector regions) is larger returns PHB_ERR_WORKSPACE and
- *     launches nothing; with constant lambda this allows roughly 26,000
+ *     launches nothing; with constant lambda this allows roughly 17,000
  *     particles.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call looks up the array's device address in the current context
+ *     (cudaGetSymbolAddress, a host-side query), so the call stays valid after
+ *     cudaDeviceReset and under any context.  The first call in a context
+ *     also loads the library's device code there: make it before any stream
+ *     capture.
  *   - Every call shares the array and leaves its contents behind; the kernels
  *     clear what must start at zero.  Calls that overlap on the GPU (other
  *     streams, other threads) race on the array: serialise them.

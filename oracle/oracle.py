@@ -318,6 +318,25 @@ def timestep_levels(lam, U, nbrs, gamma=5.0 / 3.0, cfl=0.1, dt_max=1.0, max_leve
     return out
 
 
+def kh_mode_amplitude(pos, U, k=4.0 * np.pi, y0=1.0, ly=4.0):
+    """Magnitude of the unstable y-velocity mode of the Kelvin-Helmholtz test
+    by a discrete convolution over the particles (Sec. 3.4):
+      M = 2 [ (sum s_i / sum d_i)^2 + (sum c_i / sum d_i)^2 ]^(1/2),
+      s_i = Vy_i sin(k x_i) e_i,  c_i = Vy_i cos(k x_i) e_i,  d_i = e_i^2,
+      e_i = exp(-k |y~_i - y0|),  y~ = y below ly / 2, ly - y above it,
+    the sums running over all particles.  The paper's set-up is k = 4 pi, a
+    layer at y0 = 1 and its mirror image at ly - y0 = 3 (ly = 4).  Plain FP64,
+    in particle order.  Returns (M, (sum s, sum c, sum d))."""
+    pos, U = _c(pos), _c(U)
+    x, y, vy = pos[0], pos[1], U[2]
+    yt = np.where(y < 0.5 * ly, y, ly - y)
+    e = np.exp(-k * np.abs(yt - y0))
+    s = float(np.sum(vy * np.sin(k * x) * e))
+    c = float(np.sum(vy * np.cos(k * x) * e))
+    d = float(np.sum(e * e))
+    return 2.0 * np.sqrt((s / d) ** 2 + (c / d) ** 2), (s, c, d)
+
+
 def workload_rhs(w, query=None, **kw):
     """Convenience: brute-force neighbours plus dU/dt for a workloads.Workload."""
     box = box_of(w)
@@ -334,7 +353,8 @@ def available() -> bool:
 
 
 __all__ = ["Box", "Params", "lib", "load", "using", "make_box", "box_of", "neighbors", "mls_derivs", "mhd_rhs", "adapt_scan", "adapt_apply",
-           "rhs_jvp", "pc_step", "timestep_levels", "workload_rhs", "available"]
+           "rhs_jvp", "pc_step", "timestep_levels", "kh_mode_amplitude", "workload_rhs",
+           "available"]
 
 if os.environ.get("PHB_ORACLE_EAGER"):
     lib()

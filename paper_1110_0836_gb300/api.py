@@ -406,6 +406,20 @@ def rhs_adjoint_stored(plan: Plan, params: Params, pos, lam, U, gbar, record, Ub
     return Ubar, xbar
 
 
+def kh_mode_amplitude(plan: Plan, pos, U, k: float = 4.0 * 3.141592653589793, y0: float = 1.0,
+                      ly: float = 4.0):
+    """Kelvin-Helmholtz mode amplitude (phb_kh_mode_amplitude): returns a
+    float64 device tensor (sum s, sum c, sum d, M)."""
+    n = plan.n
+    _need(pos, (3, n), "pos")
+    _need(U, (8, n), "U")
+    out = torch.empty(4, dtype=torch.float64, device=pos.device)
+    check(_lib.lib().phb_kh_mode_amplitude(C.byref(plan.c), _ptr(pos), _ptr(U), float(k), float(y0),
+                                           float(ly), _ptr(plan.ws), plan.ws.numel(), _ptr(out),
+                                           _stream()), "phb_kh_mode_amplitude")
+    return out
+
+
 def tensors_of(w, device="cuda"):
     """(pos, lam, U) float64 CUDA tensors of a workloads.Workload."""
     dev = torch.device(device)

@@ -225,16 +225,16 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
 
 // One corrected semi-normal-equations pass for the fields of parked slots
 // [k0, k0 + NFG): c0 (all 19 coefficients, slot order [k][19][n] in the
-// workspace) in registers, residuals r_j = du_j - p(q_j).c0 from the global
-// records, acc_k = sum_j w_j p(q_j) r_j parked in the slots' columns.
+// workspace) in registers, residuals r_j = du_j - p(q_j).c0 recomputed from
+// the global records (RawA = RawB there), acc_k = sum_j w_j p(q_j) r_j.
 // B selects the record half (false: rho, sigma, Vx, Vy; true: Vz, Bx, By, Bz);
 // du0 is the first du component used.
-template <int NFG, bool B, int T>
-__device__ __forceinline__ void csne_pass(const GlobalSrc& src, int64_t beg, int64_t end,
-                                          float inv_l, float inv_rf2, bool unweighted,
-                                          const float* c0, int64_t n, int s, int k0, int du0,
-                                          float* park, int col) {
-  float c[NFG][kNB], acc[NFG][kNB];
+template <int NFG, bool B, class Src>
+__device__ __forceinline__ void csne_pass(const Src& src, int64_t beg, int64_t end, float inv_l,
+                                          float inv_rf2, bool unweighted, const float* c0,
+                                          int64_t n, int s, int k0, int du0,
+                                          float (&acc)[NFG][kNB]) {
+  float c[NFG][kNB];
 #pragma unroll
   for (int f = 0; f < NFG; ++f)
 #pragma unroll
@@ -242,11 +242,15 @@ __device__ __forceinline__ void csne_pass(const GlobalSrc& src, int64_t beg, int
       c[f][k] = c0[((k0 + f) * kNB + k) * n + s];
       acc[f][k] = 0.f;
     }
+  // the next neighbour's record is loaded while this one is used
+  typename Src::RawB nxt;
+  if (beg < end) nxt = B ? src.fetch_b(src.index(beg)) : src.fetch_a(src.index(beg));
   for (int64_t e = beg; e < end; ++e) {
-    const int t = src.index(e);
+    const typename Src::RawB cur = nxt;
+    if (e + 1 < end) nxt = B ? src.fetch_b(src.index(e + 1)) : src.fetch_a(src.index(e + 1));
     float dx, dy, dz, du[4];
-    if (B) src.decode_b(src.fetch_b(t), dx, dy, dz, du);
-    else src.decode_a(src.fetch_a(t), dx, dy, dz, du);
+    if (B) src.decode_b(cur, dx, dy, dz, du);
+    else src.decode_a(cur, dx, dy, dz, du);
     const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
     const float sw = 1.f - s2;
     const float wt = s2 < 1.f ? (unweighted ? 1.f : sw * sw) : 0.f;
@@ -260,10 +264,6 @@ __device__ __forceinline__ void csne_pass(const GlobalSrc& src, int64_t beg, int
       mls_accum_rhs_basis(qg, wt * r, acc[f]);
     }
   }
-#pragma unroll
-  for (int f = 0; f < NFG; ++f)
-#pragma unroll
-    for (int k = 0; k < kNB; ++k) park[((k0 + f) * kNB + k) * T + col] = acc[f][k];
 }
 
 // Linear and quadratic coefficients b[10..18] -> derivatives in the first
@@ -301,6 +301,47 @@ struct FitShared {
   int tile;       // persistent schedule: tile taken from the queue
 };
 
+// Stage a tile's neighbourhood (count records, slots from the plan) in shared
+// memory: offsets and field differences relative to the tile's middle slot
+// sr, from the FP32 hi/lo records.  All T threads call it; no barrier inside.
+template <int T>
+__device__ __forceinline__ void stage_tile(const FitArgs& a, const Per32& P, const TileArgs& ta,
+                                           int tile, int sr, int count, float4* stage, int tid) {
+  const float4* rec = reinterpret_cast<const float4*>(a.rec);
+  // records relative to the tile's middle particle: the staged FP32 offsets
+  // and field differences round to at most half the tile's extent
+  const float4 rh = rec[6 * sr], rl = rec[6 * sr + 1];
+  const float4 fh = rec[6 * sr + 2], fl = rec[6 * sr + 3], gh = rec[6 * sr + 4], gl = rec[6 * sr + 5];
+  const int32_t* slots = ta.tslot + static_cast<int64_t>(tile) * a.g.stage_cap;
+  // eight records per thread in flight: slots first, then all their loads
+  constexpr int kB = 8;
+  for (int l0 = tid; l0 < count; l0 += kB * T) {
+    int sl[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) sl[u] = l0 + u * T < count ? slots[l0 + u * T] : -1;
+    float4 v[kB][6];
+#pragma unroll
+    for (int u = 0; u < kB; ++u)
+      if (sl[u] >= 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[u][k] = rec[6 * sl[u] + k];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      if (sl[u] < 0) continue;
+      const float4 p0 = v[u][0], p1 = v[u][1], f0 = v[u][2], f1 = v[u][3], g0 = v[u][4], g1 = v[u][5];
+      float4* d = stage + 3 * (l0 + u * T);
+      d[0] = make_float4(mi_diff32(p0.x, p1.x, rh.x, rl.x, P.len_h[0], P.len_l[0], P.inv_len[0]),
+                         mi_diff32(p0.y, p1.y, rh.y, rl.y, P.len_h[1], P.len_l[1], P.inv_len[1]),
+                         mi_diff32(p0.z, p1.z, rh.z, rl.z, P.len_h[2], P.len_l[2], P.inv_len[2]),
+                         hl(f0.y, f1.y, fh.y, fl.y));
+      d[1] = make_float4(hl(f0.z, f1.z, fh.z, fl.z), hl(f0.w, f1.w, fh.w, fl.w),
+                         hl(g0.x, g1.x, gh.x, gl.x), hl(f0.x, f1.x, fh.x, fl.x));
+      d[2] = make_float4(hl(g0.y, g1.y, gh.y, gl.y), hl(g0.z, g1.z, gh.z, gl.z),
+                         hl(g0.w, g1.w, gh.w, gl.w), 0.f);
+    }
+  }
+}
+
 // One tile: stage its neighbourhood, accumulate, solve, write outputs.  All
 // T threads call it (it contains block barriers).  Threads are assigned to
 // the tile's particles in descending list length (map recorded by the
@@ -324,39 +365,7 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   const int2 tp = listed ? make_int2(0, 1) : ta.tplan[tile];
   const bool fb = tp.y != 0;
   if (!fb) {
-    // records relative to the tile's middle particle: the staged FP32 offsets
-    // and field differences round to at most half the tile's extent
-    const int sr = s0 + (cnt_tile >> 1);
-    const float4 rh = rec[6 * sr], rl = rec[6 * sr + 1];
-    const float4 fh = rec[6 * sr + 2], fl = rec[6 * sr + 3], gh = rec[6 * sr + 4], gl = rec[6 * sr + 5];
-    const int32_t* slots = ta.tslot + static_cast<int64_t>(tile) * a.g.stage_cap;
-    // eight records per thread in flight: slots first, then all their loads
-    constexpr int kB = 8;
-    for (int l0 = tid; l0 < tp.x; l0 += kB * T) {
-      int sl[kB];
-#pragma unroll
-      for (int u = 0; u < kB; ++u) sl[u] = l0 + u * T < tp.x ? slots[l0 + u * T] : -1;
-      float4 v[kB][6];
-#pragma unroll
-      for (int u = 0; u < kB; ++u)
-        if (sl[u] >= 0)
-#pragma unroll
-          for (int k = 0; k < 6; ++k) v[u][k] = rec[6 * sl[u] + k];
-#pragma unroll
-      for (int u = 0; u < kB; ++u) {
-        if (sl[u] < 0) continue;
-        const float4 p0 = v[u][0], p1 = v[u][1], f0 = v[u][2], f1 = v[u][3], g0 = v[u][4], g1 = v[u][5];
-        float4* d = stage + 3 * (l0 + u * T);
-        d[0] = make_float4(mi_diff32(p0.x, p1.x, rh.x, rl.x, P.len_h[0], P.len_l[0], P.inv_len[0]),
-                           mi_diff32(p0.y, p1.y, rh.y, rl.y, P.len_h[1], P.len_l[1], P.inv_len[1]),
-                           mi_diff32(p0.z, p1.z, rh.z, rl.z, P.len_h[2], P.len_l[2], P.inv_len[2]),
-                           hl(f0.y, f1.y, fh.y, fl.y));
-        d[1] = make_float4(hl(f0.z, f1.z, fh.z, fl.z), hl(f0.w, f1.w, fh.w, fl.w),
-                           hl(g0.x, g1.x, gh.x, gl.x), hl(f0.x, f1.x, fh.x, fl.x));
-        d[2] = make_float4(hl(g0.y, g1.y, gh.y, gl.y), hl(g0.z, g1.z, gh.z, gl.z),
-                           hl(g0.w, g1.w, gh.w, gl.w), 0.f);
-      }
-    }
+    stage_tile<T>(a, P, ta, tile, s0 + (cnt_tile >> 1), tp.x, stage, tid);
   } else if (tid == 0 && !listed) {
     atomicAdd(ta.fallback_count, 1);
   }
@@ -453,17 +462,33 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
 #pragma unroll
       for (int j = 0; j < kNB; ++j) a.csne[(k * kNB + j) * static_cast<int64_t>(n) + s] = b[j];
     }
-    // residual passes over the neighbours (global records: the staged
-    // neighbourhood's storage now holds the parked columns and the moments)
+    // residual passes over the neighbours from the global records: offsets and
+    // field differences straight from the hi/lo splits of the particle and the
+    // neighbour round to ~2^-24 of the difference itself, while the staged ones
+    // (relative to the tile's middle particle) round to 2^-24 of the change
+    // across the tile - too coarse a floor for the corrected solution
     GlobalSrc src;
     src.rec = rec;
     src.idx = a.idx;
     for (int k = 0; k < 6; ++k) src.o[k] = rec[6 * s + k];
     src.P = P;
-    csne_pass<G::NA, false, T>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, 0,
-                               4 - G::NA, park, tid);
-    csne_pass<4, true, T>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, G::NA, 0,
-                          park, tid);
+    {
+      float acc[G::NA][kNB];
+      csne_pass<G::NA, false>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, 0,
+                              4 - G::NA, acc);
+#pragma unroll
+      for (int f = 0; f < G::NA; ++f)
+#pragma unroll
+        for (int k = 0; k < kNB; ++k) park[(f * kNB + k) * T + tid] = acc[f][k];
+    }
+    {
+      float acc[4][kNB];
+      csne_pass<4, true>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, G::NA, 0, acc);
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = acc[f][k];
+    }
     // the same factor again from the kept moments; correction of the linear
     // and quadratic coefficients
     float mm[kNM];

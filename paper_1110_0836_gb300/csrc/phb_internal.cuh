@@ -11,6 +11,7 @@ namespace phb {
 
 constexpr int kNF = 8;      // fields rho, Vx, Vy, Vz, Bx, By, Bz, sigma
 constexpr int kRec = 24;    // floats per FP32 particle record (6 x float4)
+constexpr int kDiagBlocks = 1024;  // fixed grid of the diagnostic reductions (deterministic sums)
 
 // Workspace regions (byte offsets in plan->ws_off).  The PC-step and adjoint
 // regions share storage (never used at the same time).
@@ -48,6 +49,7 @@ enum Region {
   R_AFLAG,       // int32 [n+1]  active-subset marks / their exclusive scan
   R_QUEUE,       // int32 [n]    slots routed to FP64
   R_CSNE,        // float [8][19][n] FP32 coefficients of refined fits (corrected step)
+  R_DIAG,        // double [3][kDiagBlocks] block partial sums of the mode-amplitude diagnostic
   R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
   R_PC_Y0,       // double [11][n] saved x^n, U^n (slot order) -- PC step

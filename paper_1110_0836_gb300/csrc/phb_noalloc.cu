@@ -10,8 +10,6 @@
 // copies, FP32 records) from one fixed array that the library declares at file
 // scope in device memory.  It runs the same kernels as phb_build_neighbors
 // followed by phb_mhd_rhs, with that array as the workspace.
-#include <mutex>
-
 #include "phb_internal.cuh"
 
 namespace {
@@ -20,28 +18,20 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB on every dev
 
 // The scratch itself.  In host code `g_static_scratch` is only a host-side
 // stand-in for the symbol, not a device address: the device address comes from
-// cudaGetSymbolAddress, looked up once per device below.
+// cudaGetSymbolAddress in the context that is current when the call is made.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
-// Device address of the scratch array on the current device (looked up on
-// the first call for that device).
+// Device address of the scratch array in the current context.  It is looked
+// up on every call rather than cached per device ordinal: after
+// cudaDeviceReset, or under another context on the same device, the array
+// lives at another address, and a cached one would send the kernels to memory
+// that is no longer (or not) theirs.  The lookup is a host-side query; the
+// first one in a context also loads the library's device code there.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

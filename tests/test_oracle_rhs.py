@@ -230,3 +230,32 @@ def test_rhs_does_not_depend_on_particle_order(orc):
     assert np.array_equal(st2, st[p])
     scale = np.abs(out).max(axis=1, keepdims=True)
     assert (np.abs(out2 - out[:, p]) <= 1e-12 * scale).all()
+
+
+def test_linear_wave_generator_speeds_and_polarisations():
+    """The App. A eigen-decomposition used by the linear-wave workloads, pinned
+    to the textbook ideal-MHD wave speeds: for B0 = (1, sqrt 2, 0.5), rho0 = 1,
+    P0 = 1, gamma = 5/3 and k along x, omega^2 / k^2 = 4.5504 (fast), 0.36627
+    (slow) and 1.0 (Alfven, (k.vA)^2 / k^2), with
+    c_f,s^2 = [(c_s^2 + v_A^2) +- sqrt((c_s^2 + v_A^2)^2 - 4 c_s^2 v_Ax^2)] / 2;
+    the Alfven velocity is perpendicular to k and B0, the fast and slow ones lie
+    in their plane and are orthogonal to each other."""
+    import workloads
+    B0, rho0, P0, gamma = np.array([1.0, np.sqrt(2.0), 0.5]), 1.0, 1.0, 5.0 / 3.0
+    k = 2.0 * np.pi
+    w2, vec = workloads.linear_mhd_modes((k, 0.0, 0.0), B0, rho0, P0, gamma)
+    c2 = np.sort(w2 / k ** 2)
+    cs2, va2, vax2 = gamma * P0 / rho0, (B0 @ B0) / rho0, B0[0] ** 2 / rho0
+    root = np.sqrt((cs2 + va2) ** 2 - 4.0 * cs2 * vax2)
+    expect = np.sort([(cs2 + va2 + root) / 2, (cs2 + va2 - root) / 2, vax2])
+    assert np.allclose(c2, expect, rtol=1e-13, atol=0)
+    assert np.allclose(c2, [0.36627, 1.0, 4.5504], rtol=0, atol=6e-5)
+    ia = int(np.argmin(np.abs(w2 / k ** 2 - vax2)))
+    kx = np.array([1.0, 0.0, 0.0])
+    alfven = vec[:, ia]
+    assert abs(alfven @ kx) < 1e-12 and abs(alfven @ B0) < 1e-12
+    normal = np.cross(kx, B0) / np.linalg.norm(np.cross(kx, B0))
+    others = [vec[:, j] for j in range(3) if j != ia]
+    for v in others:
+        assert abs(v @ normal) < 1e-12
+    assert abs(others[0] @ others[1]) < 1e-12
