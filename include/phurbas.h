@@ -360,6 +360,43 @@ phb_status phb_timestep_levels(const phb_plan* plan, const phb_params* params, c
                                int32_t max_level, void* ws, size_t ws_bytes, int32_t* levels,
                                int32_t* status_word, phb_stream_t stream);
 
+/* Individual power-of-two time steps (Sec. 2: each particle has its own step,
+ * independent of the bulk velocity; Sec. 2.1: rounded down to powers of two
+ * and organised as GADGET's binary blocks), every particle advanced by the
+ * second-order predictor-corrector (read as Heun).  The paper leaves the
+ * scheme to GADGET; the readings implemented:
+ *   - a synchronised step of dt_max is cut into 2^max_level substeps of
+ *     delta = dt_max / 2^max_level; a particle of level L (levels from
+ *     phb_timestep_levels) takes steps of m = 2^(max_level - L) substeps, all
+ *     starting together at the synchronised time;
+ *   - each particle keeps an anchor: its state (x0, U0) and F0 = dU/dt at the
+ *     start of its current step; at substep time t its current state is the
+ *     prediction (x0, U0) + (t - t0) (V0, F0), the predictor itself when its
+ *     step ends at t;
+ *   - at substep time t the particles whose step ends there are corrected:
+ *     F = dU/dt at the current states of all particles (neighbour sets built
+ *     at the current positions), x = x0 + (D/2)(V0 + V), U = U0 + (D/2)(F0 +
+ *     F), D = m delta; dU/dt at the corrected states (the others still at
+ *     their predictions) is their new anchor's F0.
+ * With every particle on one level a synchronised step is the plain Heun step.
+ * anchor: caller-owned device double [19][n], caller order: x0 [3], U0 [8],
+ * F0 [8].  phb_block_begin fills it at a synchronised time from pos, U (one
+ * full right-hand side); phb_block_substep(k) advances from substep k to
+ * k + 1 (0 <= k < 2^max_level, in order): pos and U (in-out) become the
+ * current states at t_{k+1}; after the last substep every particle is
+ * synchronised at t + dt_max and the anchor continues into the next step
+ * (levels may change there).  levels: device int32 [n]; a level outside
+ * [0, max_level] is clamped and sets PHB_FLAG_BAD_INDEX.  0 <= max_level <=
+ * 30 and dt_max > 0, else PHB_ERR_INVALID_ARG.  Uses the step part of the
+ * workspace (PHB_PART_STEP) and rebuilds the plan's neighbour lists. */
+phb_status phb_block_begin(const phb_plan* plan, const phb_params* params, const double* pos,
+                           const double* lambda, const double* U, double* anchor, void* ws,
+                           size_t ws_bytes, int32_t* status_word, phb_stream_t stream);
+phb_status phb_block_substep(const phb_plan* plan, const phb_params* params, double* pos,
+                             const double* lambda, double* U, double* anchor,
+                             const int32_t* levels, int32_t k, int32_t max_level, double dt_max,
+                             void* ws, size_t ws_bytes, int32_t* status_word, phb_stream_t stream);
+
 /* Reverse-mode derivative of the fused fit + right-hand side (not in the
  * paper): given gbar = dL/d(dudt) [8][n], returns Ubar = dL/dU [8][n] and
  * xbar = dL/dpos [3][n] with the neighbour sets of the last build held fixed

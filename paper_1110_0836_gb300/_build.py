@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphurbas.so")
 SOURCES = ["phb_plan.cu", "phb_neighbors.cu", "phb_rhs.cu", "phb_fit_mixed.cu", "phb_fit_fp64.cu",
            "phb_pc.cu", "phb_adjoint.cu", "phb_bench.cu", "phb_noalloc.cu", "phb_levels.cu",
-           "phb_diag.cu"]
+           "phb_diag.cu", "phb_block.cu"]
 HEADERS = ["phb_internal.cuh", "phb_mhd.cuh", "mls_gen.cuh", "phb_tile.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -406,6 +406,35 @@ def rhs_adjoint_stored(plan: Plan, params: Params, pos, lam, U, gbar, record, Ub
     return Ubar, xbar
 
 
+def block_step(plan: Plan, params: Params, pos, lam, U, levels, dt_max: float, max_level: int,
+               anchor=None):
+    """One synchronised step of dt_max with individual power-of-two steps
+    (phb_block_begin when no anchor is given, then phb_block_substep for each
+    of the 2^max_level substeps).  pos and U are advanced in place; returns
+    the anchor ([19, n] float64) to continue with."""
+    n = plan.n
+    _need(pos, (3, n), "pos")
+    _need(lam, (n,), "lam")
+    _need(U, (8, n), "U")
+    _need(levels, (n,), "levels", torch.int32)
+    L = _lib.lib()
+    if anchor is None:
+        anchor = torch.empty((19, n), dtype=torch.float64, device=pos.device)
+        pc = params.c()
+        check(L.phb_block_begin(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                                _ptr(anchor), _ptr(plan.ws), plan.ws.numel(),
+                                _ptr(plan.status_word), _stream()), "phb_block_begin")
+    else:
+        _need(anchor, (19, n), "anchor")
+    pc = params.c()
+    for k in range(1 << int(max_level)):
+        check(L.phb_block_substep(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                                  _ptr(anchor), _ptr(levels), k, int(max_level), float(dt_max),
+                                  _ptr(plan.ws), plan.ws.numel(), _ptr(plan.status_word),
+                                  _stream()), "phb_block_substep")
+    return anchor
+
+
 def kh_mode_amplitude(plan: Plan, pos, U, k: float = 4.0 * 3.141592653589793, y0: float = 1.0,
                       ly: float = 4.0):
     """Kelvin-Helmholtz mode amplitude (phb_kh_mode_amplitude): returns a

@@ -45,6 +45,11 @@ __device__ __forceinline__ float hl(float ah, float al, float bh, float bl) {
   return (ah - bh) + (al - bl);
 }
 
+// Column k (0..18) of paired accumulators (basis indices 2j, 2j+1 in pair j).
+__device__ __forceinline__ float pair_at(const float2 (&v)[kNB2], int k) {
+  return (k & 1) ? v[k >> 1].y : v[k >> 1].x;
+}
+
 // Field groups.  Pass A: (rho), sigma, Vx, Vy.  Pass B: Vz, Bx, By, Bz.
 // The RHS never uses the density fit (Drho/Dt needs only rho_i and div V),
 // so the RHS mode skips it.
@@ -159,17 +164,17 @@ struct StagedSrc {
 template <FitMode MODE, int T, class Src>
 __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t end, float inv_l,
                                           float inv_rf2, bool unweighted, float* park, int col,
-                                          float (&m)[kNM], float (&bB)[4][kNB]) {
+                                          float (&m)[kNM], float2 (&bB)[4][kNB2]) {
   using G = Groups<MODE>;
   int cnt = 0;
 #pragma unroll
   for (int k = 0; k < kNM; ++k) m[k] = 0.f;
   {
-    float bA[G::NA][kNB];
+    float2 bA[G::NA][kNB2];
 #pragma unroll
     for (int f = 0; f < G::NA; ++f)
 #pragma unroll
-      for (int k = 0; k < kNB; ++k) bA[f][k] = 0.f;
+      for (int j = 0; j < kNB2; ++j) bA[f][j] = make_float2(0.f, 0.f);
     int n1 = beg < end ? src.index(beg) : 0;
     int n2 = beg + 1 < end ? src.index(beg + 1) : 0;
     int n3 = beg + 2 < end ? src.index(beg + 2) : 0;
@@ -185,23 +190,24 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
       const float sw = 1.f - s2;
       const float wt = inside ? (unweighted ? 1.f : sw * sw) : 0.f;
       cnt += inside ? 1 : 0;
-      float qg[kNB], wq[kNB + 1];
-      mls_monomials_cubic_w(dx * inv_l, dy * inv_l, dz * inv_l, wt, qg, wq);
-      mls_accum_moments(qg, wq, m);
-      if (MODE == FitMode::kDerivs) mls_accum_rhs_basis(qg, wt * du[0], bA[0]);
-      mls_accum_rhs_basis(qg, wt * du[1], bA[G::NA - 3]);
-      mls_accum_rhs_basis(qg, wt * du[2], bA[G::NA - 2]);
-      mls_accum_rhs_basis(qg, wt * du[3], bA[G::NA - 1]);
+      float2 qg2[kNB2];
+      float wq[kNB + 1];
+      mls_monomials_cubic_w2(dx * inv_l, dy * inv_l, dz * inv_l, wt, qg2, wq);
+      mls_accum_moments2(qg2, wq, m);
+      if (MODE == FitMode::kDerivs) mls_accum_rhs_basis2(qg2, wt * du[0], bA[0]);
+      mls_accum_rhs_basis2(qg2, wt * du[1], bA[G::NA - 3]);
+      mls_accum_rhs_basis2(qg2, wt * du[2], bA[G::NA - 2]);
+      mls_accum_rhs_basis2(qg2, wt * du[3], bA[G::NA - 1]);
     }
 #pragma unroll
     for (int f = 0; f < G::NA; ++f)
 #pragma unroll
-      for (int k = 0; k < kNB; ++k) park[(f * kNB + k) * T + col] = bA[f][k];
+      for (int k = 0; k < kNB; ++k) park[(f * kNB + k) * T + col] = pair_at(bA[f], k);
   }
 #pragma unroll
   for (int f = 0; f < 4; ++f)
 #pragma unroll
-    for (int k = 0; k < kNB; ++k) bB[f][k] = 0.f;
+    for (int j = 0; j < kNB2; ++j) bB[f][j] = make_float2(0.f, 0.f);
   int n1 = beg < end ? src.index(beg) : 0;
   int n2 = beg + 1 < end ? src.index(beg + 1) : 0;
   int n3 = beg + 2 < end ? src.index(beg + 2) : 0;
@@ -215,10 +221,10 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
     const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
     const float sw = 1.f - s2;
     const float wt = s2 < 1.f ? (unweighted ? 1.f : sw * sw) : 0.f;
-    float qg[kNB];
-    mls_basis(dx * inv_l, dy * inv_l, dz * inv_l, qg);
+    float2 qg2[kNB2];
+    mls_basis2(dx * inv_l, dy * inv_l, dz * inv_l, qg2);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) mls_accum_rhs_basis(qg, wt * du[f], bB[f]);
+    for (int f = 0; f < 4; ++f) mls_accum_rhs_basis2(qg2, wt * du[f], bB[f]);
   }
   return cnt;
 }
@@ -233,14 +239,16 @@ template <int NFG, bool B, class Src>
 __device__ __forceinline__ void csne_pass(const Src& src, int64_t beg, int64_t end, float inv_l,
                                           float inv_rf2, bool unweighted, const float* c0,
                                           int64_t n, int s, int k0, int du0,
-                                          float (&acc)[NFG][kNB]) {
-  float c[NFG][kNB];
+                                          float2 (&acc)[NFG][kNB2]) {
+  float2 c[NFG][kNB2];
 #pragma unroll
   for (int f = 0; f < NFG; ++f)
 #pragma unroll
-    for (int k = 0; k < kNB; ++k) {
-      c[f][k] = c0[((k0 + f) * kNB + k) * n + s];
-      acc[f][k] = 0.f;
+    for (int j = 0; j < kNB2; ++j) {
+      const float lo = c0[((k0 + f) * kNB + 2 * j) * n + s];
+      const float hi = 2 * j + 1 < kNB ? c0[((k0 + f) * kNB + 2 * j + 1) * n + s] : 0.f;
+      c[f][j] = make_float2(lo, hi);
+      acc[f][j] = make_float2(0.f, 0.f);
     }
   // the next neighbour's record is loaded while this one is used
   typename Src::RawB nxt;
@@ -254,17 +262,16 @@ __device__ __forceinline__ void csne_pass(const Src& src, int64_t beg, int64_t e
     const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
     const float sw = 1.f - s2;
     const float wt = s2 < 1.f ? (unweighted ? 1.f : sw * sw) : 0.f;
-    float qg[kNB];
-    mls_basis(dx * inv_l, dy * inv_l, dz * inv_l, qg);
+    float2 qg2[kNB2];
+    mls_basis2(dx * inv_l, dy * inv_l, dz * inv_l, qg2);
 #pragma unroll
     for (int f = 0; f < NFG; ++f) {
-      float r = du[du0 + f];
-#pragma unroll
-      for (int k = 0; k < kNB; ++k) r = fmaf(-qg[k], c[f][k], r);
-      mls_accum_rhs_basis(qg, wt * r, acc[f]);
+      const float r = du[du0 + f] - mls_dot2(qg2, c[f]);
+      mls_accum_rhs_basis2(qg2, wt * r, acc[f]);
     }
   }
 }
+
 
 // Linear and quadratic coefficients b[10..18] -> derivatives in the first
 // nine rows of the parked column (gradient, then the packed Hessian).
@@ -371,7 +378,8 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   }
   __syncthreads();
 
-  float m[kNM], bB[4][kNB];
+  float m[kNM];
+  float2 bB[4][kNB2];
   int cnt = 0;
   float inv_l = 1.f, inv_rf2 = 0.f;
   int64_t beg = 0, end = 0;
@@ -416,7 +424,7 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
-      for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = bB[f][k];
+      for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = pair_at(bB[f], k);
     if (!singular) {
       if (may_refine)
 #pragma unroll
@@ -473,21 +481,21 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     for (int k = 0; k < 6; ++k) src.o[k] = rec[6 * s + k];
     src.P = P;
     {
-      float acc[G::NA][kNB];
+      float2 acc[G::NA][kNB2];
       csne_pass<G::NA, false>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, 0,
                               4 - G::NA, acc);
 #pragma unroll
       for (int f = 0; f < G::NA; ++f)
 #pragma unroll
-        for (int k = 0; k < kNB; ++k) park[(f * kNB + k) * T + tid] = acc[f][k];
+        for (int k = 0; k < kNB; ++k) park[(f * kNB + k) * T + tid] = pair_at(acc[f], k);
     }
     {
-      float acc[4][kNB];
+      float2 acc[4][kNB2];
       csne_pass<4, true>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, G::NA, 0, acc);
 #pragma unroll
       for (int f = 0; f < 4; ++f)
 #pragma unroll
-        for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = acc[f][k];
+        for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = pair_at(acc[f], k);
     }
     // the same factor again from the kept moments; correction of the linear
     // and quadratic coefficients

@@ -314,6 +314,13 @@ void note_launch(int count = 1);
 int trace_begin(int kernel_id, cudaStream_t st);
 void trace_end(int slot, cudaStream_t st);
 
+// Fused FP32-mixed / FP64 right-hand side of the slots marked 1 in the
+// workspace's active-subset marks (R_AFLAG, n + 1 entries, the last 0), over
+// the slot-order state already in the workspace; dudt in caller order at the
+// marked particles only.
+cudaError_t run_fit_marked(const phb_plan* plan, const phb_params* prm, void* ws, double* dudt,
+                           int32_t* fit_status, int32_t* status_word, cudaStream_t st);
+
 // Run the fused fit over the slot-order state already in the workspace:
 // mixed kernel + FP64 queue, or the FP64 kernel alone; over all slots, or
 // over list[0 .. *list_len) (list_cap entries at most) when list is given.

@@ -63,6 +63,21 @@ __global__ void k_list_active(int n, const int32_t* __restrict__ scan, int32_t* 
 
 }  // namespace
 
+cudaError_t run_fit_marked(const phb_plan* plan, const phb_params* prm, void* ws, double* dudt,
+                           int32_t* fit_status, int32_t* status_word, cudaStream_t st) {
+  const int n = static_cast<int>(plan->n);
+  int32_t* mark = region<int32_t>(plan, ws, R_AFLAG);
+  int32_t* list = region<int32_t>(plan, ws, R_ALIST);
+  int32_t* list_len = region<int32_t>(plan, ws, R_MISC) + 4;
+  cudaError_t e = scan_exclusive_i32(mark, n + 1, region<int64_t>(plan, ws, R_SCAN), st);
+  if (e) return e;
+  k_list_active<<<static_cast<unsigned>((n + 1 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+      n, mark, list, list_len);
+  note_launch();
+  return run_fit(plan, prm, ws, FitMode::kRHS, region<int32_t>(plan, ws, R_PERM), dudt, nullptr,
+                 nullptr, fit_status, status_word, st, list, list_len, n);
+}
+
 cudaError_t gather_sorted(const phb_plan* p, const Grid& g, const double* pos, const double* lam,
                           const double* U, void* ws, int32_t* status_word, cudaStream_t st) {
   k_gather_all<<<static_cast<unsigned>((g.n + kThreads - 1) / kThreads), kThreads, 0, st>>>(

@@ -149,3 +149,42 @@ def test_apply_mutation_is_caught(name, monkeypatch):
             caught = True
             break
     assert caught, f"no pin caught mutation {name}"
+
+
+# Mistakes planted in the numpy block-step integrator: each must fail one of
+# its pins.
+BLOCK_MUTATIONS = {
+    # inactive neighbours held at their anchor state instead of predicted
+    "block_no_prediction": ("tau = ((k + 1) - s) * delta",
+                            "tau = np.where((k + 1) % m == 0, ((k + 1) - s) * delta, 0.0)"),
+    # corrector with one substep instead of the particle's own step
+    "block_wrong_step": ("half = 0.5 * (m[A] * delta)", "half = 0.5 * delta"),
+    # explicit Euler instead of the trapezoidal corrector
+    "block_euler": ("ua = u0[:, A] + half * (f0[:, A] + F)", "ua = u0[:, A] + 2.0 * half * f0[:, A]"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(BLOCK_MUTATIONS))
+def test_block_mutation_is_caught(name):
+    import inspect
+    import types
+    from oracle import oracle as omod
+    import test_oracle_step as tstep
+    src = inspect.getsource(omod.block_step)
+    old, new = BLOCK_MUTATIONS[name]
+    assert src.count(old) == 1, f"mutation anchor not unique/found: {old!r}"
+    ns = dict(vars(omod))
+    exec(compile(src.replace(old, new), "<mutated block_step>", "exec"), ns)
+    mutated = types.SimpleNamespace(**{k: getattr(oracle, k) for k in dir(oracle)
+                                       if not k.startswith("_")})
+    mutated.block_step = ns["block_step"]
+    caught = False
+    for pin in (tstep.test_block_step_one_level_is_heun, tstep.test_block_step_uniform_flow_is_exact,
+                tstep.test_block_step_two_levels_second_order):
+        try:
+            pin(mutated)
+        except AssertionError:
+            caught = True
+            break
+    assert caught, f"no pin caught mutation {name}"
