@@ -87,6 +87,9 @@ def parse():
                     help="launch the timed steps eagerly instead of replaying a captured CUDA graph")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 steps (0 = skip)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
+    ap.add_argument("--tc-experiment", action="store_true",
+                    help="also time the tensor-core form of the fit's accumulation (mma.sync, "
+                         "3xTF32) against the FP32 CUDA-core kernel on the workload")
     return ap.parse_args()
 
 
@@ -356,7 +359,11 @@ def run_profile(args):
             phb.reorder(plan, pos, lam, U)
         out = torch.empty((8, w.n), dtype=torch.float64, device=dev)
         for _ in range(2):
-            phb.mhd_rhs(plan, prm, pos, lam, U, out=out)
+            if args.tc_experiment:
+                phb.fit_tc_experiment(plan, phb.Params(gamma=w.gamma, refine="off"), pos, lam, U,
+                                      out=out)
+            else:
+                phb.mhd_rhs(plan, prm, pos, lam, U, out=out)
     else:
         plan = phb.Plan.for_workload(w, skin=skin, device=dev, **shape)
         phb.build_neighbors(plan, pos, lam)
@@ -563,6 +570,36 @@ def run_ours(args):
     e1.synchronize()
     build_ms = e0.elapsed_time(e1)
 
+    # ---------------- tensor-core experiment: the accumulation as per-particle
+    # Gram matrices on mma.sync (3xTF32), against the CUDA-core kernel with
+    # the corrected step off (the experiment has none)
+    tc = None
+    if args.tc_experiment:
+        cc_prm = phb.Params(gamma=w.gamma, precision="fp32_mixed", refine="off")
+        cc_out = torch.empty((8, n), dtype=torch.float64, device=dev)
+        phb.mhd_rhs(plan, cc_prm, pos0, lam, U0, out=cc_out)
+        tc_out, gram = phb.fit_tc_experiment(plan, cc_prm, pos0, lam, U0)
+        reps = 10
+        capn = 8 * reps + 8
+        tms, tid = (C.c_float * capn)(), (C.c_int32 * capn)()
+        L.phb_trace_start(capn)
+        for _ in range(reps):
+            flush.zero_()
+            phb.mhd_rhs(plan, cc_prm, pos0, lam, U0, out=cc_out)
+            flush.zero_()
+            phb.fit_tc_experiment(plan, cc_prm, pos0, lam, U0, gram=gram, out=tc_out)
+        ntc = L.phb_trace_stop(tms, tid, capn)
+        by = {k: [tms[i] for i in range(max(ntc, 0)) if tid[i] == k] for k in (1, 6, 7)}
+        diff = (tc_out - cc_out).abs().amax(dim=1) / cc_out.abs().amax(dim=1).clamp_min(1e-300)
+        tc = {"cuda_core_fit_ms": float(np.mean(by[1])) if by[1] else None,
+              "tensor_gram_ms": float(np.mean(by[6])) if by[6] else None,
+              "solve_from_gram_ms": float(np.mean(by[7])) if by[7] else None,
+              "max_rel_diff_vs_cuda_core": float(diff.max().item()),
+              "how": "mma.sync m16n8k8 TF32, operands split hi + lo, 3 products per tile, "
+                     "5 output tiles (lower triangle), one warp per particle in turn; "
+                     "events around each launch, L2 flushed before each call"}
+        del gram, tc_out, cc_out
+
     # ---------------- adjoint (FP64 reverse mode, factorisations recomputed)
     adjoint = None
     if not args.no_adjoint:
@@ -754,6 +791,7 @@ def run_ours(args):
                      "search_ms_in_step": float(np.mean(search_ms)) if search_ms else None,
                      "compaction_ms_in_step": float(np.mean(compact_ms)) if compact_ms else None},
         "adjoint": adjoint,
+        "tc_experiment": tc,
         "adaptivity": adapt,
         "err_vs_oracle": err,
         "routed_to_fp64": routed,

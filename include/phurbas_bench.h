@@ -52,6 +52,21 @@ int phb_workspace_stats(const phb_plan* plan, const void* ws, int32_t* out, int3
                         phb_stream_t stream);
 int phb_trace_stop(float* ms, int32_t* kernel_ids, int32_t capacity);
 
+/* Tensor-core experiment for the fit's accumulation (measurement only; no
+ * other call uses it).  Same result as phb_mhd_rhs in FP32_MIXED with
+ * refine = -1 and no FP64 routing, except that the moments and right-hand
+ * sides of each particle are formed as the Gram matrix A^T W A of its
+ * neighbour rows [p(q_j) | du_j] on the tensor cores: mma.sync m16n8k8 with
+ * TF32 inputs split hi + lo (three products, FP32 accumulation), one warp per
+ * particle in turn.  gram: device float [214][n] scratch (moments, right-hand
+ * sides, neighbour count), gram_bytes >= 214 * 4 * n.  Trace ids 6 (Gram
+ * kernel) and 7 (solve).  Needs plan->tile = 128 and the lists of the last
+ * build; returns a phb_status. */
+int phb_fit_tc_experiment(const phb_plan* plan, const phb_params* params, const double* pos,
+                          const double* lambda, const double* U, void* ws, size_t ws_bytes,
+                          float* gram, size_t gram_bytes, double* dudt, int32_t* status_word,
+                          phb_stream_t stream);
+
 /* Same read-out as phb_trace_stop without destroying the events or disarming
  * the trace.  For launches captured into a CUDA graph while the trace was
  * armed, the event pairs are recorded by the graph at every replay, so a read

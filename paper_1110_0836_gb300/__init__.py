@@ -8,7 +8,8 @@ FP64), the Heun predictor-corrector step, and the hand-written adjoint.
 from ._lib import PhbError  # noqa: F401
 from .api import (FIELDS, Params, Plan, StepGraph, active_at, adapt, adapt_apply,  # noqa: F401
                   adapt_scan, adjoint_record, block_step,
-                  build_neighbors, export_neighbors, kh_mode_amplitude, mhd_rhs, mhd_rhs_active,
+                  build_neighbors, export_neighbors, fit_tc_experiment, kh_mode_amplitude, mhd_rhs,
+                  mhd_rhs_active,
                   mls_derivs, pc_step, reorder,
                   rhs, rhs_adjoint, rhs_adjoint_stored, tensors_of, timestep_levels)
 from .autograd import PhbRHS, rhs_autograd  # noqa: F401

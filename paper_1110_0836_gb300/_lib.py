@@ -28,7 +28,7 @@ EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_chec
            "phb_rhs_adjoint_stored", "phb_mhd_rhs_active", "phb_timestep_levels",
            "phb_struct_sizes", "phb_reorder", "phb_adapt_scan", "phb_adapt_apply",
            "phb_workspace_part", "phb_kh_mode_amplitude", "phb_block_begin",
-           "phb_block_substep"]
+           "phb_block_substep", "phb_fit_tc_experiment"]
 
 
 class Box(C.Structure):
@@ -137,6 +137,9 @@ def lib(path: str | None = None) -> C.CDLL:
     L.phb_block_substep.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, _vp, C.c_int32,
                                     C.c_int32, C.c_double, _vp, C.c_size_t, _vp, _vp]
     L.phb_block_substep.restype = C.c_int
+    L.phb_fit_tc_experiment.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, C.c_size_t, _vp,
+                                        C.c_size_t, _vp, _vp, _vp]
+    L.phb_fit_tc_experiment.restype = C.c_int
     L.phb_workspace_part.argtypes = [P(Plan), C.c_int32, _vp, _vp]
     L.phb_workspace_part.restype = C.c_int
     L.phb_struct_sizes.argtypes = [_vp, C.c_int32]

@@ -435,6 +435,24 @@ def block_step(plan: Plan, params: Params, pos, lam, U, levels, dt_max: float, m
     return anchor
 
 
+def fit_tc_experiment(plan: Plan, params: Params, pos, lam, U, gram=None, out=None):
+    """Right-hand side with the fit's moments and right-hand sides formed on
+    the tensor cores (phb_fit_tc_experiment, a measurement helper): returns
+    (dudt [8, n], gram scratch [214, n])."""
+    n = plan.n
+    _need(pos, (3, n), "pos"), _need(lam, (n,), "lam"), _need(U, (8, n), "U")
+    if gram is None:
+        gram = torch.empty((214, n), dtype=torch.float32, device=pos.device)
+    if out is None:
+        out = torch.empty((8, n), dtype=torch.float64, device=pos.device)
+    pc = params.c()
+    check(_lib.lib().phb_fit_tc_experiment(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam),
+                                           _ptr(U), _ptr(plan.ws), plan.ws.numel(), _ptr(gram),
+                                           gram.numel() * 4, _ptr(out), _ptr(plan.status_word),
+                                           _stream()), "phb_fit_tc_experiment")
+    return out, gram
+
+
 def kh_mode_amplitude(plan: Plan, pos, U, k: float = 4.0 * 3.141592653589793, y0: float = 1.0,
                       ly: float = 4.0):
     """Kelvin-Helmholtz mode amplitude (phb_kh_mode_amplitude): returns a

@@ -23,8 +23,8 @@
 // steep front leak into the quadratic ones (Hessian errors of 4e-4 of their
 // scale at the shear layer).  A tile whose largest estimate exceeds
 // refine_kappa (or every tile, by choice) therefore takes one corrected step
-// after the first solve: all 19 coefficients c0 of every field go to the
-// workspace, one more pass over the neighbours accumulates P^T W r with the
+// after the first solve: all 19 coefficients c0 of every field replace its
+// parked right-hand side, one more pass over the neighbours accumulates P^T W r with the
 // residuals r_j = (U_j - U_i) - p(q_j).c0 recomputed from the records, and the
 // same factor (re-formed from the moments kept in shared memory) solves for
 // the correction.  The error then follows cond(A) = cond(M_s)^(1/2) instead of
@@ -230,23 +230,22 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
 }
 
 // One corrected semi-normal-equations pass for the fields of parked slots
-// [k0, k0 + NFG): c0 (all 19 coefficients, slot order [k][19][n] in the
-// workspace) in registers, residuals r_j = du_j - p(q_j).c0 recomputed from
-// the global records (RawA = RawB there), acc_k = sum_j w_j p(q_j) r_j.
+// [k0, k0 + NFG): c0 (all 19 coefficients, parked in the thread's column) in
+// registers, residuals r_j = du_j - p(q_j).c0 recomputed from the global
+// records (RawA = RawB there), acc_k = sum_j w_j p(q_j) r_j.
 // B selects the record half (false: rho, sigma, Vx, Vy; true: Vz, Bx, By, Bz);
 // du0 is the first du component used.
-template <int NFG, bool B, class Src>
+template <int NFG, bool B, int T, class Src>
 __device__ __forceinline__ void csne_pass(const Src& src, int64_t beg, int64_t end, float inv_l,
-                                          float inv_rf2, bool unweighted, const float* c0,
-                                          int64_t n, int s, int k0, int du0,
-                                          float2 (&acc)[NFG][kNB2]) {
+                                          float inv_rf2, bool unweighted, const float* park,
+                                          int col, int k0, int du0, float2 (&acc)[NFG][kNB2]) {
   float2 c[NFG][kNB2];
 #pragma unroll
   for (int f = 0; f < NFG; ++f)
 #pragma unroll
     for (int j = 0; j < kNB2; ++j) {
-      const float lo = c0[((k0 + f) * kNB + 2 * j) * n + s];
-      const float hi = 2 * j + 1 < kNB ? c0[((k0 + f) * kNB + 2 * j + 1) * n + s] : 0.f;
+      const float lo = park[((k0 + f) * kNB + 2 * j) * T + col];
+      const float hi = 2 * j + 1 < kNB ? park[((k0 + f) * kNB + 2 * j + 1) * T + col] : 0.f;
       c[f][j] = make_float2(lo, hi);
       acc[f][j] = make_float2(0.f, 0.f);
     }
@@ -459,7 +458,9 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
     }
   } else if (solve) {
-    // first solve: all 19 coefficients of every field to the workspace
+    // first solve: all 19 coefficients of every field in place of its parked
+    // right-hand side, and the nine linear and quadratic ones (which the
+    // correction is added to) in the workspace
 #pragma unroll 1
     for (int k = 0; k < G::NF; ++k) {
       float b[kNB];
@@ -468,7 +469,10 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       mls_forward(M, invd, b);
       mls_back19(M, invd, b);
 #pragma unroll
-      for (int j = 0; j < kNB; ++j) a.csne[(k * kNB + j) * static_cast<int64_t>(n) + s] = b[j];
+      for (int j = 0; j < kNB; ++j) park[(k * kNB + j) * T + tid] = b[j];
+#pragma unroll
+      for (int j = kQuad0; j < kNB; ++j)
+        a.csne[(k * 9 + j - kQuad0) * static_cast<int64_t>(n) + s] = b[j];
     }
     // residual passes over the neighbours from the global records: offsets and
     // field differences straight from the hi/lo splits of the particle and the
@@ -482,8 +486,8 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     src.P = P;
     {
       float2 acc[G::NA][kNB2];
-      csne_pass<G::NA, false>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, 0,
-                              4 - G::NA, acc);
+      csne_pass<G::NA, false, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, 0,
+                                 4 - G::NA, acc);
 #pragma unroll
       for (int f = 0; f < G::NA; ++f)
 #pragma unroll
@@ -491,7 +495,7 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     }
     {
       float2 acc[4][kNB2];
-      csne_pass<4, true>(src, beg, end, inv_l, inv_rf2, unweighted, a.csne, n, s, G::NA, 0, acc);
+      csne_pass<4, true, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, G::NA, 0, acc);
 #pragma unroll
       for (int f = 0; f < 4; ++f)
 #pragma unroll
@@ -513,7 +517,8 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       mls_forward(M2, invd2, b);
       mls_back9(M2, invd2, b);
 #pragma unroll
-      for (int j = kQuad0; j < kNB; ++j) b[j] += a.csne[(k * kNB + j) * static_cast<int64_t>(n) + s];
+      for (int j = kQuad0; j < kNB; ++j)
+        b[j] += a.csne[(k * 9 + j - kQuad0) * static_cast<int64_t>(n) + s];
       park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
     }
   }
@@ -604,6 +609,250 @@ __global__ void __launch_bounds__(T, 256 / T) k_fit_mixed_persistent(const FitAr
   }
 }
 
+// ------------------------------------------------------------------------
+// Tensor-core form of the accumulation (a measured experiment, reachable only
+// through phb_fit_tc_experiment).  Per particle the moments and right-hand
+// sides are the Gram matrix G = A^T W A of the rows a_j = [p(q_j) (19 basis
+// monomials) | du_j (7 fitted fields) | 0 (6)], W = diag(w_j): a dense
+// contraction over the neighbours.  One warp forms the Grams of its 32
+// particles in turn: the lanes build 32 neighbour rows at a time in shared
+// memory, then mma.sync m16n8k8 (TF32 inputs, FP32 accumulation) takes them
+// eight rows per step, with each operand split into TF32 hi + lo parts and
+// the three products hi*hi + hi*lo + lo*hi (3xTF32) for FP32-level products.
+// Only the five 16x8 output tiles that hold the lower triangle's moments and
+// right-hand sides are formed.  A second kernel reads them back and runs the
+// same solve and right-hand side as k_fit_mixed (no FP64 routing and no
+// corrected step: the experiment compares the accumulation alone).
+
+constexpr int kTcRow = 33;                    // floats per staged row (32 + 1 pad)
+constexpr int kTcWarpFloats = 32 * kTcRow + 32 + 26 * 26;  // rows, weights, Gram
+constexpr int kTcWords = kNM + 7 * kNB + 1;   // moments, right-hand sides, count
+
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One neighbour row: basis monomials, then the fitted fields' differences in
+// the RHS mode's parked order (sigma, Vx, Vy, Vz, Bx, By, Bz); weight w.
+template <class Src>
+__device__ __forceinline__ void tc_row(const Src& src, int nb, float inv_l, float inv_rf2,
+                                       bool unweighted, float* row, float& w) {
+  float dx, dy, dz, ua[4], ub[4];
+  src.decode_a(src.fetch_a(nb), dx, dy, dz, ua);
+  src.decode_b(src.fetch_b(nb), dx, dy, dz, ub);
+  const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
+  const float sw = 1.f - s2;
+  w = s2 < 1.f ? (unweighted ? 1.f : sw * sw) : 0.f;
+  float qg[kNB];
+  mls_basis(dx * inv_l, dy * inv_l, dz * inv_l, qg);
+#pragma unroll
+  for (int k = 0; k < kNB; ++k) row[k] = qg[k];
+  row[19] = ua[1];
+  row[20] = ua[2];
+  row[21] = ua[3];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) row[22 + f] = ub[f];
+#pragma unroll
+  for (int k = 26; k < 32; ++k) row[k] = 0.f;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T, 2) k_gram_tc(const FitArgs a, const Per32 P, const TileArgs ta,
+                                                  float* __restrict__ gram) {
+  extern __shared__ float4 smem4[];
+  float4* stage = smem4;
+  float* wbuf = reinterpret_cast<float*>(stage + 3 * a.g.stage_cap);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  float* rows = wbuf + warp * kTcWarpFloats;
+  float* wts = rows + 32 * kTcRow;
+  float* G = wts + 32;
+  const int n = a.n, tile = blockIdx.x, s0 = tile * T;
+  const int cnt_tile = min(T, n - s0);
+  const int mine = ta.tmap[static_cast<int64_t>(tile) * T + tid];
+  const bool active = mine < cnt_tile;
+  const int s_own = s0 + mine;
+  const float4* rec = reinterpret_cast<const float4*>(a.rec);
+  const int2 tp = ta.tplan[tile];
+  const bool fb = tp.y != 0;
+  if (!fb) stage_tile<T>(a, P, ta, tile, s0 + (cnt_tile >> 1), tp.x, stage, tid);
+  __syncthreads();
+  const bool unweighted = a.weight_kind == 1;
+  for (int p = 0; p < 32; ++p) {
+    if (!__shfl_sync(0xffffffffu, active, p)) continue;
+    const int s = __shfl_sync(0xffffffffu, s_own, p);
+    const double lam = a.slam[s];
+    const double rf = a.g.rf_factor * lam;
+    const float inv_l = static_cast<float>(1.0 / lam);
+    const float inv_rf2 = static_cast<float>(1.0 / (rf * rf));
+    const int64_t beg = a.off[s];
+    const int64_t end = a.off[s + 1] < a.g.capacity ? a.off[s + 1] : a.g.capacity;
+    StagedSrc ssrc;
+    GlobalSrc gsrc;
+    if (fb) {
+      gsrc.rec = rec;
+      gsrc.idx = a.idx;
+      for (int k = 0; k < 6; ++k) gsrc.o[k] = rec[6 * s + k];
+      gsrc.P = P;
+    } else {
+      ssrc.stage = stage;
+      ssrc.lidx = ta.lidx;
+      const int ls = ta.lself[s];
+      ssrc.me0 = stage[3 * ls];
+      ssrc.me1 = stage[3 * ls + 1];
+      ssrc.me2 = stage[3 * ls + 2];
+      for (int c = 0; c < 3; ++c) {
+        ssrc.len[c] = P.len[c];
+        ssrc.inv_len[c] = P.inv_len[c];
+      }
+    }
+    float acc[5][4];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
+    int inside = 0;
+    for (int64_t c0 = beg; c0 < end; c0 += 32) {
+      const int64_t e = c0 + lane;
+      float w = 0.f;
+      float* row = rows + lane * kTcRow;
+      if (e < end) {
+        if (fb) tc_row(gsrc, gsrc.index(e), inv_l, inv_rf2, unweighted, row, w);
+        else tc_row(ssrc, ssrc.index(e), inv_l, inv_rf2, unweighted, row, w);
+      } else {
+        for (int k = 0; k < 32; ++k) row[k] = 0.f;
+      }
+      wts[lane] = w;
+      inside += __popc(__ballot_sync(0xffffffffu, w > 0.f));
+      __syncwarp();
+      const int nrows = static_cast<int>(end - c0 < 32 ? end - c0 : 32);
+      for (int ks = 0; ks * 8 < nrows; ++ks) {
+        const int r0 = ks * 8 + t, r1 = r0 + 4;
+        const float w0 = wts[r0], w1 = wts[r1];
+        uint32_t ahi[2][4], alo[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const int f = mt * 16 + g;
+          split_tf32(rows[r0 * kTcRow + f], ahi[mt][0], alo[mt][0]);
+          split_tf32(rows[r0 * kTcRow + f + 8], ahi[mt][1], alo[mt][1]);
+          split_tf32(rows[r1 * kTcRow + f], ahi[mt][2], alo[mt][2]);
+          split_tf32(rows[r1 * kTcRow + f + 8], ahi[mt][3], alo[mt][3]);
+        }
+        uint32_t bhi[3][2], blo[3][2];
+#pragma unroll
+        for (int nt = 0; nt < 3; ++nt) {
+          const int f = nt * 8 + g;
+          split_tf32(w0 * rows[r0 * kTcRow + f], bhi[nt][0], blo[nt][0]);
+          split_tf32(w1 * rows[r1 * kTcRow + f], bhi[nt][1], blo[nt][1]);
+        }
+        // tiles (m, n): (0,0) (0,1) (1,0) (1,1) (1,2)
+        constexpr int tm[5] = {0, 0, 1, 1, 1}, tn[5] = {0, 1, 0, 1, 2};
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          mma_tf32(acc[i], ahi[tm[i]], bhi[tn[i]][0], bhi[tn[i]][1]);
+          mma_tf32(acc[i], ahi[tm[i]], blo[tn[i]][0], blo[tn[i]][1]);
+          mma_tf32(acc[i], alo[tm[i]], bhi[tn[i]][0], bhi[tn[i]][1]);
+        }
+      }
+      __syncwarp();
+    }
+    // lower triangle of G from the accumulator fragments
+    {
+      constexpr int tm[5] = {0, 0, 1, 1, 1}, tn[5] = {0, 1, 0, 1, 2};
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = tm[i] * 16 + g + 8 * (q >> 1), c = tn[i] * 8 + 2 * t + (q & 1);
+          if (r < 26 && c <= r) G[r * 26 + c] = acc[i][q];
+        }
+    }
+    __syncwarp();
+    for (int k = lane; k < kTcWords; k += 32) {
+      float v;
+      if (k < kNM) {
+        int r, c;
+        mls_moment_pair(k, r, c);
+        v = G[r * 26 + c];
+      } else if (k < kTcWords - 1) {
+        const int f = (k - kNM) / kNB, j = (k - kNM) % kNB;
+        v = G[(19 + f) * 26 + j];
+      } else {
+        v = static_cast<float>(inside);
+      }
+      gram[static_cast<int64_t>(k) * n + s] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// Solve and right-hand side from the Gram words (thread per slot).
+__global__ void __launch_bounds__(128) k_solve_gram(const FitArgs a, const float* __restrict__ gram) {
+  using G = Groups<FitMode::kRHS>;
+  const int n = a.n;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int64_t N = n;
+  const int dst = a.perm_out ? a.perm_out[s] : s;
+  const float inv_l = static_cast<float>(1.0 / a.slam[s]);
+  const float il = inv_l, il2 = inv_l * inv_l;
+  MhdDerivs<float> D;
+  mhd_zero(D);
+  bool singular = gram[(kTcWords - 1) * N + s] < static_cast<float>(kNB);
+  if (!singular) {
+    float m[kNM], M[kNT], invd[kNB];
+#pragma unroll
+    for (int k = 0; k < kNM; ++k) m[k] = gram[k * N + s];
+    mls_assemble(m, M);
+    singular = !(mls_cholesky<float>(M, invd) > 0.f);
+    if (!singular) {
+#pragma unroll 1
+      for (int k = 0; k < G::NF; ++k) {
+        float b[kNB];
+#pragma unroll
+        for (int j = 0; j < kNB; ++j) b[j] = gram[(kNM + k * kNB + j) * N + s];
+        mls_forward(M, invd, b);
+        mls_back9(M, invd, b);
+        const float gr[3] = {b[kLin0] * il, b[kLin0 + 1] * il, b[kLin0 + 2] * il};
+        const float h[6] = {2.f * b[kQuad0] * il2, b[kQuad0 + 1] * il2, b[kQuad0 + 2] * il2,
+                            2.f * b[kQuad0 + 3] * il2, b[kQuad0 + 4] * il2, 2.f * b[kQuad0 + 5] * il2};
+        mhd_collect(D, G::field(k), gr, h);
+      }
+    }
+  }
+  if (a.fit_status) a.fit_status[dst] = singular ? 1 : 0;
+  if (singular) {
+    mhd_zero(D);
+    raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
+  }
+  const float4* rec = reinterpret_cast<const float4*>(a.rec);
+  const float4 o2 = rec[6 * s + 2], o3 = rec[6 * s + 3], o4 = rec[6 * s + 4], o5 = rec[6 * s + 5];
+  const float u[8] = {o2.x + o3.x, o2.z + o3.z, o2.w + o3.w, o4.x + o5.x,
+                      o4.y + o5.y, o4.z + o5.z, o4.w + o5.w, o2.y + o3.y};
+  const int src = a.perm_in ? a.perm_in[s] : s;
+  const float zeta = a.zeta ? static_cast<float>(a.zeta[src]) : 0.f;
+  const float eta = a.eta ? static_cast<float>(a.eta[src]) : 0.f;
+  float out[8];
+  mhd_rhs(u, D, static_cast<float>(a.gamma), zeta, eta, out);
+  for (int f = 0; f < 8; ++f) a.dudt[f * N + dst] = out[f];
+}
+
 Per32 make_per32(const Grid& g) {
   Per32 P;
   for (int a = 0; a < 3; ++a) {
@@ -669,6 +918,28 @@ cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int2* tplan, 
                           : launch_t<FitMode::kDerivs, 128>(a, P, ta, list_cap, st);
   return a.g.tile == 64 ? launch_t<FitMode::kRHS, 64>(a, P, ta, list_cap, st)
                         : launch_t<FitMode::kRHS, 128>(a, P, ta, list_cap, st);
+}
+
+cudaError_t launch_fit_tc(const FitArgs& a, const int2* tplan, const int32_t* tslot,
+                          const uint16_t* lself, const uint8_t* tmap, const uint16_t* lidx,
+                          float* gram, cudaStream_t st) {
+  if (a.g.tile != 128) return cudaErrorInvalidValue;
+  const Per32 P = make_per32(a.g);
+  const TileArgs ta{tplan, tslot, lself, tmap, lidx, nullptr, nullptr, nullptr,
+                    static_cast<int32_t>((a.n + 127) / 128), nullptr, nullptr};
+  const size_t smem = size_t(a.g.stage_cap) * 3 * sizeof(float4) + 4 * kTcWarpFloats * sizeof(float);
+  cudaFuncSetAttribute(k_gram_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(smem));
+  const unsigned tiles = static_cast<unsigned>((a.n + 127) / 128);
+  int tr = trace_begin(6, st);
+  k_gram_tc<128><<<tiles, 128, smem, st>>>(a, P, ta, gram);
+  note_launch();
+  trace_end(tr, st);
+  tr = trace_begin(7, st);
+  k_solve_gram<<<static_cast<unsigned>((a.n + 127) / 128), 128, 0, st>>>(a, gram);
+  note_launch();
+  trace_end(tr, st);
+  return cudaGetLastError();
 }
 
 }  // namespace phb

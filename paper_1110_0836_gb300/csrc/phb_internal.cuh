@@ -48,7 +48,7 @@ enum Region {
   R_ALIST,       // int32 [n+64] slots of an active subset (ascending)
   R_AFLAG,       // int32 [n+1]  active-subset marks / their exclusive scan
   R_QUEUE,       // int32 [n]    slots routed to FP64
-  R_CSNE,        // float [8][19][n] FP32 coefficients of refined fits (corrected step)
+  R_CSNE,        // float [8][9][n] linear + quadratic coefficients of refined fits' first solve
   R_DIAG,        // double [3][kDiagBlocks] block partial sums of the mode-amplitude diagnostic
   R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
@@ -291,7 +291,8 @@ struct FitArgs {
   // largest conditioning estimate exceeds refine_kappa, 1 every tile
   int32_t refine_mode;
   float refine_kappa;
-  float* csne;                 // [8][19][n] coefficients of the first solve (slot order)
+  float* csne;                 // [8][9][n] linear and quadratic coefficients of the first
+                               // solve (slot order)
   int32_t* refined_tiles;      // count of refined tiles (zeroed before the launch)
 };
 
@@ -302,6 +303,16 @@ cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int2* tplan, 
                              int32_t* fallback_count, const int32_t* order, int32_t* queue_head,
                              const int32_t* list, const int32_t* list_len, int64_t list_cap,
                              cudaStream_t st);
+// Tensor-core experiment: Gram matrices on mma.sync (3xTF32) into gram
+// [214][n], then the solve and right-hand side (tile 128 only).
+cudaError_t launch_fit_tc(const FitArgs& a, const int2* tplan, const int32_t* tslot,
+                          const uint16_t* lself, const uint8_t* tmap, const uint16_t* lidx,
+                          float* gram, cudaStream_t st);
+// Fit arguments of a plan, parameters and workspace (as the fused fits use them).
+FitArgs fit_args(const phb_plan* plan, const phb_params* prm, void* ws, const int32_t* perm_out,
+                 double* dudt, double* grad, double* hess, int32_t* fit_status,
+                 int32_t* status_word);
+
 // FP64 fused fit over all slots (list == null) or over list[0 .. *list_len);
 // routed: the list is the FP32-mixed kernel's route queue (fit status 2).
 cudaError_t launch_fit_fp64(const FitArgs& a, FitMode mode, const int32_t* list,

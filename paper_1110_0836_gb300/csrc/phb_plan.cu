@@ -299,7 +299,7 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   sz[R_ALIST] = size_t(n + 64) * 4;
   sz[R_AFLAG] = size_t(n + 1) * 4;
   sz[R_QUEUE] = (n + 64) * 4;  // also the export's n+1 counts
-  sz[R_CSNE] = size_t(kNF) * 19 * n * 4;
+  sz[R_CSNE] = size_t(kNF) * 9 * n * 4;
   sz[R_DIAG] = size_t(3) * kDiagBlocks * 8;
   size_t off = 0;
   for (int r = R_MISC; r <= R_DIAG; ++r) {

@@ -88,10 +88,9 @@ cudaError_t gather_sorted(const phb_plan* p, const Grid& g, const double* pos, c
   return cudaGetLastError();
 }
 
-cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMode mode,
-                    const int32_t* perm_out, double* dudt, double* grad, double* hess,
-                    int32_t* fit_status, int32_t* status_word, cudaStream_t st,
-                    const int32_t* list, const int32_t* list_len, int64_t list_cap) {
+FitArgs fit_args(const phb_plan* plan, const phb_params* prm, void* ws, const int32_t* perm_out,
+                 double* dudt, double* grad, double* hess, int32_t* fit_status,
+                 int32_t* status_word) {
   FitArgs a;
   a.g = make_grid(plan);
   a.n = static_cast<int32_t>(plan->n);
@@ -122,6 +121,14 @@ cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMo
   a.refine_kappa = static_cast<float>(prm->refine_kappa > 0 ? prm->refine_kappa : 500.0);
   a.csne = region<float>(plan, ws, R_CSNE);
   a.refined_tiles = a.queue_len + 5;
+  return a;
+}
+
+cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMode mode,
+                    const int32_t* perm_out, double* dudt, double* grad, double* hess,
+                    int32_t* fit_status, int32_t* status_word, cudaStream_t st,
+                    const int32_t* list, const int32_t* list_len, int64_t list_cap) {
+  FitArgs a = fit_args(plan, prm, ws, perm_out, dudt, grad, hess, fit_status, status_word);
   cudaError_t e;
   if (prm->precision == PHB_FP64) return launch_fit_fp64(a, mode, list, list_len, st);
   if ((e = cudaMemsetAsync(a.queue_len, 0, sizeof(int32_t), st))) return e;
@@ -207,6 +214,28 @@ extern "C" phb_status phb_mhd_rhs_active(const phb_plan* plan, const phb_params*
   const int64_t cap = n_active < n ? n_active : n;
   e = run_fit(plan, prm, ws, FitMode::kRHS, region<int32_t>(plan, ws, R_PERM), dudt, nullptr,
               nullptr, fit_status, status_word, st, list, list_len, cap);
+  return launch_status(e);
+}
+
+extern "C" int phb_fit_tc_experiment(const phb_plan* plan, const phb_params* prm, const double* pos,
+                                     const double* lambda, const double* U, void* ws,
+                                     size_t ws_bytes, float* gram, size_t gram_bytes, double* dudt,
+                                     int32_t* status_word, phb_stream_t stream) {
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_END_COMMON] : 0);
+  if (s != PHB_OK) return s;
+  if (!prm || !pos || !lambda || !U || !dudt || !gram || plan->tile != 128 ||
+      prm->precision != PHB_FP32_MIXED || (prm->weight_kind != 0 && prm->weight_kind != 1) ||
+      !(prm->gamma > 1.0) || gram_bytes < size_t(80 + 7 * 19 + 1) * 4 * size_t(plan->n))
+    return PHB_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Grid g = make_grid(plan);
+  cudaError_t e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st);
+  if (e) return launch_status(e);
+  const FitArgs a = fit_args(plan, prm, ws, region<int32_t>(plan, ws, R_PERM), dudt, nullptr,
+                             nullptr, nullptr, status_word);
+  e = launch_fit_tc(a, region<int2>(plan, ws, R_TPLAN), region<int32_t>(plan, ws, R_TSLOT),
+                    region<uint16_t>(plan, ws, R_LSELF), region<uint8_t>(plan, ws, R_TMAP),
+                    region<uint16_t>(plan, ws, R_LIDX), gram, st);
   return launch_status(e);
 }
 
