@@ -332,37 +332,6 @@ struct Lin {
 // particle: the particles of one cell then walk identical rows and runs, so a
 // warp's lanes stay together (measured faster than culling, which skips ~20%
 // of the candidates but leaves half the lanes idle).
-// The z cells of a reach row as up to two runs [a0, b0], [a1, b1] of the
-// linear cell order, in the order of the reach offsets (a periodic reach that
-// wraps below reads cells ncz + za .. first, one that wraps above reads
-// za .. ncz - 1 first); returns the number of runs (the first is [a0, b0]).
-__device__ __forceinline__ int z_segments(const Reach& qz, int ncz, int& a0, int& b0, int& a1,
-                                          int& b1) {
-  const int za = qz.start, zb = qz.start + qz.count - 1;
-  a0 = za;
-  b0 = zb;
-  a1 = 0;
-  b1 = -1;
-  if (!qz.wrap) {
-    a0 = max(za, 0);
-    b0 = min(zb, ncz - 1);
-  } else if (za < 0) {  // wraps below: cells ncz + za .., then 0 .. zb
-    a0 = za + ncz;
-    b0 = zb < 0 ? zb + ncz : ncz - 1;
-    b1 = zb < 0 ? -1 : zb;
-  } else if (zb >= ncz) {  // wraps above: cells za .. ncz - 1, then 0 .. zb - ncz
-    a0 = za < ncz ? za : za - ncz;
-    b0 = za < ncz ? ncz - 1 : zb - ncz;
-    b1 = za < ncz ? zb - ncz : -1;
-  }
-  const int nseg = (a0 <= b0 ? 1 : 0) + (a1 <= b1 ? 1 : 0);
-  if (a0 > b0) {
-    a0 = a1;
-    b0 = b1;
-  }
-  return nseg;
-}
-
 template <int OUT, bool kWrap>
 __device__ int search_runs(const Grid& g, const Lin& lin, const double* __restrict__ spos,
                            const Screen& q, const Reach& qx, const Reach& qy, const Reach& qz,
@@ -386,8 +355,23 @@ __device__ int search_runs(const Grid& g, const Lin& lin, const double* __restri
       bool oky;
       const int cy = axis_cell(g, 1, qy, ky, oky);
       if (!oky) continue;
-      int a0, b0, a1, b1;
-      const int nseg = z_segments(qz, ncz, a0, b0, a1, b1);
+      int za = qz.start, zb = qz.start + qz.count - 1;
+      // up to two runs of cells [a0, b0], [a1, b1], in the order of the reach offsets
+      int a0 = za, b0 = zb, a1 = 0, b1 = -1;
+      if (!qz.wrap) {
+        a0 = max(za, 0);
+        b0 = min(zb, ncz - 1);
+      } else if (za < 0) {  // wraps below: cells ncz + za .., then 0 .. zb
+        a0 = za + ncz;
+        b0 = zb < 0 ? zb + ncz : ncz - 1;
+        b1 = zb < 0 ? -1 : zb;
+      } else if (zb >= ncz) {  // wraps above: cells za .. ncz - 1, then 0 .. zb - ncz
+        a0 = za < ncz ? za : za - ncz;
+        b0 = za < ncz ? ncz - 1 : zb - ncz;
+        b1 = za < ncz ? zb - ncz : -1;
+      }
+      const int nseg = (a0 <= b0 ? 1 : 0) + (a1 <= b1 ? 1 : 0);
+      if (a0 > b0) { a0 = a1; b0 = b1; }
       const int64_t row = (static_cast<int64_t>(cx) * g.ncell[1] + cy) * ncz;
       for (int k = 0; k < nseg; ++k) {
         const int t0 = lin.start[row + (k == 0 ? a0 : a1)];
@@ -482,171 +466,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_search_ell(Grid g, const int2* 
   const double r = list_radius(g, slam[s]);
   ncnt[s] = search_particle<kFillEll>(g, clin, lin, cellc, scr, spos, r, s, 0, 0,
                                       ell + static_cast<int64_t>(s) * g.ell);
-}
-
-// Warp per cell (single pass, kFillEll output): the particles of a cell share
-// their candidates, so one warp reads the cell's reach - the rows of the box
-// for the largest list radius among its particles, each row's z cells as
-// runs of the linear-order records - as one list of candidates, 32 at a time
-// (a lane per candidate), and tests every chunk against every particle of
-// the cell; a ballot and a prefix count append each particle's hits in
-// candidate order.  A particle's own reach box is a sub-box of the cell's,
-// read in the same row and run order, and candidates outside it lie beyond
-// its radius, so its list - entries and order - is the one the
-// thread-per-particle search produces.  All lanes stay active whatever the
-// cells' sizes, and each candidate record is read once per cell instead of
-// once per particle.  Cells of more than kCellMax particles, or whose reach
-// covers a whole periodic axis, take the thread-per-particle search.
-constexpr int kCellMax = 64;
-constexpr int kSegMax = 128;
-constexpr int kCellWarps = 8;
-
-struct CellShared {
-  float4 me[kCellMax];
-  float in2[kCellMax], out2[kCellMax];
-  double r2[kCellMax];
-  int seg_t0[kSegMax];       // first record of each run
-  int seg_v0[kSegMax + 1];   // candidate index of each run's first record
-};
-
-template <bool kWrap>
-__device__ __forceinline__ void cell_candidates(const Grid& g, const Lin& lin,
-                                                const double* __restrict__ spos, const Screen& qs,
-                                                const CellShared& sh, int s0, int m, int total,
-                                                int32_t* __restrict__ ncnt,
-                                                int32_t* __restrict__ ell, int lane) {
-  int cnt0 = 0, cnt1 = 0;  // list lengths of the cell's particles lane and lane + 32
-  int seg = 0;             // this lane's run
-  const unsigned below = (1u << lane) - 1u;
-  for (int v0 = 0; v0 < total; v0 += 32) {
-    const int v = v0 + lane;
-    const bool valid = v < total;
-    float4 o = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    if (valid) {
-      while (sh.seg_v0[seg + 1] <= v) ++seg;
-      o = lin.rec[sh.seg_t0[seg] + (v - sh.seg_v0[seg])];
-    }
-    const int t = __float_as_int(o.w);
-    for (int i = 0; i < m; ++i) {
-      const int si = s0 + i;
-      const float d2 = screen_d2<kWrap>(qs, sh.me[i], o);
-      bool hit = false;
-      if (valid && t != si) {
-        hit = d2 < sh.in2[i];
-        if (!hit && d2 <= sh.out2[i]) hit = dist2_exact(g, spos, g.n, si, t) < sh.r2[i];
-      }
-      const unsigned mask = __ballot_sync(0xffffffffu, hit);
-      if (mask) {
-        const int base = __shfl_sync(0xffffffffu, i < 32 ? cnt0 : cnt1, i & 31);
-        if (hit) {
-          const int pos = base + __popc(mask & below);
-          if (pos < g.ell) ell[static_cast<int64_t>(si) * g.ell + pos] = t;
-        }
-        if (lane == (i & 31)) {
-          if (i < 32) cnt0 += __popc(mask);
-          else cnt1 += __popc(mask);
-        }
-      }
-    }
-  }
-  if (lane < m) ncnt[s0 + lane] = cnt0;
-  if (lane + 32 < m) ncnt[s0 + lane + 32] = cnt1;
-}
-
-__global__ void __launch_bounds__(kCellWarps * 32) k_search_cells(
-    Grid g, const int32_t* __restrict__ cstart, int64_t nkeys, const int2* __restrict__ clin,
-    Lin lin, const int32_t* __restrict__ cellc, const float4* __restrict__ scr,
-    const double* __restrict__ spos, const double* __restrict__ slam, int32_t* __restrict__ ncnt,
-    int32_t* __restrict__ ell) {
-  __shared__ CellShared shm[kCellWarps];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t key = static_cast<int64_t>(blockIdx.x) * kCellWarps + wib;
-  if (key == 0 && lane == 0) ncnt[g.n] = 0;  // the offsets scan's sentinel
-  if (key >= nkeys) return;
-  const int s0 = cstart[key], m = cstart[key + 1] - s0;
-  if (m == 0) return;
-  CellShared& sh = shm[wib];
-  int c[3];
-  unpack_cell(cellc[s0], c[0], c[1], c[2]);
-  double rmax = 0.0;
-  if (m <= kCellMax) {
-    for (int i = lane; i < m; i += 32) {
-      const double r = list_radius(g, slam[s0 + i]);
-      const Screen q = make_screen(g, r);
-      sh.me[i] = scr[s0 + i];
-      sh.in2[i] = q.in2;
-      sh.out2[i] = q.out2;
-      sh.r2[i] = q.r2;
-      rmax = r > rmax ? r : rmax;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double x = __shfl_xor_sync(0xffffffffu, rmax, o);
-    rmax = x > rmax ? x : rmax;
-  }
-  const Reach qx = axis_reach(g, 0, c[0], rmax);
-  const Reach qy = axis_reach(g, 1, c[1], rmax);
-  const Reach qz = axis_reach(g, 2, c[2], rmax);
-  const bool whole = (g.periodic[0] && !qx.wrap) || (g.periodic[1] && !qy.wrap) ||
-                     (g.periodic[2] && !qz.wrap);
-  const int nrows = qx.count * qy.count;
-  if (m > kCellMax || whole || 2 * nrows > kSegMax) {
-    for (int i = lane; i < m; i += 32) {
-      const int s = s0 + i;
-      ncnt[s] = search_particle<kFillEll>(g, clin, lin, cellc, scr, spos, list_radius(g, slam[s]),
-                                          s, 0, 0, ell + static_cast<int64_t>(s) * g.ell);
-    }
-    return;
-  }
-  // run table: a lane per reach row (x-major, as the per-particle search
-  // reads them), two runs per row (the second may be empty), their starts
-  // and the candidate index of each run's first record by a warp scan
-  const int ncz = g.ncell[2];
-  int carry = 0;
-  for (int rb = 0; rb < nrows; rb += 32) {
-    const int row = rb + lane;
-    int t0a = 0, la = 0, t0b = 0, lb = 0;
-    if (row < nrows) {
-      bool okx, oky;
-      const int cx = axis_cell(g, 0, qx, row / qy.count, okx);
-      const int cy = axis_cell(g, 1, qy, row % qy.count, oky);
-      if (okx && oky) {
-        int a0, b0, a1, b1;
-        const int nseg = z_segments(qz, ncz, a0, b0, a1, b1);
-        const int64_t base = (static_cast<int64_t>(cx) * g.ncell[1] + cy) * ncz;
-        if (nseg >= 1) {
-          t0a = lin.start[base + a0];
-          la = lin.start[base + b0 + 1] - t0a;
-        }
-        if (nseg == 2) {
-          t0b = lin.start[base + a1];
-          lb = lin.start[base + b1 + 1] - t0b;
-        }
-      }
-    }
-    int inc = la + lb;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += u;
-    }
-    if (row < nrows) {
-      const int v = carry + inc - la - lb;
-      sh.seg_t0[2 * row] = t0a;
-      sh.seg_v0[2 * row] = v;
-      sh.seg_t0[2 * row + 1] = t0b;
-      sh.seg_v0[2 * row + 1] = v + la;
-    }
-    carry += __shfl_sync(0xffffffffu, inc, 31);
-  }
-  if (lane == 0) sh.seg_v0[2 * nrows] = carry;
-  __syncwarp();
-  const Screen qs = make_screen(g, rmax);
-  const bool plain =
-      plain_axis(g, 0, c[0], qx) && plain_axis(g, 1, c[1], qy) && plain_axis(g, 2, c[2], qz);
-  if (plain) cell_candidates<false>(g, lin, spos, qs, sh, s0, m, carry, ncnt, ell, lane);
-  else cell_candidates<true>(g, lin, spos, qs, sh, s0, m, carry, ncnt, ell, lane);
 }
 
 // One CTA per tile: move the tile's lists from the single-pass scratch into
@@ -1202,8 +1021,7 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   const Lin lin{lscr, lstart};
   int32_t* ell = region<int32_t>(p, ws, R_ELL);
   int tr = trace_begin(4, st);
-  k_search_cells<<<static_cast<unsigned>((p->nkeys + kCellWarps - 1) / kCellWarps), kCellWarps * 32,
-                   0, st>>>(g, cell, p->nkeys, clin, lin, cellc, scr, spos, slam, ncnt, ell);
+  k_search_ell<<<blocks_for(n), kThreads, 0, st>>>(g, clin, lin, cellc, scr, spos, slam, ncnt, ell);
   trace_end(tr, st);
   note_launch();
   if ((e = scan_exclusive_i32_to_i64(ncnt, off, n + 1, bsum, st))) return e;

@@ -82,3 +82,16 @@ def test_one_level_equals_the_predictor_corrector_step():
     phb.pc_step(plan, phb.Params(gamma=w.gamma, precision="fp64"), pos, lam, U, dt)
     e = incr_err(pg, ug, pos.cpu().numpy(), U.cpu().numpy(), w.pos, w.U)
     assert e.max() < 1e-12, e
+
+
+def test_substeps_without_active_particles():
+    """Every particle on level 0 of max_level 2: the first three substeps have
+    no particle whose step ends there (nothing is evaluated, the states are
+    only predicted), and the result equals the one-level step of dt_max."""
+    phb = need_gpu()
+    w = workloads.random_modes(10, seed=54, amp=0.05)
+    dt = 0.003
+    p2, u2 = run_gpu(phb, w, np.zeros(w.n, np.int64), dt, 2, "fp64")
+    p0, u0 = run_gpu(phb, w, np.zeros(w.n, np.int64), dt, 0, "fp64")
+    e = incr_err(p2, u2, p0, u0, w.pos, w.U)
+    assert e.max() < 1e-13, e

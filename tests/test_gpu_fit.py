@@ -269,3 +269,61 @@ def test_tile_shapes_and_global_fallback(tile, stage_cap, schedule):
         assert stats["fit_fallback_tiles"] == stats["tiles"] == plan.c.ntiles
     elif tile == 128:
         assert stats["fit_fallback_tiles"] < 0.1 * stats["tiles"]
+
+
+@pytest.mark.parametrize("n", [1, 2, 5])
+def test_tiny_sets_are_singular_everywhere(n):
+    """Fewer particles than basis terms: every fit is singular on both sides,
+    every derivative and time derivative is zero, the status flag is raised,
+    and a predictor-corrector step just advects with V."""
+    phb = need_gpu()
+    from paper_1110_0836_gb300 import _lib
+    rng = np.random.default_rng(n)
+    pos = rng.uniform(0.2, 0.8, size=(3, n))
+    lam = np.full(n, 0.05)
+    U = np.zeros((8, n))
+    U[0], U[7] = 1.0, 1.5
+    U[1:4] = rng.uniform(-0.1, 0.1, size=(3, n))
+    U[4:7] = rng.uniform(-1, 1, size=(3, n))
+    w = workloads.Workload("tiny", np.zeros(3), np.ones(3), np.ones(3, np.int32), pos, lam, U,
+                           5.0 / 3.0)
+    for prec in ("fp64", "fp32_mixed"):
+        out, st, plan = gpu_run(phb, w, phb.Params(gamma=w.gamma, precision=prec))
+        exp, sto = oracle_run(w)
+        assert (sto == 1).all() and (st == 1).all()
+        assert not out.any() and not exp.any()
+        assert plan.read_status() & _lib.FLAG_FIT_SINGULAR
+        plan2 = phb.Plan.for_workload(w, skin=0.01)
+        p, l, u = phb.tensors_of(w)
+        phb.pc_step(plan2, phb.Params(gamma=w.gamma, precision=prec), p, l, u, 0.01)
+        assert np.array_equal(u.cpu().numpy(), U)
+        assert np.allclose(p.cpu().numpy(), pos + 0.01 * U[1:4], rtol=0, atol=1e-15)
+
+
+def test_planar_set_all_fits_singular():
+    """A set on one z plane: every monomial with z vanishes, so the normal
+    matrix is singular for every particle - status 1 and zero derivatives on
+    both sides (the FP32-mixed path routes the failed factorisations to FP64,
+    which declares them singular)."""
+    phb = need_gpu()
+    n_side = 12
+    h = 1.0 / n_side
+    idx = np.arange(n_side) + 0.5
+    X, Y = np.meshgrid(idx * h, idx * h, indexing="ij")
+    rng = np.random.default_rng(3)
+    pos = np.stack([X.ravel(), Y.ravel(), np.full(X.size, 0.5)])
+    pos[:2] += rng.uniform(-0.1 * h, 0.1 * h, size=(2, X.size))
+    n = pos.shape[1]
+    U = np.zeros((8, n))
+    U[0], U[7], U[4] = 1.0, 1.5, 1.0
+    U[1] = 0.01 * np.sin(2 * np.pi * pos[0])
+    # lambda = 1.5 h: ~37 neighbours in the plane, more than the 19 basis
+    # terms, so the singular normal matrix and not the count decides
+    w = workloads.Workload("planar", np.zeros(3), np.ones(3), np.array([1, 1, 0], np.int32), pos,
+                           np.full(n, 1.5 * h), U, 5.0 / 3.0)
+    for prec in ("fp64", "fp32_mixed"):
+        (g, hs), st, plan = gpu_run(phb, w, phb.Params(gamma=w.gamma, precision=prec), "derivs")
+        (go, ho), sto = oracle_run(w, "derivs")
+        assert (sto == 1).all() and (st == 1).all()
+        assert not g.any() and not hs.any()
+        assert plan.neighbor_total() >= 19 * n
