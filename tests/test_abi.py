@@ -145,3 +145,37 @@ def test_default_row_width_follows_the_lambda_range(L):
     assert L.phb_plan_init(C.byref(p)) == 0 and p.ell_width == 128
     p = _plan(lmin=1 / 32, lmax=1 / 16)
     assert L.phb_plan_init(C.byref(p)) == 0 and p.ell_width == 256
+
+
+def test_new_entry_points_reject_bad_arguments_on_host(L):
+    """The block step, the mode-amplitude diagnostic and the tensor-core
+    experiment check their arguments before any CUDA call: a non-null
+    workspace pointer is never dereferenced on these paths."""
+    from paper_1110_0836_gb300 import _lib
+    p = _plan()
+    assert L.phb_plan_init(C.byref(p)) == 0
+    prm = _lib.Params()
+    prm.gamma, prm.precision = 5.0 / 3.0, _lib.PHB_FP64
+    ws, big = C.c_void_p(0x1000), p.ws_bytes
+    arr = C.c_void_p(0x2000)
+    bad = _lib.PHB_ERR_INVALID_ARG
+    sub = L.phb_block_substep
+    # substep index outside [0, 2^max_level), level range, step length
+    assert sub(C.byref(p), C.byref(prm), arr, arr, arr, arr, arr, -1, 2, 0.1, ws, big, None, None) == bad
+    assert sub(C.byref(p), C.byref(prm), arr, arr, arr, arr, arr, 4, 2, 0.1, ws, big, None, None) == bad
+    assert sub(C.byref(p), C.byref(prm), arr, arr, arr, arr, arr, 0, 31, 0.1, ws, big, None, None) == bad
+    assert sub(C.byref(p), C.byref(prm), arr, arr, arr, arr, arr, 0, 2, 0.0, ws, big, None, None) == bad
+    assert sub(C.byref(p), C.byref(prm), arr, arr, arr, None, arr, 0, 2, 0.1, ws, big, None, None) == bad
+    assert sub(C.byref(p), C.byref(prm), arr, arr, arr, arr, arr, 0, 2, 0.1, ws, 16, None, None) == \
+        _lib.PHB_ERR_WORKSPACE
+    assert L.phb_block_begin(C.byref(p), C.byref(prm), arr, arr, arr, None, ws, big, None, None) == bad
+    kh = L.phb_kh_mode_amplitude
+    assert kh(C.byref(p), arr, arr, -1.0, 1.0, 4.0, ws, big, arr, None) == bad
+    assert kh(C.byref(p), arr, arr, 1.0, 1.0, 0.0, ws, big, arr, None) == bad
+    assert kh(C.byref(p), arr, arr, 1.0, float("nan"), 4.0, ws, big, arr, None) == bad
+    tc = L.phb_fit_tc_experiment
+    prm.precision = _lib.PHB_FP64   # the experiment is an FP32-mixed form
+    assert tc(C.byref(p), C.byref(prm), arr, arr, arr, ws, big, arr, 214 * 4 * p.n, arr, None, None) == bad
+    prm.precision = _lib.PHB_FP32_MIXED
+    assert tc(C.byref(p), C.byref(prm), arr, arr, arr, ws, big, arr, 214 * 4 * p.n - 4, arr, None,
+              None) == bad
