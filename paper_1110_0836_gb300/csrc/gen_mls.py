@@ -62,6 +62,83 @@ def split(alpha):
     raise AssertionError(alpha)
 
 
+# Packed moment accumulation.  The 80 moments are held as 40 float2
+# accumulator pairs.  With the weighted basis pairs wp[k] = w qg2[k] (k < 8),
+# degree 2 and 3 are wp[5..7] and wp[0..4] themselves (packed adds), and a
+# packed FMA wp[k] * qg2[j] adds the two monomials (w q^(a_k + a_j),
+# w q^(b_k + b_j)) of pairs k = (a_k, b_k), j = (a_j, b_j).  PAIRED lists the
+# (k, j) products used for degrees 4, 5 and 6: a maximum matching of each
+# degree's moments under such products (5 of 15, 7 of 21 and 9 of 28 pairs;
+# no product pairs xxxy with another moment).  The remaining 22 moments take
+# one scalar FMA each, two to an accumulator pair: 40 packed and 22 scalar
+# instructions instead of 80 scalar ones.
+PAIRED = [(0, 8), (1, 8), (2, 8), (6, 6), (7, 7),
+          (0, 5), (0, 6), (0, 7), (1, 6), (2, 7), (3, 6), (4, 6),
+          (0, 0), (0, 1), (0, 2), (1, 1), (1, 3), (1, 4), (2, 2), (3, 3), (4, 4)]
+NWP = 8  # weighted pairs formed (w q for basis pairs 0..7: cubic and quadratic)
+
+
+def packed_moment_layout():
+    """[(kind, operands, (alpha_x, alpha_y))] per accumulator pair, and alpha -> (pair, half)."""
+    bp = [(BASIS[2 * j], BASIS[2 * j + 1] if 2 * j + 1 < NB else None) for j in range(10)]
+    pairs = [("add", k, bp[k]) for k in (5, 6, 7, 0, 1, 2, 3, 4)]
+    for k, j in PAIRED:
+        h = (add(bp[k][0], bp[j][0]), add(bp[k][1], bp[j][1]))
+        assert h[0] != h[1] and sum(h[0]) == sum(h[1]) >= 4
+        pairs.append(("ffma2", (k, j), h))
+    done = [a for p in pairs for a in p[2]]
+    assert len(done) == len(set(done)) == 58
+    singles = [a for a in MOMENTS if a not in set(done)]
+    assert len(singles) == 22
+    for i in range(0, 22, 2):
+        pairs.append(("single", None, (singles[i], singles[i + 1])))
+    assert len(pairs) == 40
+    pos = {}
+    for p, (_, _, h) in enumerate(pairs):
+        for half, a in enumerate(h):
+            pos[a] = (p, "xy"[half])
+    assert sorted(pos) == sorted(MOMENTS)
+    return pairs, pos
+
+
+def gen_packed_moments(w):
+    pairs, pos = packed_moment_layout()
+    w("constexpr int kNM2 = 40;  // float2 accumulator pairs of the 80 moments (packed layout)")
+    w("constexpr int kNWP = 8;   // weighted basis pairs w qg2[k], k < 8")
+    w("")
+    w("// wp[k] = w qg2[k] for the cubic and quadratic basis pairs.")
+    w("__device__ __forceinline__ void mls_weight_pairs(const float2 (&qg2)[kNB2], float wt, float2 (&wp)[kNWP]) {")
+    w("  const float2 w2 = make_float2(wt, wt);")
+    w("#pragma unroll")
+    w("  for (int k = 0; k < kNWP; ++k) wp[k] = __fmul2_rn(qg2[k], w2);")
+    w("}")
+    w("")
+    w("// m2 += w q^alpha for the 80 moments in the packed layout: 8 packed adds,")
+    w("// 21 packed FMAs and 22 scalar FMAs.")
+    w("__device__ __forceinline__ void mls_accum_moments_p2(const float2 (&qg2)[kNB2], const float2 (&wp)[kNWP], float2 (&m2)[kNM2]) {")
+    for p, (kind, op, h) in enumerate(pairs):
+        if kind == "add":
+            w(f"  m2[{p}] = __fadd2_rn(m2[{p}], wp[{op}]);  // {name(h[0])}, {name(h[1])}")
+        elif kind == "ffma2":
+            w(f"  m2[{p}] = __ffma2_rn(wp[{op[0]}], qg2[{op[1]}], m2[{p}]);  // {name(h[0])}, {name(h[1])}")
+        else:
+            for half, a in zip("xy", h):
+                b, g = split(a)
+                assert b >= 0 and b < 2 * NWP
+                w(f"  m2[{p}].{half} = fmaf(wp[{b // 2}].{'xy'[b % 2]}, qg2[{g // 2}].{'xy'[g % 2]}, m2[{p}].{half});  // {name(a)}")
+    w("}")
+    w("")
+    w("// Normal matrix, packed lower triangle, from the packed moment layout.")
+    w("template <typename MT>")
+    w("__device__ __forceinline__ void mls_assemble_p2(const float2 (&m2)[kNM2], MT& M) {")
+    for r in range(NB):
+        for c in range(r + 1):
+            p, half = pos[add(BASIS[r], BASIS[c])]
+            w(f"  M[{tri(r, c)}] = m2[{p}].{half};")
+    w("}")
+    w("")
+
+
 def tri(r, c):
     """packed lower-triangle index of (r, c), r >= c"""
     return r * (r + 1) // 2 + c
@@ -134,25 +211,6 @@ def gen():
         w(f"  qg2[{j}] = make_float2({exprs[2 * j]}, {exprs[2 * j + 1]});")
     w("}")
     w("")
-    w("// Paired basis plus w and w q^beta for the ten cubic betas (as")
-    w("// mls_monomials_cubic_w; wq[11..19] are not set).")
-    w("__device__ __forceinline__ void mls_monomials_cubic_w2(float x, float y, float z, float wt, float2 (&qg2)[kNB2], float (&wq)[kNB + 1]) {")
-    w("  mls_basis2(x, y, z, qg2);")
-    w("  wq[0] = wt;")
-    for i, e in enumerate(BASIS):
-        if sum(e) == 3:
-            half = "x" if i % 2 == 0 else "y"
-            w(f"  wq[{i + 1}] = wt * qg2[{i // 2}].{half};")
-    w("}")
-    w("")
-    w("// m[alpha] += w q^alpha for the 80 moments, from the paired basis.")
-    w("__device__ __forceinline__ void mls_accum_moments2(const float2 (&qg2)[kNB2], const float (&wq)[kNB + 1], float (&m)[kNM]) {")
-    for a, alpha in enumerate(MOMENTS):
-        b, g = split(alpha)
-        half = "x" if g % 2 == 0 else "y"
-        w(f"  m[{a}] = fmaf(wq[{b + 1}], qg2[{g // 2}].{half}, m[{a}]);  // {name(alpha)}")
-    w("}")
-    w("")
     w("// b2 += q^beta (w du) for the basis pairs: ten packed FP32x2 FMAs (the")
     w("// second half of b2[9] accumulates 0).")
     w("__device__ __forceinline__ void mls_accum_rhs_basis2(const float2 (&qg2)[kNB2], float wdu, float2 (&b2)[kNB2]) {")
@@ -169,6 +227,7 @@ def gen():
     w("  return acc.x + acc.y;")
     w("}")
     w("")
+    gen_packed_moments(w)
     w("// m[alpha] += w q^alpha for the 80 moments.")
     w("template <typename T>")
     w("__device__ __forceinline__ void mls_accum_moments(const T (&qg)[kNB], const T (&wq)[kNB + 1], T (&m)[kNM]) {")

@@ -158,17 +158,17 @@ struct StagedSrc {
 // loaded four neighbours ahead (fetching the neighbours' data ahead as well
 // measured slower: the extra registers cost more than the hidden
 // shared-memory latency).  Both passes fold the weight into the field
-// difference for the right-hand sides, so only w and the ten w q^cubic
-// products the moments need are formed (the moments are complete after
-// pass A).
+// difference for the right-hand sides, so only the eight weighted basis
+// pairs the moments need are formed (the moments, in the packed pair layout,
+// are complete after pass A).
 template <FitMode MODE, int T, class Src>
 __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t end, float inv_l,
                                           float inv_rf2, bool unweighted, float* park, int col,
-                                          float (&m)[kNM], float2 (&bB)[4][kNB2]) {
+                                          float2 (&m2)[kNM2], float2 (&bB)[4][kNB2]) {
   using G = Groups<MODE>;
   int cnt = 0;
 #pragma unroll
-  for (int k = 0; k < kNM; ++k) m[k] = 0.f;
+  for (int k = 0; k < kNM2; ++k) m2[k] = make_float2(0.f, 0.f);
   {
     float2 bA[G::NA][kNB2];
 #pragma unroll
@@ -190,10 +190,10 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
       const float sw = 1.f - s2;
       const float wt = inside ? (unweighted ? 1.f : sw * sw) : 0.f;
       cnt += inside ? 1 : 0;
-      float2 qg2[kNB2];
-      float wq[kNB + 1];
-      mls_monomials_cubic_w2(dx * inv_l, dy * inv_l, dz * inv_l, wt, qg2, wq);
-      mls_accum_moments2(qg2, wq, m);
+      float2 qg2[kNB2], wp[kNWP];
+      mls_basis2(dx * inv_l, dy * inv_l, dz * inv_l, qg2);
+      mls_weight_pairs(qg2, wt, wp);
+      mls_accum_moments_p2(qg2, wp, m2);
       if (MODE == FitMode::kDerivs) mls_accum_rhs_basis2(qg2, wt * du[0], bA[0]);
       mls_accum_rhs_basis2(qg2, wt * du[1], bA[G::NA - 3]);
       mls_accum_rhs_basis2(qg2, wt * du[2], bA[G::NA - 2]);
@@ -377,7 +377,7 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   }
   __syncthreads();
 
-  float m[kNM];
+  float2 m2[kNM2];
   float2 bB[4][kNB2];
   int cnt = 0;
   float inv_l = 1.f, inv_rf2 = 0.f;
@@ -396,7 +396,7 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       src.idx = a.idx;
       for (int k = 0; k < 6; ++k) src.o[k] = rec[6 * s + k];
       src.P = P;
-      cnt = accumulate<MODE, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, m, bB);
+      cnt = accumulate<MODE, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, m2, bB);
     } else {
       StagedSrc src;
       src.stage = stage;
@@ -409,7 +409,7 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
         src.len[c] = P.len[c];
         src.inv_len[c] = P.inv_len[c];
       }
-      cnt = accumulate<MODE, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, m, bB);
+      cnt = accumulate<MODE, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, m2, bB);
     }
   }
   __syncthreads();  // the staged records are dead from here on
@@ -427,8 +427,11 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     if (!singular) {
       if (may_refine)
 #pragma unroll
-        for (int k = 0; k < kNM; ++k) mstash[k * T + tid] = m[k];
-      mls_assemble(m, M);
+        for (int k = 0; k < kNM2; ++k) {
+          mstash[(2 * k) * T + tid] = m2[k].x;
+          mstash[(2 * k + 1) * T + tid] = m2[k].y;
+        }
+      mls_assemble_p2(m2, M);
       const float minpiv = mls_cholesky<float>(M, invd);
       // conditioning estimate of the Jacobi-scaled matrix: n_b times the
       // greedy estimate of ||M_s^-1||_inf (|M_s,rc| <= 1, so ||M_s||_inf <= n_b)
@@ -503,11 +506,12 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     }
     // the same factor again from the kept moments; correction of the linear
     // and quadratic coefficients
-    float mm[kNM];
+    float2 mm[kNM2];
 #pragma unroll
-    for (int k = 0; k < kNM; ++k) mm[k] = mstash[k * T + tid];
+    for (int k = 0; k < kNM2; ++k)
+      mm[k] = make_float2(mstash[(2 * k) * T + tid], mstash[(2 * k + 1) * T + tid]);
     float M2[kNT], invd2[kNB];
-    mls_assemble(mm, M2);
+    mls_assemble_p2(mm, M2);
     mls_cholesky<float>(M2, invd2);
 #pragma unroll 1
     for (int k = 0; k < G::NF; ++k) {
