@@ -56,8 +56,8 @@ KERNEL_FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
 # scaled by the particles processed.  Absent = null.
 FIT_TRAFFIC = {
     "random_modes_64^3": (68603136 + 2836480, "ncu, this workload, one launch"),
-    "shock_tube_1048576": (492951296 + 300872192, "ncu, this workload, one launch"),
-    "shear_layer_8000000": (8 * (473969664 + 285154560),
+    "shock_tube_1048576": (491513856 + 300554496, "ncu, this workload, one launch"),
+    "shear_layer_8000000": (8 * (473792512 + 285099008),
                             "ncu on the 1,000,000-particle set of the same recipe, x 8 "
                             "(particles processed)"),
 }
