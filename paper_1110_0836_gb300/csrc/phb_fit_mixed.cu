@@ -384,10 +384,12 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   int64_t beg = 0, end = 0;
   const bool unweighted = a.weight_kind == 1;
   if (active) {
-    const double lam = a.slam[s];
-    const double rf = a.g.rf_factor * lam;
-    inv_l = static_cast<float>(1.0 / lam);
-    inv_rf2 = static_cast<float>(1.0 / (rf * rf));
+    // the scales in FP32: two FP64 divisions per particle would queue on
+    // GB300's narrow FP64 pipe whenever a CTA's threads start together
+    const float lamf = static_cast<float>(a.slam[s]);
+    const float rff = static_cast<float>(a.g.rf_factor) * lamf;
+    inv_l = 1.f / lamf;
+    inv_rf2 = 1.f / (rff * rff);
     beg = a.off[s];
     end = a.off[s + 1] < a.g.capacity ? a.off[s + 1] : a.g.capacity;
     if (fb) {

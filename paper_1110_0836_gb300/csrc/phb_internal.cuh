@@ -100,16 +100,44 @@ __device__ __forceinline__ void raise_flag(int32_t* status_word, int32_t bits) {
   if (status_word) atomicOr(status_word, bits);
 }
 
+// FP64 finiteness from the exponent bits, on the integer pipe.  GB300's FP64
+// rate is about 1/64 of its FP32 rate, so the bookkeeping kernels keep FP64
+// instructions to the arithmetic that needs them.
+__device__ __forceinline__ bool finite64(double x) {
+  return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
 // Cell coordinate on one axis and the matching wrap count k: with
 // u = floor((x - lo) / cell) (reciprocal cell edge), a periodic axis gives
-// c = u - k nc, k = floor(u / nc) in exact integer-valued FP64, and the
-// wrapped position x - k len lies in cell c up to the rounding of that
-// subtraction - the cell and the wrapped position never disagree by a box
-// length, also for a particle at lo + len exactly.  An open axis clamps c into
-// [0, ncell) with k = 0.  x must be finite.
-__device__ __forceinline__ int cell_wrap(const Grid& g, int a, double x, double& k_out) {
-  const double u = floor((x - g.lo[a]) * g.inv_cell[a]);
+// c = u - k nc, k = floor(u / nc), and the wrapped position x - k len lies in
+// cell c up to the rounding of that subtraction - the cell and the wrapped
+// position never disagree by a box length, also for a particle at lo + len
+// exactly.  An open axis clamps c into [0, ncell) with k = 0.  The scaled
+// position is formed in FP64; for |u| < 2^30 the floor, the wrap and the clamp
+// are integer operations (k_zero: no wrap), further out the same steps run in
+// exact integer-valued FP64.  x must be finite.
+__device__ __forceinline__ int cell_wrap(const Grid& g, int a, double x, double& k_out,
+                                         bool& k_zero) {
+  const double t = (x - g.lo[a]) * g.inv_cell[a];
   const int nc = g.ncell[a];
+  if (((__double2hiint(t) >> 20) & 0x7ff) < 1023 + 30) {
+    const int u = __double2int_rd(t);
+    if (g.periodic[a]) {
+      if (static_cast<unsigned>(u) < static_cast<unsigned>(nc)) {
+        k_zero = true;
+        k_out = 0.0;
+        return u;
+      }
+      const int k = u >= 0 ? u / nc : -((-1 - u) / nc) - 1;
+      k_zero = false;
+      k_out = static_cast<double>(k);
+      return u - k * nc;
+    }
+    k_zero = true;
+    k_out = 0.0;
+    return u < 0 ? 0 : (u >= nc ? nc - 1 : u);
+  }
+  const double u = floor(t);
   if (g.periodic[a]) {
     double k = floor(u * g.inv_ncell[a]);
     double c = u - k * nc;
@@ -121,15 +149,31 @@ __device__ __forceinline__ int cell_wrap(const Grid& g, int a, double x, double&
       k += 1;
     }
     k_out = k;
+    k_zero = false;
     return static_cast<int>(c);
   }
   k_out = 0.0;
+  k_zero = true;
   return u < 0 ? 0 : (u >= nc ? nc - 1 : static_cast<int>(u));
 }
 
 __device__ __forceinline__ int cell_coord(const Grid& g, int a, double x) {
   double k;
-  return cell_wrap(g, a, x, k);
+  bool kz;
+  return cell_wrap(g, a, x, k, kz);
+}
+
+// lambda_min <= l <= lambda_max for lambda_min >= 0, on the integer pipe: the
+// bit patterns of non-negative doubles order like their values; negative
+// values and NaNs fall outside.
+__device__ __forceinline__ bool lambda_in_range(const Grid& g, double l) {
+  const long long b = __double_as_longlong(l);
+  return b >= __double_as_longlong(g.lambda_min) && b <= __double_as_longlong(g.lambda_max);
+}
+
+// FP32 wrapped position x - k len from cell_wrap's outputs.
+__device__ __forceinline__ float wrapped32(const Grid& g, int a, double x, double k, bool k_zero) {
+  return k_zero ? __double2float_rn(x) : static_cast<float>(__dsub_rn(x, __dmul_rn(k, g.len[a])));
 }
 
 // Index of brick (x, y, z) along a 3-D Hilbert curve of order b (2^b bricks per
@@ -238,8 +282,33 @@ cudaError_t gather_sorted(const phb_plan* plan, const Grid& g, const double* pos
 cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const double* lam, void* ws,
                                  int32_t* status_word, cudaStream_t st);
 
-// FP32 hi/lo split of an FP64 value.
+// FP32 hi/lo split of an FP64 value: h = v rounded to FP32, l = (v - h)
+// rounded to FP32 (v - h is exact in FP64).  For 2^-74 <= |v| < 2^127 both
+// come from the bits on the integer pipe - h rounds the 53-bit significand to
+// 24 bits (to nearest, ties to even), l is the signed remainder (|r| <= 2^28)
+// converted once and scaled by a power of two - with the same results as the
+// FP64 form, which serves every other value.
 __device__ __forceinline__ void split_hl(double v, float& h, float& l) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = static_cast<int>((b >> 52) & 0x7ff);
+  if (e >= 949 && e < 1150) {
+    const unsigned long long sig = (b & 0xfffffffffffffull) | (1ull << 52);
+    const unsigned int r = static_cast<unsigned int>(sig & 0x1fffffffull);
+    unsigned long long q = sig >> 29;
+    q += (r > 0x10000000u || (r == 0x10000000u && (q & 1ull))) ? 1ull : 0ull;
+    const int rem = static_cast<int>(static_cast<long long>(sig) - static_cast<long long>(q << 29));
+    unsigned int qh = static_cast<unsigned int>(q);
+    int eh = e - 1023;
+    if (qh == (1u << 24)) {
+      qh >>= 1;
+      eh += 1;
+    }
+    const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
+    h = __uint_as_float(sign | (static_cast<unsigned int>(eh + 127) << 23) | (qh & 0x7fffffu));
+    const float lm = __int2float_rn(rem) * __uint_as_float(static_cast<unsigned int>(e - 948) << 23);
+    l = rem == 0 ? 0.f : (sign ? -lm : lm);
+    return;
+  }
   h = __double2float_rn(v);
   l = __double2float_rn(v - static_cast<double>(h));
 }

@@ -25,13 +25,14 @@ __global__ void k_keys(Grid g, const double* __restrict__ pos, const double* __r
   int c[3];
   bool finite = true;
   for (int a = 0; a < 3; ++a) {
-    double x = pos[a * n + i];
-    finite &= isfinite(x);
-    c[a] = isfinite(x) ? cell_coord(g, a, x) : 0;
+    const double x = pos[a * n + i];
+    const bool f = finite64(x);
+    finite &= f;
+    c[a] = f ? cell_coord(g, a, x) : 0;
   }
   const double l = lam[i];
-  if (!finite || !isfinite(l)) raise_flag(status_word, PHB_FLAG_NONFINITE);
-  if (!(l >= g.lambda_min && l <= g.lambda_max)) raise_flag(status_word, PHB_FLAG_LAMBDA_RANGE);
+  if (!finite || !finite64(l)) raise_flag(status_word, PHB_FLAG_NONFINITE);
+  if (!lambda_in_range(g, l)) raise_flag(status_word, PHB_FLAG_LAMBDA_RANGE);
   const int32_t k = cell_key(g, c[0], c[1], c[2]);
   keys[i] = k;
   atomicAdd(&counts[k], 1);
@@ -78,8 +79,9 @@ __global__ void k_gather_pos(Grid g, const int32_t* __restrict__ perm, const dou
     const double x = pos[a * n + i];
     spos[a * n + s] = x;
     double k = 0.0;
-    c[a] = isfinite(x) ? cell_wrap(g, a, x, k) : 0;
-    w[a] = static_cast<float>(__dsub_rn(x, __dmul_rn(k, g.len[a])));
+    bool kz = true;
+    c[a] = finite64(x) ? cell_wrap(g, a, x, k, kz) : 0;
+    w[a] = wrapped32(g, a, x, k, kz);
   }
   slam[s] = lam[i];
   scr[s] = make_float4(w[0], w[1], w[2], 0.f);
@@ -643,8 +645,9 @@ __global__ void k_adapt_gather(Grid g, const int32_t* __restrict__ perm, const d
     const double x = pos[a * n + i];
     spos[a * n + s] = x;
     double k = 0.0;
-    if (isfinite(x)) cell_wrap(g, a, x, k);
-    w[a] = static_cast<float>(__dsub_rn(x, __dmul_rn(k, g.len[a])));
+    bool kz = true;
+    if (finite64(x)) cell_wrap(g, a, x, k, kz);
+    w[a] = wrapped32(g, a, x, k, kz);
   }
   slam[s] = lam[i];
   scr[s] = make_float4(w[0], w[1], w[2], 0.f);

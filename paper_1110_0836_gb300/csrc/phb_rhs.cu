@@ -21,15 +21,15 @@ __global__ void k_gather_all(Grid g, const int32_t* __restrict__ perm, const dou
   for (int a = 0; a < 3; ++a) {
     x[a] = pos[a * static_cast<int64_t>(n) + i];
     spos[a * static_cast<int64_t>(n) + s] = x[a];
-    finite &= isfinite(x[a]);
+    finite &= finite64(x[a]);
   }
   const double l = lam[i];
   slam[s] = l;
-  if (!(l >= g.lambda_min && l <= g.lambda_max)) raise_flag(status_word, PHB_FLAG_LAMBDA_RANGE);
+  if (!lambda_in_range(g, l)) raise_flag(status_word, PHB_FLAG_LAMBDA_RANGE);
   for (int f = 0; f < 8; ++f) {
     u[f] = U ? U[f * static_cast<int64_t>(n) + i] : 0.0;
     sU[f * static_cast<int64_t>(n) + s] = u[f];
-    finite &= isfinite(u[f]);
+    finite &= finite64(u[f]);
   }
   if (!finite) raise_flag(status_word, PHB_FLAG_NONFINITE);
   write_record(rec, s, x, u);
