@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(kT, 1) k_fit_fp64(const FitArgs a, int routed,
   const int lane = threadIdx.x % lanes;
   const int groups = kT / lanes;
   const int grp = threadIdx.x / lanes;
+  // a block without work (an empty or short routed queue) leaves before any
+  // FP64 set-up
+  if (static_cast<int64_t>(blockIdx.x) * groups >= total) return;
   double* my = sm + threadIdx.x * kStride;
   double* head = sm + grp * lanes * kStride;  // the group's lane 0 region: totals, factor, c
   double(&mom)[kNM] = *reinterpret_cast<double(*)[kNM]>(my);

@@ -78,6 +78,7 @@ __host__ __device__ inline const T* region(const phb_plan* p, const void* ws, Re
 // Plain-old-data view of the plan handed to kernels by value.
 struct Grid {
   double lo[3], len[3], inv_cell[3], cell[3], inv_ncell[3];
+  float lenf[3], inv_lenf[3];  // FP32 box lengths and (periodic axes) their reciprocals, else 0
   int32_t periodic[3], ncell[3], nbrick[3];
   int32_t hbits;      // Hilbert order of the brick curve
   int32_t tile;       // particles per tile
@@ -116,6 +117,9 @@ __device__ __forceinline__ bool finite64(double x) {
 // position is formed in FP64; for |u| < 2^30 the floor, the wrap and the clamp
 // are integer operations (k_zero: no wrap), further out the same steps run in
 // exact integer-valued FP64.  x must be finite.
+static __device__ __noinline__ int cell_wrap_fp64(const Grid& g, int a, double t, double& k_out,
+                                                 bool& k_zero);
+
 __device__ __forceinline__ int cell_wrap(const Grid& g, int a, double x, double& k_out,
                                          bool& k_zero) {
   const double t = (x - g.lo[a]) * g.inv_cell[a];
@@ -137,6 +141,14 @@ __device__ __forceinline__ int cell_wrap(const Grid& g, int a, double x, double&
     k_out = 0.0;
     return u < 0 ? 0 : (u >= nc ? nc - 1 : u);
   }
+  return cell_wrap_fp64(g, a, t, k_out, k_zero);
+}
+
+// cell_wrap far outside the box, out of line (not run predicated for every
+// position).
+static __device__ __noinline__ int cell_wrap_fp64(const Grid& g, int a, double t, double& k_out,
+                                                 bool& k_zero) {
+  const int nc = g.ncell[a];
   const double u = floor(t);
   if (g.periodic[a]) {
     double k = floor(u * g.inv_ncell[a]);
@@ -171,9 +183,15 @@ __device__ __forceinline__ bool lambda_in_range(const Grid& g, double l) {
   return b >= __double_as_longlong(g.lambda_min) && b <= __double_as_longlong(g.lambda_max);
 }
 
-// FP32 wrapped position x - k len from cell_wrap's outputs.
+// FP32 wrapped position x - k len from cell_wrap's outputs (the wrapped case
+// out of line).
+static __device__ __noinline__ float wrapped32_shift(const Grid& g, int a, double x, double k) {
+  return static_cast<float>(__dsub_rn(x, __dmul_rn(k, g.len[a])));
+}
+
 __device__ __forceinline__ float wrapped32(const Grid& g, int a, double x, double k, bool k_zero) {
-  return k_zero ? __double2float_rn(x) : static_cast<float>(__dsub_rn(x, __dmul_rn(k, g.len[a])));
+  if (k_zero) return __double2float_rn(x);
+  return wrapped32_shift(g, a, x, k);
 }
 
 // Index of brick (x, y, z) along a 3-D Hilbert curve of order b (2^b bricks per
@@ -274,43 +292,60 @@ phb_status check_common(const phb_plan* plan, const void* ws, size_t ws_bytes, s
 phb_status launch_status(cudaError_t e);
 
 // Gather caller-order pos, lambda, U into slot order (FP64 copies and FP32
-// hi/lo records).  U may be NULL (positions only).
+// hi/lo records).  U may be NULL (positions only).  y0, if not NULL, gets a
+// second slot-order copy of (x, U) ([11][n]; the predictor-corrector's Y^n).
 cudaError_t gather_sorted(const phb_plan* plan, const Grid& g, const double* pos,
                           const double* lambda, const double* U, void* ws, int32_t* status_word,
-                          cudaStream_t st);
+                          cudaStream_t st, double* y0 = nullptr);
 
 cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const double* lam, void* ws,
                                  int32_t* status_word, cudaStream_t st);
 
 // FP32 hi/lo split of an FP64 value: h = v rounded to FP32, l = (v - h)
 // rounded to FP32 (v - h is exact in FP64).  For 2^-74 <= |v| < 2^127 both
-// come from the bits on the integer pipe - h rounds the 53-bit significand to
-// 24 bits (to nearest, ties to even), l is the signed remainder (|r| <= 2^28)
-// converted once and scaled by a power of two - with the same results as the
-// FP64 form, which serves every other value.
-__device__ __forceinline__ void split_hl(double v, float& h, float& l) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-  const int e = static_cast<int>((b >> 52) & 0x7ff);
-  if (e >= 949 && e < 1150) {
-    const unsigned long long sig = (b & 0xfffffffffffffull) | (1ull << 52);
-    const unsigned int r = static_cast<unsigned int>(sig & 0x1fffffffull);
-    unsigned long long q = sig >> 29;
-    q += (r > 0x10000000u || (r == 0x10000000u && (q & 1ull))) ? 1ull : 0ull;
-    const int rem = static_cast<int>(static_cast<long long>(sig) - static_cast<long long>(q << 29));
-    unsigned int qh = static_cast<unsigned int>(q);
-    int eh = e - 1023;
-    if (qh == (1u << 24)) {
-      qh >>= 1;
-      eh += 1;
-    }
-    const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
-    h = __uint_as_float(sign | (static_cast<unsigned int>(eh + 127) << 23) | (qh & 0x7fffffu));
-    const float lm = __int2float_rn(rem) * __uint_as_float(static_cast<unsigned int>(e - 948) << 23);
-    l = rem == 0 ? 0.f : (sign ? -lm : lm);
-    return;
-  }
+// come from the two 32-bit words of v with integer and FP32 operations only:
+// h rounds the 53-bit significand to 24 bits (to nearest, ties to even); the
+// signed remainder r (|r| <= 2^28, in units of v's last significand bit) is
+// rounded once by one FMA of its exact high and low 14-bit parts and scaled
+// by a power of two.  The results equal the FP64 form's, which serves zero
+// and every other value.
+__device__ __forceinline__ float exact_small_float(unsigned int m) {
+  // m < 2^23 as an FP32 value, exactly: 2^23 + m has m in its significand
+  return __uint_as_float(0x4b000000u | m) - 8388608.f;
+}
+
+// The FP64 form, out of line: inlined, the compiler would run it predicated
+// for every value.
+static __device__ __noinline__ void split_hl_fp64(double v, float& h, float& l) {
   h = __double2float_rn(v);
   l = __double2float_rn(v - static_cast<double>(h));
+}
+
+__device__ __forceinline__ void split_hl(double v, float& h, float& l) {
+  const unsigned int hw = static_cast<unsigned int>(__double2hiint(v));
+  const unsigned int lw = static_cast<unsigned int>(__double2loint(v));
+  const int e = static_cast<int>((hw >> 20) & 0x7ffu);
+  if (e >= 949 && e < 1150) {
+    unsigned int q = 0x800000u | ((hw & 0xfffffu) << 3) | (lw >> 29);  // leading 24 bits
+    const unsigned int r = lw & 0x1fffffffu;                           // the other 29
+    const bool up = r > 0x10000000u || (r == 0x10000000u && (q & 1u));
+    const unsigned int mag = up ? 0x20000000u - r : r;  // |remainder| <= 2^28
+    q += up ? 1u : 0u;
+    int eh = e - 1023;
+    if (q == 0x1000000u) {
+      q >>= 1;
+      eh += 1;
+    }
+    const unsigned int sign = hw & 0x80000000u;
+    h = __uint_as_float(sign | (static_cast<unsigned int>(eh + 127) << 23) | (q & 0x7fffffu));
+    // the remainder's sign is the value's when rounded down, the opposite when rounded up
+    const float rm = fmaf(exact_small_float(mag >> 14), 16384.f, exact_small_float(mag & 0x3fffu));
+    const float lm = rm * __uint_as_float(static_cast<unsigned int>(e - 948) << 23);
+    const bool neg = (sign != 0u) != up;
+    l = mag == 0u ? 0.f : (neg ? -lm : lm);
+    return;
+  }
+  split_hl_fp64(v, h, l);
 }
 
 // Write the 6-float4 record of slot s: (xh,yh,zh,0) (xl,yl,zl,0)

@@ -176,8 +176,8 @@ __device__ __forceinline__ Screen make_screen(const Grid& g, double r) {
   q.in2 = static_cast<float>(r > m ? (r - m) * (r - m) : 0.0);
   q.out2 = static_cast<float>((r + m) * (r + m));
   for (int a = 0; a < 3; ++a) {
-    q.lenf[a] = static_cast<float>(g.len[a]);
-    q.invlf[a] = g.periodic[a] ? static_cast<float>(1.0 / g.len[a]) : 0.f;
+    q.lenf[a] = g.lenf[a];
+    q.invlf[a] = g.inv_lenf[a];  // formed on the host: no FP64 division per particle
   }
   return q;
 }

@@ -85,10 +85,7 @@ extern "C" phb_status phb_pc_step(const phb_plan* plan, const phb_params* prm, d
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   cudaError_t e;
   if ((e = build_neighbors_impl(plan, pos, lambda, ws, status_word, st))) return launch_status(e);
-  if ((e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st))) return launch_status(e);
-  if ((e = cudaMemcpyAsync(y0, spos, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, st)))
-    return launch_status(e);
-  if ((e = cudaMemcpyAsync(y0 + 3 * N, sU, 8 * N * sizeof(double), cudaMemcpyDeviceToDevice, st)))
+  if ((e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st, y0)))
     return launch_status(e);
   if ((e = run_fit(plan, prm, ws, FitMode::kRHS, nullptr, f0, nullptr, nullptr, nullptr,
                    status_word, st)))

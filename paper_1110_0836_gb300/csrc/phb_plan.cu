@@ -26,6 +26,8 @@ Grid make_grid(const phb_plan* p) {
     g.inv_ncell[a] = 1.0 / p->ncell[a];
     g.cell[a] = p->cell[a];
     g.periodic[a] = p->box.periodic[a] ? 1 : 0;
+    g.lenf[a] = static_cast<float>(p->box.len[a]);
+    g.inv_lenf[a] = p->box.periodic[a] ? static_cast<float>(1.0 / p->box.len[a]) : 0.f;
     g.ncell[a] = p->ncell[a];
     g.nbrick[a] = p->nbrick[a];
   }

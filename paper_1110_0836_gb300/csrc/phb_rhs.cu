@@ -11,7 +11,7 @@ __global__ void k_gather_all(Grid g, const int32_t* __restrict__ perm, const dou
                              const double* __restrict__ lam, const double* __restrict__ U,
                              double* __restrict__ spos, double* __restrict__ slam,
                              double* __restrict__ sU, float* __restrict__ rec,
-                             int32_t* status_word) {
+                             int32_t* status_word, double* __restrict__ y0) {
   const int n = g.n;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
@@ -21,6 +21,7 @@ __global__ void k_gather_all(Grid g, const int32_t* __restrict__ perm, const dou
   for (int a = 0; a < 3; ++a) {
     x[a] = pos[a * static_cast<int64_t>(n) + i];
     spos[a * static_cast<int64_t>(n) + s] = x[a];
+    if (y0) y0[a * static_cast<int64_t>(n) + s] = x[a];
     finite &= finite64(x[a]);
   }
   const double l = lam[i];
@@ -29,6 +30,7 @@ __global__ void k_gather_all(Grid g, const int32_t* __restrict__ perm, const dou
   for (int f = 0; f < 8; ++f) {
     u[f] = U ? U[f * static_cast<int64_t>(n) + i] : 0.0;
     sU[f * static_cast<int64_t>(n) + s] = u[f];
+    if (y0) y0[(3 + f) * static_cast<int64_t>(n) + s] = u[f];
     finite &= finite64(u[f]);
   }
   if (!finite) raise_flag(status_word, PHB_FLAG_NONFINITE);
@@ -79,11 +81,12 @@ cudaError_t run_fit_marked(const phb_plan* plan, const phb_params* prm, void* ws
 }
 
 cudaError_t gather_sorted(const phb_plan* p, const Grid& g, const double* pos, const double* lam,
-                          const double* U, void* ws, int32_t* status_word, cudaStream_t st) {
+                          const double* U, void* ws, int32_t* status_word, cudaStream_t st,
+                          double* y0) {
   k_gather_all<<<static_cast<unsigned>((g.n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
       g, region<int32_t>(p, ws, R_PERM), pos, lam, U, region<double>(p, ws, R_SPOS),
       region<double>(p, ws, R_SLAM), region<double>(p, ws, R_SU), region<float>(p, ws, R_REC),
-      status_word);
+      status_word, y0);
   note_launch();
   return cudaGetLastError();
 }
