@@ -674,33 +674,27 @@ def run_ours(args):
              "readings": "9^3 test grid, d_v = lambda, clumps closer than lambda/4"}
     del scan, gder, hder, applied
 
-    # ---------------- end to end through the API with host buffers
+    # ---------------- end to end through the API with host buffers: phb_pc_step_host
+    # uploads pos and lambda, then U on a side stream while the lists are built,
+    # steps, and downloads the new pos and U (all inside the timed region)
     hpos = pos0.cpu().pin_memory()
     hlam = lam.cpu().pin_memory()
     hU = U0.cpu().pin_memory()
     opos = torch.empty_like(hpos).pin_memory()
     oU = torch.empty_like(hU).pin_memory()
-    dpos, dlam, dU = pos0.clone(), lam.clone(), U0.clone()
     e2e_graph = None
     if not args.no_graph:
-        # the same captured step as the timed region, on the e2e device buffers
-        phb.build_neighbors(plan, dpos, dlam)
-        e2e_graph = phb.StepGraph(plan, mixed, dpos, dlam, dU, dt)
+        e2e_graph = phb.HostStepGraph(plan, mixed, hpos, hlam, hU, dt, opos, oU)
     k_e2e = max(3, min(args.steps, 10))
     te = []
     for _ in range(k_e2e):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dpos.copy_(hpos, non_blocking=True)
-        dlam.copy_(hlam, non_blocking=True)
-        dU.copy_(hU, non_blocking=True)
         if e2e_graph is not None:
             e2e_graph.replay()
         else:
-            phb.pc_step(plan, mixed, dpos, dlam, dU, dt)
-        opos.copy_(dpos, non_blocking=True)
-        oU.copy_(dU, non_blocking=True)
+            phb.pc_step_host(plan, mixed, hpos, hlam, hU, dt, opos, oU)
         torch.cuda.synchronize()
         te.append(time.perf_counter() - t0)
     status = plan.read_status()
@@ -711,9 +705,11 @@ def run_ours(args):
     e2e = {"value": world * 2 * n / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(hpos.numel() + hlam.numel() + hU.numel()) * 8,
            "d2h_bytes_per_step": int(opos.numel() + oU.numel()) * 8,
-           "path": "pinned host -> device copies, the predictor-corrector step (StepGraph replay, "
-                   "or phb_pc_step with --no-graph), device -> pinned host; host wall clock around "
-                   "each step with a synchronize on both sides"}
+           "path": "phb_pc_step_host on pinned host arrays: pos and lambda uploaded, U uploaded "
+                   "on a side stream during the neighbour build, the predictor-corrector step, "
+                   "the new pos and U downloaded (HostStepGraph replay, or the eager call with "
+                   "--no-graph); host wall clock around each step with a synchronize on both "
+                   "sides"}
 
     # ---------------- measured FMA peaks (project probe) and the FP64 path's roofline
     p32 = fma_peak_tflops(L, dev, 1, sm_count)

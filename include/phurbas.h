@@ -328,6 +328,22 @@ phb_status phb_pc_step(const phb_plan* plan, const phb_params* params, double* p
                        const double* lambda, double* U, double dt, void* ws, size_t ws_bytes,
                        int32_t* status_word, phb_stream_t stream);
 
+/* phb_pc_step on HOST arrays: pos_in [3][n], lambda_in [n], U_in [8][n]
+ * (caller order, page-locked for the copies to run asynchronously) are copied
+ * to the workspace's step part, stepped as by phb_pc_step, and x^{n+1}, U^{n+1}
+ * copied back to pos_out [3][n] and U_out [8][n] (host; they may be pos_in and
+ * U_in).  The positions and lambda go first; U follows on a side stream (one
+ * per device, made on first use and kept) while the neighbour lists are built,
+ * and the stream waits for it before U is read.  All of it is ordered on
+ * `stream`: the outputs are valid once the stream has reached this point (a
+ * synchronisation, an event).  Capturable in a CUDA graph after one eager
+ * call.  Same results and status as phb_pc_step; PHB_ERR_INVALID_ARG also for
+ * a NULL output. */
+phb_status phb_pc_step_host(const phb_plan* plan, const phb_params* params, const double* pos_in,
+                            const double* lambda_in, const double* U_in, double* pos_out,
+                            double* U_out, double dt, void* ws, size_t ws_bytes,
+                            int32_t* status_word, phb_stream_t stream);
+
 /* Right-hand side of an active subset only (the individual time steps of
  * Sec. 2 / Sec. 2.1: at a substep only the particles whose step ends there
  * are evaluated).  Same result as phb_mhd_rhs at the listed particles, with

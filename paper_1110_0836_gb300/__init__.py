@@ -6,11 +6,12 @@ fit + ideal-MHD Lagrangian right-hand side (FP32-mixed with FP64 routing, or
 FP64), the Heun predictor-corrector step, and the hand-written adjoint.
 """
 from ._lib import PhbError  # noqa: F401
-from .api import (FIELDS, Params, Plan, StepGraph, active_at, adapt, adapt_apply,  # noqa: F401
+from .api import (FIELDS, HostStepGraph, Params, Plan, StepGraph, active_at, adapt,  # noqa: F401
+                  adapt_apply,
                   adapt_scan, adjoint_record, block_step,
                   build_neighbors, export_neighbors, fit_tc_experiment, kh_mode_amplitude, mhd_rhs,
                   mhd_rhs_active,
-                  mls_derivs, pc_step, reorder,
+                  mls_derivs, pc_step, pc_step_host, reorder,
                   rhs, rhs_adjoint, rhs_adjoint_stored, tensors_of, timestep_levels)
 from .autograd import PhbRHS, rhs_autograd  # noqa: F401
 

@@ -28,7 +28,7 @@ EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_chec
            "phb_rhs_adjoint_stored", "phb_mhd_rhs_active", "phb_timestep_levels",
            "phb_struct_sizes", "phb_reorder", "phb_adapt_scan", "phb_adapt_apply",
            "phb_workspace_part", "phb_kh_mode_amplitude", "phb_block_begin",
-           "phb_block_substep", "phb_fit_tc_experiment"]
+           "phb_block_substep", "phb_fit_tc_experiment", "phb_pc_step_host"]
 
 
 class Box(C.Structure):
@@ -91,6 +91,8 @@ def lib(path: str | None = None) -> C.CDLL:
     L.phb_mhd_rhs.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, C.c_size_t, _vp, _vp, _vp, _vp]
     L.phb_pc_step.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, C.c_double, _vp, C.c_size_t, _vp,
                               _vp]
+    L.phb_pc_step_host.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, _vp, C.c_double, _vp,
+                                   C.c_size_t, _vp, _vp]
     L.phb_rhs_adjoint.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp, _vp,
                                   _vp, _vp]
     L.phb_mhd_rhs_active.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, C.c_int64, _vp,
@@ -150,7 +152,7 @@ def lib(path: str | None = None) -> C.CDLL:
         raise RuntimeError(f"{p}: struct sizes {tuple(sizes)} differ from the binding's "
                            f"{(C.sizeof(Box), C.sizeof(Params), C.sizeof(Plan))}; rebuild")
     for f in ("phb_plan_init", "phb_check", "phb_build_neighbors", "phb_export_neighbors",
-              "phb_mls_derivs", "phb_mhd_rhs", "phb_pc_step", "phb_rhs_adjoint"):
+              "phb_mls_derivs", "phb_mhd_rhs", "phb_pc_step", "phb_pc_step_host", "phb_rhs_adjoint"):
         getattr(L, f).restype = C.c_int
     if path is None:
         _LIB = L

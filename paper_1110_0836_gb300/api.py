@@ -305,6 +305,33 @@ def pc_step(plan: Plan, params: Params, pos, lam, U, dt: float):
                                  _stream()), "phb_pc_step")
 
 
+def _need_host(t, shape, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != torch.float64 or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name}: expected contiguous float64 {tuple(shape)}, got {t.dtype} "
+                         f"{tuple(t.shape)}")
+    return t
+
+
+def pc_step_host(plan: Plan, params: Params, pos, lam, U, dt: float, pos_out=None, U_out=None):
+    """One predictor-corrector step on host tensors (phb_pc_step_host): pos [3, n], lam [n],
+    U [8, n] on the CPU (pinned for asynchronous copies) are uploaded, stepped and the new
+    pos and U written to pos_out / U_out (default: in place).  Asynchronous on the current
+    stream: synchronise before reading the outputs."""
+    n = plan.n
+    _need_host(pos, (3, n), "pos"), _need_host(lam, (n,), "lam"), _need_host(U, (8, n), "U")
+    pos_out = pos if pos_out is None else _need_host(pos_out, (3, n), "pos_out")
+    U_out = U if U_out is None else _need_host(U_out, (8, n), "U_out")
+    if params.frozen is not None:
+        _need(params.frozen, (n,), "frozen", params.frozen.dtype)
+    pc = params.c()
+    check(_lib.lib().phb_pc_step_host(C.byref(plan.c), C.byref(pc), _ptr(pos), _ptr(lam), _ptr(U),
+                                      _ptr(pos_out), _ptr(U_out), float(dt), _ptr(plan.ws),
+                                      plan.ws.numel(), _ptr(plan.status_word), _stream()),
+          "phb_pc_step_host")
+
+
 def rhs_adjoint(plan: Plan, params: Params, pos, lam, U, gbar, Ubar=None, xbar=None):
     """dL/dU [8, n] and dL/dpos [3, n] for gbar = dL/d(dudt) (phb_rhs_adjoint), with the
     neighbour lists of the last build held fixed."""
@@ -512,4 +539,29 @@ class StepGraph:
 
     def replay(self):
         """Advance pos and U by `steps` steps in place (asynchronous)."""
+        self.graph.replay()
+
+
+class HostStepGraph:
+    """CUDA graph of one predictor-corrector step on host tensors (phb_pc_step_host):
+    the uploads of pos, lam and U (U overlapped with the neighbour build), the step and
+    the downloads of the new pos and U to pos_out / U_out, captured once after one eager
+    step (which also makes the library's side stream) and replayed on the current stream.
+    Keep the tensors alive and in place; replay() is asynchronous: synchronise before
+    reading the outputs."""
+
+    def __init__(self, plan: Plan, params: Params, pos, lam, U, dt: float, pos_out, U_out):
+        self.plan, self.params = plan, params
+        self._keep = (pos, lam, U, pos_out, U_out, params.zeta, params.eta, params.frozen, plan.ws)
+        pc_step_host(plan, params, pos, lam, U, dt, pos_out, U_out)
+        torch.cuda.synchronize(plan.device)
+        self.graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device=plan.device)
+        side.wait_stream(torch.cuda.current_stream(plan.device))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side):
+                pc_step_host(plan, params, pos, lam, U, dt, pos_out, U_out)
+        torch.cuda.current_stream(plan.device).wait_stream(side)
+
+    def replay(self):
         self.graph.replay()

@@ -53,6 +53,7 @@ enum Region {
   R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
   R_PC_Y0,       // double [11][n] saved x^n, U^n (slot order) -- PC step
+  R_PC_IO,       // double [12][n] pos, lambda, U (caller order) of phb_pc_step_host -- PC step
   R_ADJ_ROFF,    // int64 [n+1] reverse-list offsets                     -- adjoint
   R_ADJ_RSRC,    // int32 [capacity] reverse lists: the particles naming each particle -- adjoint
   R_ADJ_RCNT,    // int32 [n+1] reverse-list counts / cursors            -- adjoint

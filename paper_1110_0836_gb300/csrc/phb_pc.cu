@@ -7,6 +7,7 @@
 // launches on one stream (no host synchronisation), so it can be captured
 // in a CUDA graph.  Particles marked in params->frozen keep x and U.
 #include <cmath>
+#include <mutex>
 
 #include "phb_internal.cuh"
 
@@ -61,22 +62,13 @@ __global__ void k_correct(int n, double dt, const int32_t* __restrict__ perm,
   for (int f = 0; f < 8; ++f) U[f * N + i] = y0[(3 + f) * N + s] + h * (f0[f * N + s] + f1[f * N + s]);
 }
 
-}  // namespace
-}  // namespace phb
-
-using namespace phb;
-
-extern "C" phb_status phb_pc_step(const phb_plan* plan, const phb_params* prm, double* pos,
-                                  const double* lambda, double* U, double dt, void* ws,
-                                  size_t ws_bytes, int32_t* status_word, phb_stream_t stream) {
-  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_PC_Y0] + 11 * 8 * plan->n : 0);
-  if (s != PHB_OK) return s;
-  if (!prm || !pos || !lambda || !U || !std::isfinite(dt)) return PHB_ERR_INVALID_ARG;
-  if (prm->precision != PHB_FP64 && prm->precision != PHB_FP32_MIXED) return PHB_ERR_INVALID_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+// The step on device arrays; the stream waits on wait_U (if not null) before
+// the first read of U.
+phb_status pc_step_impl(const phb_plan* plan, const phb_params* prm, double* pos,
+                        const double* lambda, double* U, double dt, void* ws, int32_t* status_word,
+                        cudaStream_t st, cudaEvent_t wait_U) {
   const Grid g = make_grid(plan);
   const int n = g.n;
-  const int64_t N = n;
   double* y0 = region<double>(plan, ws, R_PC_Y0);
   double* f0 = region<double>(plan, ws, R_PC_F0);
   double* f1 = region<double>(plan, ws, R_PC_F1);
@@ -85,6 +77,7 @@ extern "C" phb_status phb_pc_step(const phb_plan* plan, const phb_params* prm, d
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   cudaError_t e;
   if ((e = build_neighbors_impl(plan, pos, lambda, ws, status_word, st))) return launch_status(e);
+  if (wait_U && (e = cudaStreamWaitEvent(st, wait_U, 0))) return launch_status(e);
   if ((e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st, y0)))
     return launch_status(e);
   if ((e = run_fit(plan, prm, ws, FitMode::kRHS, nullptr, f0, nullptr, nullptr, nullptr,
@@ -100,4 +93,84 @@ extern "C" phb_status phb_pc_step(const phb_plan* plan, const phb_params* prm, d
   k_correct<<<blocks, kThreads, 0, st>>>(n, dt, perm, prm->frozen, y0, sU, f0, f1, pos, U);
   note_launch();
   return launch_status(cudaSuccess);
+}
+
+phb_status pc_args(const phb_plan* plan, const phb_params* prm, const void* pos, const void* lambda,
+                   const void* U, double dt, void* ws, size_t ws_bytes) {
+  phb_status s = check_common(plan, ws, ws_bytes, plan ? plan->ws_off[R_END_PC] : 0);
+  if (s != PHB_OK) return s;
+  if (!prm || !pos || !lambda || !U || !std::isfinite(dt)) return PHB_ERR_INVALID_ARG;
+  if (prm->precision != PHB_FP64 && prm->precision != PHB_FP32_MIXED) return PHB_ERR_INVALID_ARG;
+  return PHB_OK;
+}
+
+// A side stream and two events per device for the host-buffer step, made on
+// first use and kept for the process.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_side_mu;
+SideStream g_side[64];
+
+cudaError_t side_stream(SideStream*& out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_side_mu);
+  SideStream& ss = g_side[dev];
+  if (!ss.s) {
+    if ((e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking))) return e;
+    if ((e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming))) return e;
+    if ((e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming))) return e;
+  }
+  out = &ss;
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace phb
+
+using namespace phb;
+
+extern "C" phb_status phb_pc_step(const phb_plan* plan, const phb_params* prm, double* pos,
+                                  const double* lambda, double* U, double dt, void* ws,
+                                  size_t ws_bytes, int32_t* status_word, phb_stream_t stream) {
+  const phb_status s = pc_args(plan, prm, pos, lambda, U, dt, ws, ws_bytes);
+  if (s != PHB_OK) return s;
+  return pc_step_impl(plan, prm, pos, lambda, U, dt, ws, status_word,
+                      reinterpret_cast<cudaStream_t>(stream), nullptr);
+}
+
+extern "C" phb_status phb_pc_step_host(const phb_plan* plan, const phb_params* prm,
+                                       const double* pos_in, const double* lambda_in,
+                                       const double* U_in, double* pos_out, double* U_out,
+                                       double dt, void* ws, size_t ws_bytes,
+                                       int32_t* status_word, phb_stream_t stream) {
+  phb_status s = pc_args(plan, prm, pos_in, lambda_in, U_in, dt, ws, ws_bytes);
+  if (s != PHB_OK) return s;
+  if (!pos_out || !U_out) return PHB_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = static_cast<size_t>(plan->n);
+  double* dpos = region<double>(plan, ws, R_PC_IO);
+  double* dlam = dpos + 3 * n;
+  double* dU = dpos + 4 * n;
+  SideStream* ss = nullptr;
+  cudaError_t e;
+  if ((e = side_stream(ss))) return launch_status(e);
+  // positions and lambda first: the neighbour build needs only them; the
+  // fields follow on the side stream while the build runs
+  if ((e = cudaMemcpyAsync(dpos, pos_in, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(dlam, lambda_in, n * sizeof(double), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaEventRecord(ss->fork, st)) || (e = cudaStreamWaitEvent(ss->s, ss->fork, 0)) ||
+      (e = cudaMemcpyAsync(dU, U_in, 8 * n * sizeof(double), cudaMemcpyHostToDevice, ss->s)) ||
+      (e = cudaEventRecord(ss->join, ss->s)))
+    return launch_status(e);
+  if ((s = pc_step_impl(plan, prm, dpos, dlam, dU, dt, ws, status_word, st, ss->join)) != PHB_OK)
+    return s;
+  if ((e = cudaMemcpyAsync(pos_out, dpos, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
+      (e = cudaMemcpyAsync(U_out, dU, 8 * n * sizeof(double), cudaMemcpyDeviceToHost, st)))
+    return launch_status(e);
+  return PHB_OK;
 }

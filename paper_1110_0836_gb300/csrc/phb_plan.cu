@@ -146,22 +146,34 @@ __global__ void k_scan_add(TOut* out, int64_t count, const int64_t* bsum) {
 }
 
 // Whole scan in one block for short arrays (one launch instead of three):
-// 4096 consecutive elements per round, coalesced, with a running carry.  In
-// place is fine (each element is read before it is written).
+// 4096 consecutive elements per round, coalesced, with a running carry; the
+// next round's elements are loaded before this round's block scan, so the
+// rounds do not wait on memory one after another.  In place is fine (a
+// round's elements are read before they are written, and the next round's
+// are not written yet).
 constexpr int64_t kScanSingleMax = 65536;
 template <typename TIn, typename TOut>
 __global__ void __launch_bounds__(1024) k_scan_single(const TIn* in, TOut* out, int64_t count) {
   __shared__ int64_t sw[33];
   int64_t carry = 0;
+  int64_t nx[4];
+  {
+    const int64_t b = 4 * threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) nx[k] = b + k < count ? static_cast<int64_t>(in[b + k]) : 0;
+  }
   for (int64_t c0 = 0; c0 < count; c0 += 4 * 1024) {
     const int64_t b = c0 + 4 * threadIdx.x;
     int64_t v[4];
     int64_t run = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      v[k] = b + k < count ? static_cast<int64_t>(in[b + k]) : 0;
+      v[k] = nx[k];
       run += v[k];
     }
+    const int64_t bn = b + 4 * 1024;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) nx[k] = bn + k < count ? static_cast<int64_t>(in[bn + k]) : 0;
     int64_t total;
     int64_t pre = block_excl_scan<int64_t>(run, sw, total) + carry;
 #pragma unroll
@@ -317,6 +329,8 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   pc += align256(size_t(8) * n * 8);
   p->ws_off[R_PC_Y0] = pc;
   pc += align256(size_t(11) * n * 8);
+  p->ws_off[R_PC_IO] = pc;
+  pc += align256(size_t(12) * n * 8);
   // adjoint regions overlay the PC ones
   size_t ad = off;
   p->ws_off[R_ADJ_ROFF] = ad;

@@ -207,3 +207,35 @@ def test_linear_wave_convergence_and_mixed_precision(wave):
     assert order >= 2.0, (e16, e32, order)
     m32 = _evolve_wave(phb, 32, "fp32_mixed", wave)
     assert abs(m32 - e32) <= 0.02 * e32, (m32, e32)
+
+
+def test_host_buffer_step_matches_device_step():
+    """phb_pc_step_host on pinned host arrays (eager, and replayed from a graph that
+    holds the copies) gives bit-identical states to phb_pc_step on device arrays."""
+    phb = need_gpu()
+    w = workloads.random_modes(12, seed=24, amp=0.05)
+    dt, skin = 0.002, 0.02
+    prm = phb.Params(gamma=w.gamma)
+    plan = phb.Plan.for_workload(w, skin=skin)
+    pos_d, lam_d, U_d = phb.tensors_of(w)
+    phb.pc_step(plan, prm, pos_d, lam_d, U_d, dt)
+    hpos = torch.as_tensor(w.pos).clone().pin_memory()
+    hlam = torch.as_tensor(w.lam).clone().pin_memory()
+    hU = torch.as_tensor(w.U).clone().pin_memory()
+    opos, oU = torch.empty_like(hpos).pin_memory(), torch.empty_like(hU).pin_memory()
+    phb.pc_step_host(plan, prm, hpos, hlam, hU, dt, opos, oU)
+    torch.cuda.synchronize()
+    assert plan.read_status() == 0
+    assert torch.equal(opos, pos_d.cpu()) and torch.equal(oU, U_d.cpu())
+    # inputs untouched; in place on the host (outputs = inputs) as well
+    assert torch.equal(hpos, torch.as_tensor(w.pos)) and torch.equal(hU, torch.as_tensor(w.U))
+    g = phb.HostStepGraph(plan, prm, hpos, hlam, hU, dt, opos, oU)
+    opos.zero_(), oU.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(opos, pos_d.cpu()) and torch.equal(oU, U_d.cpu())
+    phb.pc_step_host(plan, prm, hpos, hlam, hU, dt)
+    torch.cuda.synchronize()
+    assert torch.equal(hpos, pos_d.cpu()) and torch.equal(hU, U_d.cpu())
+    with pytest.raises(ValueError):
+        phb.pc_step_host(plan, prm, pos_d, lam_d, U_d, dt)
