@@ -145,63 +145,75 @@ __global__ void k_scan_add(TOut* out, int64_t count, const int64_t* bsum) {
   if (i < count) out[i] += static_cast<TOut>(bsum[i / kScanTile]);
 }
 
-// Whole scan in one block for short arrays (one launch instead of three):
-// 4096 consecutive elements per round, coalesced, with a running carry; the
-// next round's elements are loaded before this round's block scan, so the
-// rounds do not wait on memory one after another.  In place is fine (a
-// round's elements are read before they are written, and the next round's
-// are not written yet).
-constexpr int64_t kScanSingleMax = 65536;
-template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(1024) k_scan_single(const TIn* in, TOut* out, int64_t count) {
+// Two-launch scan for up to kScanTwoMax tiles: the tiles' sums, then every
+// tile scans itself after adding up the sums of the tiles before it (at most
+// kScanTwoMax values, from L2).  Every launch is as wide as the array, which
+// a one-block scan of a short array is not.  In place is fine (a tile is read
+// before it is written, and only by its own block).
+constexpr int64_t kScanTwoMax = 256;
+
+template <typename TIn>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const TIn* in, int64_t count,
+                                                              int64_t* bsum) {
   __shared__ int64_t sw[33];
-  int64_t carry = 0;
-  int64_t nx[4];
-  {
-    const int64_t b = 4 * threadIdx.x;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + threadIdx.x * kScanItems;
+  int64_t run = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) nx[k] = b + k < count ? static_cast<int64_t>(in[b + k]) : 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + k;
+    run += i < count ? static_cast<int64_t>(in[i]) : 0;
   }
-  for (int64_t c0 = 0; c0 < count; c0 += 4 * 1024) {
-    const int64_t b = c0 + 4 * threadIdx.x;
-    int64_t v[4];
-    int64_t run = 0;
+  int64_t total;
+  block_excl_scan<int64_t>(run, sw, total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const TIn* in, TOut* out, int64_t count,
+                                                             const int64_t* bsum) {
+  __shared__ int64_t sw[33];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t run = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      v[k] = nx[k];
-      run += v[k];
-    }
-    const int64_t bn = b + 4 * 1024;
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + k;
+    v[k] = i < count ? static_cast<int64_t>(in[i]) : 0;
+    run += v[k];
+  }
+  // the sums of the tiles before this one (blockIdx.x <= kScanTwoMax - 1 < kScanThreads)
+  int64_t before;
+  {
+    const int64_t b = threadIdx.x < blockIdx.x ? bsum[threadIdx.x] : 0;
+    block_excl_scan<int64_t>(b, sw, before);
+  }
+  int64_t total;
+  int64_t pre = block_excl_scan<int64_t>(run, sw, total) + before;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) nx[k] = bn + k < count ? static_cast<int64_t>(in[bn + k]) : 0;
-    int64_t total;
-    int64_t pre = block_excl_scan<int64_t>(run, sw, total) + carry;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (b + k < count) out[b + k] = static_cast<TOut>(pre);
-      pre += v[k];
-    }
-    carry += total;
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + k;
+    if (i < count) out[i] = static_cast<TOut>(pre);
+    pre += v[k];
   }
 }
 
 template <typename TIn, typename TOut>
 cudaError_t scan_impl(const TIn* in, TOut* out, int64_t count, int64_t* bsum, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  if (count <= kScanSingleMax) {
-    k_scan_single<TIn, TOut><<<1, 1024, 0, st>>>(in, out, count);
+  const int64_t nb = scan_blocks(count);
+  if (nb <= kScanTwoMax) {
+    k_scan_reduce<TIn><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, count, bsum);
+    note_launch();
+    k_scan_apply<TIn, TOut><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, count, bsum);
     note_launch();
     return cudaGetLastError();
   }
-  const int64_t nb = scan_blocks(count);
   k_scan_tile<TIn, TOut><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, count, bsum);
   note_launch();
-  if (nb > 1) {
-    k_scan_sums<<<1, 1024, 0, st>>>(bsum, nb);
-    note_launch();
-    k_scan_add<TOut><<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(out, count, bsum);
-    note_launch();
-  }
+  k_scan_sums<<<1, 1024, 0, st>>>(bsum, nb);
+  note_launch();
+  k_scan_add<TOut><<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(out, count, bsum);
+  note_launch();
   return cudaGetLastError();
 }
 
