@@ -110,6 +110,10 @@ struct GlobalSrc {
 
 // Neighbour data from the staged records in shared memory:
 // r0 = (x, y, z, sigma), r1 = (Vx, Vy, Vz, rho), r2 = (Bx, By, Bz, 0).
+// Wrap = false for a tile whose staged offsets all lie within a quarter box
+// length of its middle particle on every periodic axis: differences of two
+// such offsets are minimum images already.
+template <bool Wrap>
 struct StagedSrc {
   const float4* stage;
   const uint16_t* lidx;
@@ -125,9 +129,15 @@ struct StagedSrc {
     // relative offsets are minimum images of size <= len/2; one more wrap
     // keeps the difference a minimum image too (exact when no wrap occurs)
     const float ax = r0.x - me0.x, ay = r0.y - me0.y, az = r0.z - me0.z;
-    dx = fmaf(-len[0], rintf(ax * inv_len[0]), ax);
-    dy = fmaf(-len[1], rintf(ay * inv_len[1]), ay);
-    dz = fmaf(-len[2], rintf(az * inv_len[2]), az);
+    if (Wrap) {
+      dx = fmaf(-len[0], rintf(ax * inv_len[0]), ax);
+      dy = fmaf(-len[1], rintf(ay * inv_len[1]), ay);
+      dz = fmaf(-len[2], rintf(az * inv_len[2]), az);
+    } else {
+      dx = ax;
+      dy = ay;
+      dz = az;
+    }
   }
   __device__ __forceinline__ int index(int64_t e) const { return lidx[e]; }
   __device__ __forceinline__ RawA fetch_a(int l) const { return RawA{stage[3 * l], stage[3 * l + 1]}; }
@@ -304,15 +314,19 @@ struct TileArgs {
 // Shared memory of one CTA besides the dynamic park/staging region.
 template <int T>
 struct FitShared {
-  int tile;       // persistent schedule: tile taken from the queue
+  int tile;         // persistent schedule: tile taken from the queue
+  int wfar[T / 32];  // per warp: staged an offset at or beyond a quarter box length
 };
 
 // Stage a tile's neighbourhood (count records, slots from the plan) in shared
 // memory: offsets and field differences relative to the tile's middle slot
 // sr, from the FP32 hi/lo records.  All T threads call it; no barrier inside.
+// Returns whether this thread staged an offset of a quarter box length or
+// more on a periodic axis (the tile's differences then need the wrap).
 template <int T>
-__device__ __forceinline__ void stage_tile(const FitArgs& a, const Per32& P, const TileArgs& ta,
+__device__ __forceinline__ bool stage_tile(const FitArgs& a, const Per32& P, const TileArgs& ta,
                                            int tile, int sr, int count, float4* stage, int tid) {
+  bool far = false;
   const float4* rec = reinterpret_cast<const float4*>(a.rec);
   // records relative to the tile's middle particle: the staged FP32 offsets
   // and field differences round to at most half the tile's extent
@@ -336,16 +350,19 @@ __device__ __forceinline__ void stage_tile(const FitArgs& a, const Per32& P, con
       if (sl[u] < 0) continue;
       const float4 p0 = v[u][0], p1 = v[u][1], f0 = v[u][2], f1 = v[u][3], g0 = v[u][4], g1 = v[u][5];
       float4* d = stage + 3 * (l0 + u * T);
-      d[0] = make_float4(mi_diff32(p0.x, p1.x, rh.x, rl.x, P.len_h[0], P.len_l[0], P.inv_len[0]),
-                         mi_diff32(p0.y, p1.y, rh.y, rl.y, P.len_h[1], P.len_l[1], P.inv_len[1]),
-                         mi_diff32(p0.z, p1.z, rh.z, rl.z, P.len_h[2], P.len_l[2], P.inv_len[2]),
-                         hl(f0.y, f1.y, fh.y, fl.y));
+      const float ox = mi_diff32(p0.x, p1.x, rh.x, rl.x, P.len_h[0], P.len_l[0], P.inv_len[0]);
+      const float oy = mi_diff32(p0.y, p1.y, rh.y, rl.y, P.len_h[1], P.len_l[1], P.inv_len[1]);
+      const float oz = mi_diff32(p0.z, p1.z, rh.z, rl.z, P.len_h[2], P.len_l[2], P.inv_len[2]);
+      far |= fabsf(ox) * P.inv_len[0] >= 0.25f || fabsf(oy) * P.inv_len[1] >= 0.25f ||
+             fabsf(oz) * P.inv_len[2] >= 0.25f;
+      d[0] = make_float4(ox, oy, oz, hl(f0.y, f1.y, fh.y, fl.y));
       d[1] = make_float4(hl(f0.z, f1.z, fh.z, fl.z), hl(f0.w, f1.w, fh.w, fl.w),
                          hl(g0.x, g1.x, gh.x, gl.x), hl(f0.x, f1.x, fh.x, fl.x));
       d[2] = make_float4(hl(g0.y, g1.y, gh.y, gl.y), hl(g0.z, g1.z, gh.z, gl.z),
                          hl(g0.w, g1.w, gh.w, gl.w), 0.f);
     }
   }
+  return far;
 }
 
 // One tile: stage its neighbourhood, accumulate, solve, write outputs.  All
@@ -371,7 +388,9 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   const int2 tp = listed ? make_int2(0, 1) : ta.tplan[tile];
   const bool fb = tp.y != 0;
   if (!fb) {
-    stage_tile<T>(a, P, ta, tile, s0 + (cnt_tile >> 1), tp.x, stage, tid);
+    const bool far = stage_tile<T>(a, P, ta, tile, s0 + (cnt_tile >> 1), tp.x, stage, tid);
+    const bool wfar = __any_sync(0xffffffffu, far);
+    if ((tid & 31) == 0) sh.wfar[tid >> 5] = wfar ? 1 : 0;
   } else if (tid == 0 && !listed) {
     atomicAdd(ta.fallback_count, 1);
   }
@@ -400,18 +419,22 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       src.P = P;
       cnt = accumulate<MODE, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, m2, bB);
     } else {
-      StagedSrc src;
-      src.stage = stage;
-      src.lidx = ta.lidx;
-      const int ls = ta.lself[s];
-      src.me0 = stage[3 * ls];
-      src.me1 = stage[3 * ls + 1];
-      src.me2 = stage[3 * ls + 2];
-      for (int c = 0; c < 3; ++c) {
-        src.len[c] = P.len[c];
-        src.inv_len[c] = P.inv_len[c];
-      }
-      cnt = accumulate<MODE, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, m2, bB);
+      auto run = [&](auto src) {
+        src.stage = stage;
+        src.lidx = ta.lidx;
+        const int ls = ta.lself[s];
+        src.me0 = stage[3 * ls];
+        src.me1 = stage[3 * ls + 1];
+        src.me2 = stage[3 * ls + 2];
+        for (int c = 0; c < 3; ++c) {
+          src.len[c] = P.len[c];
+          src.inv_len[c] = P.inv_len[c];
+        }
+        return accumulate<MODE, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, m2, bB);
+      };
+      bool wrap = false;
+      for (int w = 0; w < T / 32; ++w) wrap |= sh.wfar[w] != 0;
+      cnt = wrap ? run(StagedSrc<true>{}) : run(StagedSrc<false>{});
     }
   }
   __syncthreads();  // the staged records are dead from here on
@@ -709,7 +732,7 @@ __global__ void __launch_bounds__(T, 2) k_gram_tc(const FitArgs a, const Per32 P
     const float inv_rf2 = static_cast<float>(1.0 / (rf * rf));
     const int64_t beg = a.off[s];
     const int64_t end = a.off[s + 1] < a.g.capacity ? a.off[s + 1] : a.g.capacity;
-    StagedSrc ssrc;
+    StagedSrc<true> ssrc;  // the experiment keeps the wrap everywhere
     GlobalSrc gsrc;
     if (fb) {
       gsrc.rec = rec;
