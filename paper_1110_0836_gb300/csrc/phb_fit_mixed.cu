@@ -259,12 +259,18 @@ __device__ __forceinline__ void csne_pass(const Src& src, int64_t beg, int64_t e
       c[f][j] = make_float2(lo, hi);
       acc[f][j] = make_float2(0.f, 0.f);
     }
-  // the next neighbour's record is loaded while this one is used
+  // the next neighbour's record is loaded while this one is used, from an
+  // index loaded two neighbours before that (so that the record's load does
+  // not wait on its index's)
   typename Src::RawB nxt;
+  int i2 = beg + 1 < end ? src.index(beg + 1) : 0;
+  int i3 = beg + 2 < end ? src.index(beg + 2) : 0;
   if (beg < end) nxt = B ? src.fetch_b(src.index(beg)) : src.fetch_a(src.index(beg));
   for (int64_t e = beg; e < end; ++e) {
     const typename Src::RawB cur = nxt;
-    if (e + 1 < end) nxt = B ? src.fetch_b(src.index(e + 1)) : src.fetch_a(src.index(e + 1));
+    if (e + 1 < end) nxt = B ? src.fetch_b(i2) : src.fetch_a(i2);
+    i2 = i3;
+    if (e + 3 < end) i3 = src.index(e + 3);
     float dx, dy, dz, du[4];
     if (B) src.decode_b(cur, dx, dy, dz, du);
     else src.decode_a(cur, dx, dy, dz, du);
