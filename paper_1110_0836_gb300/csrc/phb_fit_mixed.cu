@@ -69,6 +69,7 @@ struct Groups {
 // fetch_* issues a neighbour's loads, decode_* turns them into offsets and
 // field differences, so that the loop can fetch one neighbour ahead.
 struct GlobalSrc {
+  static constexpr bool kPrefetch = true;  // accumulate: records loaded a neighbour ahead
   const float4* rec;
   const int32_t* idx;
   float4 o[6];
@@ -115,6 +116,7 @@ struct GlobalSrc {
 // such offsets are minimum images already.
 template <bool Wrap>
 struct StagedSrc {
+  static constexpr bool kPrefetch = false;
   const float4* stage;
   const uint16_t* lidx;
   float4 me0, me1, me2;
@@ -189,12 +191,24 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
     int n2 = beg + 1 < end ? src.index(beg + 1) : 0;
     int n3 = beg + 2 < end ? src.index(beg + 2) : 0;
     int n4 = beg + 3 < end ? src.index(beg + 3) : 0;
-    for (int64_t e = beg; e < end; ++e) {
-      const int cur = n1;
+    typename Src::RawA ra;
+    if (Src::kPrefetch && beg < end) {
+      ra = src.fetch_a(n1);
       n1 = n2; n2 = n3; n3 = n4;
-      if (e + 4 < end) n4 = src.index(e + 4);
+      if (beg + 4 < end) n4 = src.index(beg + 4);
+    }
+    for (int64_t e = beg; e < end; ++e) {
+      typename Src::RawA cur;
+      if constexpr (Src::kPrefetch) {
+        cur = ra;
+        if (e + 1 < end) ra = src.fetch_a(n1);
+      } else {
+        cur = src.fetch_a(n1);
+      }
+      n1 = n2; n2 = n3; n3 = n4;
+      if (e + (Src::kPrefetch ? 5 : 4) < end) n4 = src.index(e + (Src::kPrefetch ? 5 : 4));
       float dx, dy, dz, du[4];
-      src.decode_a(src.fetch_a(cur), dx, dy, dz, du);
+      src.decode_a(cur, dx, dy, dz, du);
       const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
       const bool inside = s2 < 1.f;
       const float sw = 1.f - s2;
@@ -222,12 +236,24 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
   int n2 = beg + 1 < end ? src.index(beg + 1) : 0;
   int n3 = beg + 2 < end ? src.index(beg + 2) : 0;
   int n4 = beg + 3 < end ? src.index(beg + 3) : 0;
-  for (int64_t e = beg; e < end; ++e) {
-    const int cur = n1;
+  typename Src::RawB rb;
+  if (Src::kPrefetch && beg < end) {
+    rb = src.fetch_b(n1);
     n1 = n2; n2 = n3; n3 = n4;
-    if (e + 4 < end) n4 = src.index(e + 4);
+    if (beg + 4 < end) n4 = src.index(beg + 4);
+  }
+  for (int64_t e = beg; e < end; ++e) {
+    typename Src::RawB cur;
+    if constexpr (Src::kPrefetch) {
+      cur = rb;
+      if (e + 1 < end) rb = src.fetch_b(n1);
+    } else {
+      cur = src.fetch_b(n1);
+    }
+    n1 = n2; n2 = n3; n3 = n4;
+    if (e + (Src::kPrefetch ? 5 : 4) < end) n4 = src.index(e + (Src::kPrefetch ? 5 : 4));
     float dx, dy, dz, du[4];
-    src.decode_b(src.fetch_b(cur), dx, dy, dz, du);
+    src.decode_b(cur, dx, dy, dz, du);
     const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * inv_rf2;
     const float sw = 1.f - s2;
     const float wt = s2 < 1.f ? (unweighted ? 1.f : sw * sw) : 0.f;
