@@ -334,7 +334,9 @@ phb_status phb_pc_step(const phb_plan* plan, const phb_params* params, double* p
  * copied back to pos_out [3][n] and U_out [8][n] (host; they may be pos_in and
  * U_in).  The positions and lambda go first; U follows on a side stream (one
  * per device, made on first use and kept) while the neighbour lists are built,
- * and the stream waits for it before U is read.  All of it is ordered on
+ * and the stream waits for it before U is read; x^{n+1}, which needs only V^n
+ * and V^p, is corrected right after the predictor and downloaded on the side
+ * stream while the second right-hand side runs.  All of it is ordered on
  * `stream`: the outputs are valid once the stream has reached this point (a
  * synchronisation, an event).  Capturable in a CUDA graph after one eager
  * call.  Same results and status as phb_pc_step; PHB_ERR_INVALID_ARG also for

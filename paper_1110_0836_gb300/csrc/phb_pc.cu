@@ -45,28 +45,42 @@ __global__ void k_predict(Grid g, double dt, const double* __restrict__ y0,
 }
 
 // Y^{n+1} = Y^n + dt/2 (F(Y^n) + F(Y^p)), written to the caller's arrays;
-// a frozen particle's entries are left as they are.
+// a frozen particle's entries are left as they are.  parts: 1 = positions
+// (they need only V^n and V^p, so they can be written before F(Y^p) is
+// known), 2 = fields (f1 = F(Y^p)), 3 = both.
 __global__ void k_correct(int n, double dt, const int32_t* __restrict__ perm,
                           const uint8_t* __restrict__ frozen, const double* __restrict__ y0,
                           const double* __restrict__ sU_p, const double* __restrict__ f0,
                           const double* __restrict__ f1, double* __restrict__ pos,
-                          double* __restrict__ U) {
+                          double* __restrict__ U, int parts) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int64_t N = n;
   const int i = perm[s];
   if (frozen && frozen[i]) return;
   const double h = 0.5 * dt;
-  for (int a = 0; a < 3; ++a)
-    pos[a * N + i] = y0[a * N + s] + h * (y0[(3 + 1 + a) * N + s] + sU_p[(1 + a) * N + s]);
-  for (int f = 0; f < 8; ++f) U[f * N + i] = y0[(3 + f) * N + s] + h * (f0[f * N + s] + f1[f * N + s]);
+  if (parts & 1)
+    for (int a = 0; a < 3; ++a)
+      pos[a * N + i] = y0[a * N + s] + h * (y0[(3 + 1 + a) * N + s] + sU_p[(1 + a) * N + s]);
+  if (parts & 2)
+    for (int f = 0; f < 8; ++f)
+      U[f * N + i] = y0[(3 + f) * N + s] + h * (f0[f * N + s] + f1[f * N + s]);
 }
 
-// The step on device arrays; the stream waits on wait_U (if not null) before
-// the first read of U.
+// Side work of the host-buffer step: the upload of U to wait for before U is
+// first read, and the download of x^{n+1} started on a side stream as soon as
+// the positions are corrected (before the second fit).
+struct PcOverlap {
+  cudaEvent_t wait_U = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t pos_ready = nullptr, pos_copied = nullptr;
+  double* pos_out = nullptr;
+};
+
+// The step on device arrays, with the overlaps of `ov` if given.
 phb_status pc_step_impl(const phb_plan* plan, const phb_params* prm, double* pos,
                         const double* lambda, double* U, double dt, void* ws, int32_t* status_word,
-                        cudaStream_t st, cudaEvent_t wait_U) {
+                        cudaStream_t st, const PcOverlap* ov) {
   const Grid g = make_grid(plan);
   const int n = g.n;
   double* y0 = region<double>(plan, ws, R_PC_Y0);
@@ -77,7 +91,7 @@ phb_status pc_step_impl(const phb_plan* plan, const phb_params* prm, double* pos
   const unsigned blocks = static_cast<unsigned>((n + kThreads - 1) / kThreads);
   cudaError_t e;
   if ((e = build_neighbors_impl(plan, pos, lambda, ws, status_word, st))) return launch_status(e);
-  if (wait_U && (e = cudaStreamWaitEvent(st, wait_U, 0))) return launch_status(e);
+  if (ov && (e = cudaStreamWaitEvent(st, ov->wait_U, 0))) return launch_status(e);
   if ((e = gather_sorted(plan, g, pos, lambda, U, ws, status_word, st, y0)))
     return launch_status(e);
   if ((e = run_fit(plan, prm, ws, FitMode::kRHS, nullptr, f0, nullptr, nullptr, nullptr,
@@ -87,11 +101,24 @@ phb_status pc_step_impl(const phb_plan* plan, const phb_params* prm, double* pos
   k_predict<<<blocks, kThreads, 0, st>>>(g, dt, y0, f0, perm, prm->frozen, spos, sU,
                                          region<float>(plan, ws, R_REC), status_word);
   note_launch();
+  if (ov) {
+    // x^{n+1} now, and its download beside the second fit
+    k_correct<<<blocks, kThreads, 0, st>>>(n, dt, perm, prm->frozen, y0, sU, f0, nullptr, pos, U, 1);
+    note_launch();
+    if ((e = cudaEventRecord(ov->pos_ready, st)) ||
+        (e = cudaStreamWaitEvent(ov->side, ov->pos_ready, 0)) ||
+        (e = cudaMemcpyAsync(ov->pos_out, pos, 3 * size_t(n) * sizeof(double),
+                             cudaMemcpyDeviceToHost, ov->side)) ||
+        (e = cudaEventRecord(ov->pos_copied, ov->side)))
+      return launch_status(e);
+  }
   if ((e = run_fit(plan, prm, ws, FitMode::kRHS, nullptr, f1, nullptr, nullptr, nullptr,
                    status_word, st)))
     return launch_status(e);
-  k_correct<<<blocks, kThreads, 0, st>>>(n, dt, perm, prm->frozen, y0, sU, f0, f1, pos, U);
+  k_correct<<<blocks, kThreads, 0, st>>>(n, dt, perm, prm->frozen, y0, sU, f0, f1, pos, U,
+                                         ov ? 2 : 3);
   note_launch();
+  if (ov && (e = cudaStreamWaitEvent(st, ov->pos_copied, 0))) return launch_status(e);
   return launch_status(cudaSuccess);
 }
 
@@ -108,7 +135,7 @@ phb_status pc_args(const phb_plan* plan, const phb_params* prm, const void* pos,
 // first use and kept for the process.
 struct SideStream {
   cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, pos_ready = nullptr, pos_copied = nullptr;
 };
 std::mutex g_side_mu;
 SideStream g_side[64];
@@ -124,6 +151,8 @@ cudaError_t side_stream(SideStream*& out) {
     if ((e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking))) return e;
     if ((e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming))) return e;
     if ((e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming))) return e;
+    if ((e = cudaEventCreateWithFlags(&ss.pos_ready, cudaEventDisableTiming))) return e;
+    if ((e = cudaEventCreateWithFlags(&ss.pos_copied, cudaEventDisableTiming))) return e;
   }
   out = &ss;
   return cudaSuccess;
@@ -167,10 +196,15 @@ extern "C" phb_status phb_pc_step_host(const phb_plan* plan, const phb_params* p
       (e = cudaMemcpyAsync(dU, U_in, 8 * n * sizeof(double), cudaMemcpyHostToDevice, ss->s)) ||
       (e = cudaEventRecord(ss->join, ss->s)))
     return launch_status(e);
-  if ((s = pc_step_impl(plan, prm, dpos, dlam, dU, dt, ws, status_word, st, ss->join)) != PHB_OK)
+  PcOverlap ov;
+  ov.wait_U = ss->join;
+  ov.side = ss->s;
+  ov.pos_ready = ss->pos_ready;
+  ov.pos_copied = ss->pos_copied;
+  ov.pos_out = pos_out;
+  if ((s = pc_step_impl(plan, prm, dpos, dlam, dU, dt, ws, status_word, st, &ov)) != PHB_OK)
     return s;
-  if ((e = cudaMemcpyAsync(pos_out, dpos, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st)) ||
-      (e = cudaMemcpyAsync(U_out, dU, 8 * n * sizeof(double), cudaMemcpyDeviceToHost, st)))
+  if ((e = cudaMemcpyAsync(U_out, dU, 8 * n * sizeof(double), cudaMemcpyDeviceToHost, st)))
     return launch_status(e);
   return PHB_OK;
 }
