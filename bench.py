@@ -500,6 +500,7 @@ def run_ours(args):
         eager_ms = ms
     ntr = L.phb_trace_stop(tr_ms, tr_id, cap)
     fit_ms = [tr_ms[k] for k in range(max(ntr, 0)) if tr_id[k] == 1]
+    refine_ms = [tr_ms[k] for k in range(max(ntr, 0)) if tr_id[k] == 8]
     search_ms = [tr_ms[k] for k in range(max(ntr, 0)) if tr_id[k] == 4]
     compact_ms = [tr_ms[k] for k in range(max(ntr, 0)) if tr_id[k] == 5]
     clocks = clk.summary()
@@ -510,7 +511,11 @@ def run_ours(args):
     step_ms_max = aggregate_max(step_ms, world, dev)
     value = world * 2 * n / (step_ms_max * 1e-3)
 
-    fit_avg = float(np.mean(fit_ms)) if fit_ms else float("nan")
+    # the fit is two kernels: the fused fit and the corrected step of the fits
+    # of refined tiles (an empty queue on a lattice)
+    mixed_avg = float(np.mean(fit_ms)) if fit_ms else float("nan")
+    refine_avg = float(np.sum(refine_ms)) / len(fit_ms) if (refine_ms and fit_ms) else 0.0
+    fit_avg = mixed_avg + refine_avg
     sm_count = int(torch.cuda.get_device_properties(dev).multi_processor_count)
     mhz = sm_max_mhz(local, clocks)
     flops = FLOP_PER_NEIGHBOUR * nbr_inside + FLOP_PER_PARTICLE * n
@@ -523,8 +528,11 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": None if tr is None else tr[0],
                 "traffic_unit": "DRAM bytes read + written per launch (ncu, profiles/)",
                 "traffic_how": None if tr is None else tr[1],
-                "kernel": f"{kname}<kRHS, {int(plan.c.tile)}> (fused FP32 MLS fit + MHD RHS)",
+                "kernel": f"{kname}<kRHS, {int(plan.c.tile)}> + k_fit_refine<kRHS, {int(plan.c.tile)}> "
+                          "(fused FP32 MLS fit + MHD RHS, then the corrected step of the fits of "
+                          "refined tiles)",
                 "launch_ms": fit_avg, "launches": len(fit_ms),
+                "launch_ms_parts": {kname: mixed_avg, "k_fit_refine": refine_avg},
                 "timed_on": "eager pass over the timed steps (CUDA events on the launching stream)"
                             if graph is not None else "the timed steps (CUDA events on the launching stream)",
                 "algorithmic_flop_per_launch": flops,

@@ -35,7 +35,9 @@ int64_t phb_launch_count(void);
  * the last recorded event, writes each launch's duration in milliseconds and
  * kernel id (1 = FP32-mixed fused fit, 2 = FP64 fused fit over all particles,
  * 3 = FP64 fit of the routed queue, 4 = neighbour search, 5 = list
- * compaction and tile plans), destroys the events and returns the number of
+ * compaction and tile plans, 6 and 7 = the tensor-core experiment's Gram and
+ * solve kernels, 8 = corrected step of the FP32-mixed fits of refined tiles),
+ * destroys the events and returns the number of
  * launches recorded (or -1 on a CUDA error).  Not thread-safe; one trace at a
  * time. */
 int phb_trace_start(int32_t capacity);

@@ -265,23 +265,23 @@ __device__ __forceinline__ int accumulate(const Src& src, int64_t beg, int64_t e
   return cnt;
 }
 
-// One corrected semi-normal-equations pass for the fields of parked slots
-// [k0, k0 + NFG): c0 (all 19 coefficients, parked in the thread's column) in
-// registers, residuals r_j = du_j - p(q_j).c0 recomputed from the global
-// records (RawA = RawB there), acc_k = sum_j w_j p(q_j) r_j.
-// B selects the record half (false: rho, sigma, Vx, Vy; true: Vz, Bx, By, Bz);
-// du0 is the first du component used.
-template <int NFG, bool B, int T, class Src>
+// One corrected semi-normal-equations pass for the fields of slots
+// [k0, k0 + NFG): c0 (all 19 coefficients of each, from the fit's column cg
+// of the stash, stride cs) in registers, residuals r_j = du_j - p(q_j).c0
+// recomputed from the global records (RawA = RawB there),
+// acc_k = sum_j w_j p(q_j) r_j.  B selects the record half (false: rho,
+// sigma, Vx, Vy; true: Vz, Bx, By, Bz); du0 is the first du component used.
+template <int NFG, bool B, class Src>
 __device__ __forceinline__ void csne_pass(const Src& src, int64_t beg, int64_t end, float inv_l,
-                                          float inv_rf2, bool unweighted, const float* park,
-                                          int col, int k0, int du0, float2 (&acc)[NFG][kNB2]) {
+                                          float inv_rf2, bool unweighted, const float* cg,
+                                          int64_t cs, int k0, int du0, float2 (&acc)[NFG][kNB2]) {
   float2 c[NFG][kNB2];
 #pragma unroll
   for (int f = 0; f < NFG; ++f)
 #pragma unroll
     for (int j = 0; j < kNB2; ++j) {
-      const float lo = park[((k0 + f) * kNB + 2 * j) * T + col];
-      const float hi = 2 * j + 1 < kNB ? park[((k0 + f) * kNB + 2 * j + 1) * T + col] : 0.f;
+      const float lo = cg[((k0 + f) * kNB + 2 * j) * cs];
+      const float hi = 2 * j + 1 < kNB ? cg[((k0 + f) * kNB + 2 * j + 1) * cs] : 0.f;
       c[f][j] = make_float2(lo, hi);
       acc[f][j] = make_float2(0.f, 0.f);
     }
@@ -327,6 +327,64 @@ __device__ __forceinline__ void park_derivs(float* d, const float (&b)[kNB], flo
   d[6 * T] = 2.f * b[kQuad0 + 3] * il2;
   d[7 * T] = b[kQuad0 + 4] * il2;
   d[8 * T] = 2.f * b[kQuad0 + 5] * il2;
+}
+
+// Outputs of one fitted slot from its parked derivative rows: fit status
+// and gradients / Hessians (derivative mode) or the MHD time derivatives.
+// Singular fits (too few neighbours) report zero derivatives.  No barrier.
+template <FitMode MODE, int T>
+__device__ __forceinline__ void write_outputs(const FitArgs& a, int s, bool singular, float* park,
+                                              int tid) {
+  using G = Groups<MODE>;
+  const int64_t n = a.n;
+  const float4* rec = reinterpret_cast<const float4*>(a.rec);
+  if (singular) {
+#pragma unroll 1
+    for (int k = 0; k < G::NF; ++k)
+      for (int j = 0; j < 9; ++j) park[(k * kNB + j) * T + tid] = 0.f;
+  }
+  const int dst = a.perm_out ? a.perm_out[s] : s;
+  if (a.fit_status) a.fit_status[dst] = singular ? 1 : 0;
+  if (singular) raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
+  if (MODE == FitMode::kDerivs) {
+#pragma unroll 1
+    for (int k = 0; k < G::NF; ++k) {
+      const int f = G::field(k);
+      const float* d = park + (k * kNB) * T + tid;
+      for (int c = 0; c < 3; ++c) a.grad[(f * 3 + c) * n + dst] = d[c * T];
+      if (a.hess)
+        for (int c = 0; c < 6; ++c) a.hess[(f * 6 + c) * n + dst] = d[(3 + c) * T];
+    }
+  } else {
+    MhdDerivs<float> D;
+    mhd_zero(D);
+#pragma unroll
+    for (int k = 0; k < G::NF; ++k) {
+      const float* d = park + (k * kNB) * T + tid;
+      const float g[3] = {d[0], d[T], d[2 * T]};
+      const float h[6] = {d[3 * T], d[4 * T], d[5 * T], d[6 * T], d[7 * T], d[8 * T]};
+      mhd_collect(D, G::field(k), g, h);
+    }
+    const float4 o2 = rec[6 * s + 2], o3 = rec[6 * s + 3], o4 = rec[6 * s + 4], o5 = rec[6 * s + 5];
+    const float u[8] = {o2.x + o3.x, o2.z + o3.z, o2.w + o3.w, o4.x + o5.x,
+                        o4.y + o5.y, o4.z + o5.z, o4.w + o5.w, o2.y + o3.y};
+    const int src = a.perm_in ? a.perm_in[s] : s;
+    float zeta = a.zeta ? static_cast<float>(a.zeta[src]) : 0.f;
+    float eta = a.eta ? static_cast<float>(a.eta[src]) : 0.f;
+    if (a.c_zeta_l != 0.0 || a.c_zeta_a != 0.0 || a.c_eta != 0.0)
+      mhd_laws(u, D, static_cast<float>(a.gamma), static_cast<float>(a.slam[s]),
+               static_cast<float>(a.c_zeta_l), static_cast<float>(a.c_zeta_a),
+               static_cast<float>(a.c_eta), zeta, eta);
+    float out[8];
+    mhd_rhs(u, D, static_cast<float>(a.gamma), zeta, eta, out);
+    bool finite = true;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      finite &= isfinite(out[f]);
+      a.dudt[f * n + dst] = out[f];
+    }
+    if (!finite) raise_flag(a.status_word, PHB_FLAG_NONFINITE);
+  }
 }
 
 struct TileArgs {
@@ -517,10 +575,45 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       mls_back9(M, invd, b);
       park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
     }
-  } else if (solve) {
-    // first solve: all 19 coefficients of every field in place of its parked
-    // right-hand side, and the nine linear and quadratic ones (which the
-    // correction is added to) in the workspace
+  }
+  // A refined tile of a set whose records fit in L2 hands its solved fits to
+  // k_fit_refine: one queue position per fit (one atomic per warp), its
+  // moments and the first solve's 19 coefficients of every field into the
+  // queue's stash.  (Before the in-tile step below, so that the factor is
+  // dead during that step's residual passes.)
+  const bool deferred = refine && solve && a.refine_queued;
+  const unsigned dmask = __ballot_sync(0xffffffffu, deferred);
+  if (dmask != 0u) {
+    const int lane = tid & 31;
+    const int leader = __ffs(dmask) - 1;
+    int qbase = 0;
+    if (lane == leader) qbase = atomicAdd(a.rq_len, __popc(dmask));
+    qbase = __shfl_sync(0xffffffffu, qbase, leader);
+    if (deferred) {
+      const int64_t q = qbase + __popc(dmask & ((1u << lane) - 1u));
+      a.rqueue[q] = s;
+      float* st = a.rstash + q;
+#pragma unroll 4
+      for (int k = 0; k < kNM; ++k) st[k * static_cast<int64_t>(n)] = mstash[k * T + tid];
+#pragma unroll 1
+      for (int k = 0; k < G::NF; ++k) {
+        float b[kNB];
+#pragma unroll
+        for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
+        mls_forward(M, invd, b);
+        mls_back19(M, invd, b);
+#pragma unroll
+        for (int j = 0; j < kNB; ++j) st[(kNM + k * kNB + j) * static_cast<int64_t>(n)] = b[j];
+      }
+    }
+  }
+  if (solve && refine && !a.refine_queued) {
+    // Otherwise the corrected step here, while the tile's neighbourhood is
+    // still in L2 (sets whose records exceed L2).  First solve: all 19 coefficients of
+    // every field in place of its parked right-hand side, and the nine linear
+    // and quadratic ones (which the correction is added to) in the slot's
+    // column of the stash
+    float* cq = a.rstash + s;
 #pragma unroll 1
     for (int k = 0; k < G::NF; ++k) {
       float b[kNB];
@@ -531,14 +624,10 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
 #pragma unroll
       for (int j = 0; j < kNB; ++j) park[(k * kNB + j) * T + tid] = b[j];
 #pragma unroll
-      for (int j = kQuad0; j < kNB; ++j)
-        a.csne[(k * 9 + j - kQuad0) * static_cast<int64_t>(n) + s] = b[j];
+      for (int j = kQuad0; j < kNB; ++j) cq[(kNM + k * kNB + j) * static_cast<int64_t>(n)] = b[j];
     }
-    // residual passes over the neighbours from the global records: offsets and
-    // field differences straight from the hi/lo splits of the particle and the
-    // neighbour round to ~2^-24 of the difference itself, while the staged ones
-    // (relative to the tile's middle particle) round to 2^-24 of the change
-    // across the tile - too coarse a floor for the corrected solution
+    // residual passes over the neighbours from the global records (see
+    // k_fit_refine)
     GlobalSrc src;
     src.rec = rec;
     src.idx = a.idx;
@@ -546,8 +635,8 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     src.P = P;
     {
       float2 acc[G::NA][kNB2];
-      csne_pass<G::NA, false, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, 0,
-                                 4 - G::NA, acc);
+      csne_pass<G::NA, false>(src, beg, end, inv_l, inv_rf2, unweighted, park + tid, T, 0,
+                              4 - G::NA, acc);
 #pragma unroll
       for (int f = 0; f < G::NA; ++f)
 #pragma unroll
@@ -555,7 +644,7 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     }
     {
       float2 acc[4][kNB2];
-      csne_pass<4, true, T>(src, beg, end, inv_l, inv_rf2, unweighted, park, tid, G::NA, 0, acc);
+      csne_pass<4, true>(src, beg, end, inv_l, inv_rf2, unweighted, park + tid, T, G::NA, 0, acc);
 #pragma unroll
       for (int f = 0; f < 4; ++f)
 #pragma unroll
@@ -578,63 +667,11 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       mls_forward(M2, invd2, b);
       mls_back9(M2, invd2, b);
 #pragma unroll
-      for (int j = kQuad0; j < kNB; ++j)
-        b[j] += a.csne[(k * 9 + j - kQuad0) * static_cast<int64_t>(n) + s];
+      for (int j = kQuad0; j < kNB; ++j) b[j] += cq[(kNM + k * kNB + j) * static_cast<int64_t>(n)];
       park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
     }
   }
-  if (active && singular) {
-#pragma unroll 1
-    for (int k = 0; k < G::NF; ++k)
-      for (int j = 0; j < 9; ++j) park[(k * kNB + j) * T + tid] = 0.f;
-  }
-  if (active) {
-    const int dst = a.perm_out ? a.perm_out[s] : s;
-    if (!routed) {
-      if (a.fit_status) a.fit_status[dst] = singular ? 1 : 0;
-      if (singular) raise_flag(a.status_word, PHB_FLAG_FIT_SINGULAR);
-      if (MODE == FitMode::kDerivs) {
-#pragma unroll 1
-        for (int k = 0; k < G::NF; ++k) {
-          const int f = G::field(k);
-          const float* d = park + (k * kNB) * T + tid;
-          for (int c = 0; c < 3; ++c) a.grad[(f * 3 + c) * static_cast<int64_t>(n) + dst] = d[c * T];
-          if (a.hess)
-            for (int c = 0; c < 6; ++c)
-              a.hess[(f * 6 + c) * static_cast<int64_t>(n) + dst] = d[(3 + c) * T];
-        }
-      } else {
-        MhdDerivs<float> D;
-        mhd_zero(D);
-#pragma unroll
-        for (int k = 0; k < G::NF; ++k) {
-          const float* d = park + (k * kNB) * T + tid;
-          const float g[3] = {d[0], d[T], d[2 * T]};
-          const float h[6] = {d[3 * T], d[4 * T], d[5 * T], d[6 * T], d[7 * T], d[8 * T]};
-          mhd_collect(D, G::field(k), g, h);
-        }
-        const float4 o2 = rec[6 * s + 2], o3 = rec[6 * s + 3], o4 = rec[6 * s + 4], o5 = rec[6 * s + 5];
-        const float u[8] = {o2.x + o3.x, o2.z + o3.z, o2.w + o3.w, o4.x + o5.x,
-                            o4.y + o5.y, o4.z + o5.z, o4.w + o5.w, o2.y + o3.y};
-        const int src = a.perm_in ? a.perm_in[s] : s;
-        float zeta = a.zeta ? static_cast<float>(a.zeta[src]) : 0.f;
-        float eta = a.eta ? static_cast<float>(a.eta[src]) : 0.f;
-        if (a.c_zeta_l != 0.0 || a.c_zeta_a != 0.0 || a.c_eta != 0.0)
-          mhd_laws(u, D, static_cast<float>(a.gamma), static_cast<float>(a.slam[s]),
-                   static_cast<float>(a.c_zeta_l), static_cast<float>(a.c_zeta_a),
-                   static_cast<float>(a.c_eta), zeta, eta);
-        float out[8];
-        mhd_rhs(u, D, static_cast<float>(a.gamma), zeta, eta, out);
-        bool finite = true;
-#pragma unroll
-        for (int f = 0; f < 8; ++f) {
-          finite &= isfinite(out[f]);
-          a.dudt[f * static_cast<int64_t>(n) + dst] = out[f];
-        }
-        if (!finite) raise_flag(a.status_word, PHB_FLAG_NONFINITE);
-      }
-    }
-  }
+  if (active && !routed && !deferred) write_outputs<MODE, T>(a, s, singular, park, tid);
   __syncthreads();  // the park region is reused by the next tile (persistent schedule)
 }
 
@@ -667,6 +704,88 @@ __global__ void __launch_bounds__(T, 256 / T) k_fit_mixed_persistent(const FitAr
     __syncthreads();
     if (q >= ta.ntiles) break;
     fit_tile<MODE, T>(a, P, ta, ta.order[q], park, stage, sh);
+  }
+}
+
+// The corrected step of the fits of refined tiles (queued by k_fit_mixed with
+// their moments and first solves): one thread per queued fit, grid-stride
+// over the queue, no barrier, so that warps stream through the queue instead
+// of waiting at a tile's barriers for its longest lists.  Two residual passes
+// over the neighbours from the global records (offsets and field differences
+// straight from the hi/lo splits of the particle and the neighbour round to
+// ~2^-24 of the difference itself, while the staged ones, relative to a
+// tile's middle particle, round to 2^-24 of the change across the tile - too
+// coarse a floor for the corrected solution) accumulate P^T W (du - P c0);
+// the factor re-formed from the moments gives the correction of the linear
+// and quadratic coefficients, added to c0's, and the outputs follow.
+template <FitMode MODE, int T>
+__global__ void __launch_bounds__(T, 256 / T) k_fit_refine(const FitArgs a, const Per32 P) {
+  using G = Groups<MODE>;
+  extern __shared__ float4 smem4[];
+  float* park = reinterpret_cast<float*>(smem4);  // [NF * 19][T]: one column per thread
+  const int tid = threadIdx.x;
+  const int64_t n = a.n;
+  // launched as a programmatic dependent of k_fit_mixed: wait until it has
+  // completed and its queue and stash are visible
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int64_t len = *a.rq_len;
+  const float4* rec = reinterpret_cast<const float4*>(a.rec);
+  const bool unweighted = a.weight_kind == 1;
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * T + tid; q < len;
+       q += static_cast<int64_t>(gridDim.x) * T) {
+    const int s = a.rqueue[q];
+    const float* st = a.rstash + q;
+    const float lamf = static_cast<float>(a.slam[s]);
+    const float rff = static_cast<float>(a.g.rf_factor) * lamf;
+    const float inv_l = 1.f / lamf;
+    const float inv_rf2 = 1.f / (rff * rff);
+    const int64_t beg = a.off[s];
+    const int64_t end = a.off[s + 1] < a.g.capacity ? a.off[s + 1] : a.g.capacity;
+    GlobalSrc src;
+    src.rec = rec;
+    src.idx = a.idx;
+    // the particle's own record: positions and the first field group now,
+    // the second group before its pass (fewer registers live in the first)
+    for (int k = 0; k < 4; ++k) src.o[k] = rec[6 * s + k];
+    src.P = P;
+    {
+      float2 acc[G::NA][kNB2];
+      csne_pass<G::NA, false>(src, beg, end, inv_l, inv_rf2, unweighted, st + kNM * n, n, 0,
+                              4 - G::NA, acc);
+#pragma unroll
+      for (int f = 0; f < G::NA; ++f)
+#pragma unroll
+        for (int k = 0; k < kNB; ++k) park[(f * kNB + k) * T + tid] = pair_at(acc[f], k);
+    }
+    {
+      src.o[4] = rec[6 * s + 4];
+      src.o[5] = rec[6 * s + 5];
+      float2 acc[4][kNB2];
+      csne_pass<4, true>(src, beg, end, inv_l, inv_rf2, unweighted, st + kNM * n, n, G::NA, 0, acc);
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int k = 0; k < kNB; ++k) park[((G::NA + f) * kNB + k) * T + tid] = pair_at(acc[f], k);
+    }
+    float2 mm[kNM2];
+#pragma unroll
+    for (int k = 0; k < kNM2; ++k) mm[k] = make_float2(st[(2 * k) * n], st[(2 * k + 1) * n]);
+    float M[kNT], invd[kNB];
+    mls_assemble_p2(mm, M);
+    mls_cholesky<float>(M, invd);
+    const float il = inv_l, il2 = inv_l * inv_l;
+#pragma unroll 1
+    for (int k = 0; k < G::NF; ++k) {
+      float b[kNB];
+#pragma unroll
+      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
+      mls_forward(M, invd, b);
+      mls_back9(M, invd, b);
+#pragma unroll
+      for (int j = kQuad0; j < kNB; ++j) b[j] += st[(kNM + k * kNB + j) * n];
+      park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
+    }
+    write_outputs<MODE, T>(a, s, false, park, tid);
   }
 }
 
@@ -958,6 +1077,35 @@ cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, int64
                          static_cast<int>(smem));
     const int tr = trace_begin(1, st);
     k_fit_mixed<MODE, T><<<tiles, T, smem, st>>>(a, P, ta);
+    note_launch();
+    trace_end(tr, st);
+  }
+  if ((e = cudaGetLastError())) return e;
+  if (a.refine_mode >= 0 && a.refine_queued) {
+    // the corrected step of the queued fits: a grid that keeps every SM busy
+    const size_t rsmem = size_t(G::NF) * kNB * T * sizeof(float);
+    cudaFuncSetAttribute(k_fit_refine<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(rsmem));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit_refine<MODE, T>, T, rsmem);
+    if (per_sm < 1) per_sm = 1;
+    unsigned grid = static_cast<unsigned>(num_sms() * per_sm);
+    if (grid > tiles) grid = tiles;
+    // a programmatic dependent launch: its set-up overlaps the fused fit's
+    // tail, and the kernel waits for the fit's completion before it reads the
+    // queue (an empty queue then costs little more than that wait)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = rsmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int tr = trace_begin(8, st);
+    if ((e = cudaLaunchKernelEx(&cfg, k_fit_refine<MODE, T>, a, P))) return e;
     note_launch();
     trace_end(tr, st);
   }

@@ -19,7 +19,8 @@ enum Region {
   R_MISC = 0,    // int32 [64]: 0 = FP64 route-queue length, 1 = tiles that fell back to
                  //   global gathers in the last neighbour build, 2 = same in the last
                  //   fused fit, 3 = persistent tile-queue counter, 4 = active-subset
-                 //   length, 5 = tiles refined by the last FP32-mixed fit
+                 //   length, 5 = tiles refined by the last FP32-mixed fit, 6 = fits
+                 //   queued for its corrected step
   R_KEYS,        // int32 [n]   cell key of each caller particle
   R_PERM,        // int32 [n]   slot -> caller index
   R_INV,         // int32 [n]   caller index -> slot
@@ -48,7 +49,9 @@ enum Region {
   R_ALIST,       // int32 [n+64] slots of an active subset (ascending)
   R_AFLAG,       // int32 [n+1]  active-subset marks / their exclusive scan
   R_QUEUE,       // int32 [n]    slots routed to FP64
-  R_CSNE,        // float [8][9][n] linear + quadratic coefficients of refined fits' first solve
+  R_RQUEUE,      // int32 [n]    slots of refined tiles' fits, queued for the corrected step
+  R_RSTASH,      // float [80 + 8*19][n] per queued fit (queue order): its moments in the
+                 //   packed pair layout, then the 19 first-solve coefficients of each field
   R_DIAG,        // double [3][kDiagBlocks] block partial sums of the mode-amplitude diagnostic
   R_PC_F0,       // double [8][n] F(Y^n) (slot order)        -- PC step
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
@@ -396,8 +399,13 @@ struct FitArgs {
   // largest conditioning estimate exceeds refine_kappa, 1 every tile
   int32_t refine_mode;
   float refine_kappa;
-  float* csne;                 // [8][9][n] linear and quadratic coefficients of the first
-                               // solve (slot order)
+  // the corrected step of refined tiles in k_fit_refine over a queue (sets
+  // whose FP32 records fit in L2) or inside the tile (larger sets: the
+  // tile's neighbourhood is still in L2 right after its main passes)
+  bool refine_queued;
+  int32_t* rqueue;             // [n] fits queued for the corrected step
+  int32_t* rq_len;             // their count (zeroed before the launch)
+  float* rstash;               // [kNM + 8*19][n] moments and first solves, queue order
   int32_t* refined_tiles;      // count of refined tiles (zeroed before the launch)
 };
 
@@ -423,6 +431,7 @@ FitArgs fit_args(const phb_plan* plan, const phb_params* prm, void* ws, const in
 cudaError_t launch_fit_fp64(const FitArgs& a, FitMode mode, const int32_t* list,
                             const int32_t* list_len, cudaStream_t st, bool routed = false);
 int num_sms();
+size_t l2_bytes();  // L2 cache size of the current device (queried once)
 
 // Launch bookkeeping (measurement helpers, see include/phurbas_bench.h).
 void note_launch(int count = 1);

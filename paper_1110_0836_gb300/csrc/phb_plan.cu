@@ -57,6 +57,17 @@ int num_sms() {
   return sms;
 }
 
+size_t l2_bytes() {
+  static int l2 = 0;
+  if (!l2) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0)
+      l2 = 64 << 20;
+  }
+  return static_cast<size_t>(l2);
+}
+
 phb_status launch_status(cudaError_t e) {
   if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? PHB_OK : PHB_ERR_CUDA;
@@ -325,7 +336,8 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   sz[R_ALIST] = size_t(n + 64) * 4;
   sz[R_AFLAG] = size_t(n + 1) * 4;
   sz[R_QUEUE] = (n + 64) * 4;  // also the export's n+1 counts
-  sz[R_CSNE] = size_t(kNF) * 9 * n * 4;
+  sz[R_RQUEUE] = size_t(n) * 4;
+  sz[R_RSTASH] = size_t(80 + kNF * 19) * n * 4;
   sz[R_DIAG] = size_t(3) * kDiagBlocks * 8;
   size_t off = 0;
   for (int r = R_MISC; r <= R_DIAG; ++r) {

@@ -122,7 +122,10 @@ FitArgs fit_args(const phb_plan* plan, const phb_params* prm, void* ws, const in
   a.status_word = status_word;
   a.refine_mode = prm->refine < 0 ? -1 : (prm->refine > 0 ? 1 : 0);
   a.refine_kappa = static_cast<float>(prm->refine_kappa > 0 ? prm->refine_kappa : 500.0);
-  a.csne = region<float>(plan, ws, R_CSNE);
+  a.refine_queued = static_cast<size_t>(plan->n) * 96 <= l2_bytes();
+  a.rqueue = region<int32_t>(plan, ws, R_RQUEUE);
+  a.rq_len = a.queue_len + 6;
+  a.rstash = region<float>(plan, ws, R_RSTASH);
   a.refined_tiles = a.queue_len + 5;
   return a;
 }
@@ -136,7 +139,7 @@ cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMo
   if (prm->precision == PHB_FP64) return launch_fit_fp64(a, mode, list, list_len, st);
   if ((e = cudaMemsetAsync(a.queue_len, 0, sizeof(int32_t), st))) return e;
   if ((e = cudaMemsetAsync(a.queue_len + 2, 0, sizeof(int32_t), st))) return e;
-  if ((e = cudaMemsetAsync(a.refined_tiles, 0, sizeof(int32_t), st))) return e;
+  if ((e = cudaMemsetAsync(a.refined_tiles, 0, 2 * sizeof(int32_t), st))) return e;  // and rq_len
   if ((e = launch_fit_mixed(a, mode, region<int2>(plan, ws, R_TPLAN), region<int32_t>(plan, ws, R_TSLOT),
                             region<uint16_t>(plan, ws, R_LSELF), region<uint8_t>(plan, ws, R_TMAP),
                             region<uint16_t>(plan, ws, R_LIDX),
