@@ -23,13 +23,16 @@
 // steep front leak into the quadratic ones (Hessian errors of 4e-4 of their
 // scale at the shear layer).  A tile whose largest estimate exceeds
 // refine_kappa (or every tile, by choice) therefore takes one corrected step
-// after the first solve: all 19 coefficients c0 of every field replace its
-// parked right-hand side, one more pass over the neighbours accumulates P^T W r with the
-// residuals r_j = (U_j - U_i) - p(q_j).c0 recomputed from the records, and the
-// same factor (re-formed from the moments kept in shared memory) solves for
-// the correction.  The error then follows cond(A) = cond(M_s)^(1/2) instead of
-// cond(M_s).  The decision is per tile, so the CTA's control flow and
-// barriers stay uniform.
+// after the first solve: with all 19 coefficients c0 of every field, one more
+// pass over the neighbours accumulates P^T W r with the residuals
+// r_j = (U_j - U_i) - p(q_j).c0 recomputed from the records, and the same
+// factor (re-formed from the kept moments) solves for the correction.  The
+// error then follows cond(A) = cond(M_s)^(1/2) instead of cond(M_s).  The
+// decision is per tile (a per-fit rule leaves fits above the bar).  Where the
+// set's FP32 records fit in L2, a refined tile queues its fits with their
+// moments and c0 for k_fit_refine, which streams through the queue without
+// the tile's barriers; larger sets take the step inside the tile, while its
+// neighbourhood is still in L2.
 #include "phb_internal.cuh"
 #include "mls_gen.cuh"
 #include "phb_mhd.cuh"
