@@ -477,7 +477,7 @@ phb_status phb_kh_mode_amplitude(const phb_plan* plan, const double* pos, const 
  *     (32 MiB) that every GPU which loads the library holds until exit.  A
  *     plan whose build-and-fit workspace (everything before the
  *     predictor-corrector regions) is larger returns PHB_ERR_WORKSPACE and
- *     launches nothing; with constant lambda this allows roughly 17,000
+ *     launches nothing; with constant lambda this allows roughly 15,000
  *     particles.
  *   - Every call looks up the array's device address in the current context
  *     (cudaGetSymbolAddress, a host-side query), so the call stays valid after
