@@ -40,7 +40,7 @@ class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("weight_kind", C.c_int32), ("precision", C.c_int32),
                 ("cond_threshold", C.c_double), ("zeta", C.c_void_p), ("eta", C.c_void_p),
                 ("frozen", C.c_void_p), ("c_zeta_l", C.c_double), ("c_zeta_a", C.c_double),
-                ("c_eta", C.c_double), ("refine", C.c_int32), ("pad_", C.c_int32),
+                ("c_eta", C.c_double), ("refine", C.c_int32), ("refine_schedule", C.c_int32),
                 ("refine_kappa", C.c_double)]
 
 

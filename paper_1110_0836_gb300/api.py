@@ -52,9 +52,11 @@ class Params:
     c_eta: float = 0.0
     # FP32-mixed: one corrected semi-normal-equations step per tile: "auto"
     # (tiles with a fit whose conditioning estimate exceeds refine_kappa),
-    # "on" (every tile) or "off"
+    # "on" (every tile) or "off"; refine_schedule: where it runs, "auto" (by
+    # the set's size), "queue" (a second kernel) or "tile" (inside the tile)
     refine: str = "auto"
     refine_kappa: float = 500.0
+    refine_schedule: str = "auto"
 
     def c(self) -> _lib.Params:
         p = _lib.Params()
@@ -76,6 +78,11 @@ class Params:
             raise ValueError(f"refine must be 'auto', 'on' or 'off', not {self.refine!r}")
         p.refine = modes[self.refine]
         p.refine_kappa = float(self.refine_kappa)
+        schedules = {"auto": 0, "queue": 1, "tile": 2}
+        if self.refine_schedule not in schedules:
+            raise ValueError(f"refine_schedule must be 'auto', 'queue' or 'tile', not "
+                             f"{self.refine_schedule!r}")
+        p.refine_schedule = schedules[self.refine_schedule]
         return p
 
 

@@ -122,7 +122,8 @@ FitArgs fit_args(const phb_plan* plan, const phb_params* prm, void* ws, const in
   a.status_word = status_word;
   a.refine_mode = prm->refine < 0 ? -1 : (prm->refine > 0 ? 1 : 0);
   a.refine_kappa = static_cast<float>(prm->refine_kappa > 0 ? prm->refine_kappa : 500.0);
-  a.refine_queued = static_cast<size_t>(plan->n) * 96 <= l2_bytes();
+  a.refine_queued = prm->refine_schedule == 1 ||
+                    (prm->refine_schedule != 2 && static_cast<size_t>(plan->n) * 96 <= l2_bytes());
   a.rqueue = region<int32_t>(plan, ws, R_RQUEUE);
   a.rq_len = a.queue_len + 6;
   a.rstash = region<float>(plan, ws, R_RSTASH);
