@@ -128,11 +128,12 @@ typedef struct {
    * front into the quadratic ones); refine = 1 refines every tile; refine =
    * -1 never refines. */
   int32_t refine;
-  /* Where the corrected step of refined tiles runs: 0 = by the set's size
-   * (a second kernel over a queue of the refined tiles' fits when n x 96 B of
-   * FP32 records fit in the device's L2, inside the tile otherwise), 1 = the
-   * queue, 2 = inside the tile (other values: as 0).  Same results either
-   * way. */
+  /* Where the corrected step of refined tiles runs: 0 = by the set (a second
+   * kernel over a queue of the refined tiles' fits when n x 96 B of FP32
+   * records fit in the device's L2 and lambda varies - sets of one
+   * resolution rarely refine and skip that launch - inside the tile
+   * otherwise), 1 = the queue, 2 = inside the tile (other values: as 0).
+   * Same results either way. */
   int32_t refine_schedule;
   double refine_kappa;
 } phb_params;

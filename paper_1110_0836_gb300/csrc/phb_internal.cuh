@@ -400,8 +400,9 @@ struct FitArgs {
   int32_t refine_mode;
   float refine_kappa;
   // the corrected step of refined tiles in k_fit_refine over a queue (sets
-  // whose FP32 records fit in L2) or inside the tile (larger sets: the
-  // tile's neighbourhood is still in L2 right after its main passes)
+  // whose FP32 records fit in L2 and whose lambda varies) or inside the tile
+  // (larger sets: the tile's neighbourhood is still in L2 right after its
+  // main passes)
   bool refine_queued;
   int32_t* rqueue;             // [n] fits queued for the corrected step
   int32_t* rq_len;             // their count (zeroed before the launch)

@@ -122,8 +122,12 @@ FitArgs fit_args(const phb_plan* plan, const phb_params* prm, void* ws, const in
   a.status_word = status_word;
   a.refine_mode = prm->refine < 0 ? -1 : (prm->refine > 0 ? 1 : 0);
   a.refine_kappa = static_cast<float>(prm->refine_kappa > 0 ? prm->refine_kappa : 500.0);
+  // by size: the queue where the records fit in L2 and lambda varies (sets
+  // of one resolution, lattices above all, rarely refine: they skip the
+  // queue's launch and refine inside the tile when they do)
   a.refine_queued = prm->refine_schedule == 1 ||
-                    (prm->refine_schedule != 2 && static_cast<size_t>(plan->n) * 96 <= l2_bytes());
+                    (prm->refine_schedule != 2 && static_cast<size_t>(plan->n) * 96 <= l2_bytes() &&
+                     plan->lambda_max > 1.01 * plan->lambda_min);
   a.rqueue = region<int32_t>(plan, ws, R_RQUEUE);
   a.rq_len = a.queue_len + 6;
   a.rstash = region<float>(plan, ws, R_RSTASH);
