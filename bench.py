@@ -55,10 +55,12 @@ KERNEL_FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
 # under the size rule are captured on a smaller set of the same recipe and
 # scaled by the particles processed.  Absent = null.
 FIT_TRAFFIC = {
-    "random_modes_64^3": (68616192 + 2865920, "ncu, this workload, one launch"),
-    "shock_tube_1048576": (491343872 + 300470016, "ncu, this workload, one launch"),
-    "shear_layer_8000000": (8 * (473480704 + 284794368),
-                            "ncu on the 1,000,000-particle set of the same recipe, x 8 "
+    "random_modes_64^3": (68603648 + 2520832, "ncu, this workload, one launch"),
+    "shock_tube_1048576": (287756800 + 836543488 + 1261519616 + 78016512,
+                           "ncu, this workload, one launch of each of the two fit kernels"),
+    "shear_layer_8000000": (8 * (473725696 + 285469184),
+                            "ncu on the 1,000,000-particle set of the same recipe with the "
+                            "corrected step in the tiles (the 8M set's schedule), x 8 "
                             "(particles processed)"),
 }
 
@@ -93,6 +95,9 @@ def parse():
                     help="launch the timed steps eagerly instead of replaying a captured CUDA graph")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 steps (0 = skip)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
+    ap.add_argument("--refine-schedule", choices=["auto", "queue", "tile"], default="auto",
+                    help="--profile only: where the corrected step of refined tiles runs "
+                         "(phb_params.refine_schedule)")
     ap.add_argument("--tc-experiment", action="store_true",
                     help="also time the tensor-core form of the fit's accumulation (mma.sync, "
                          "3xTF32) against the FP32 CUDA-core kernel on the workload")
@@ -356,7 +361,7 @@ def run_profile(args):
     vmax = float(np.sqrt((w.U[1:4] ** 2).sum(0)).max())
     skin = max(4.0 * dt * vmax, 0.02 * 2.3 * float(w.lam.min()))
     pos, lam, U = phb.tensors_of(w, dev)
-    prm = phb.Params(gamma=w.gamma, precision=args.precision)
+    prm = phb.Params(gamma=w.gamma, precision=args.precision, refine_schedule=args.refine_schedule)
     shape = {"tile": args.tile, "schedule": args.schedule, "cell_frac": args.cell_frac}
     if args.profile == "fit":
         plan = phb.Plan.for_workload(w, device=dev, **shape)
