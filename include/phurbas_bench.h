@@ -42,6 +42,14 @@ int64_t phb_launch_count(void);
  * time. */
 int phb_trace_start(int32_t capacity);
 
+/* Byte offset and size, inside the workspace, of the FP32 hi/lo records
+ * written by every fit and step call (slot order, 24 floats per slot:
+ * (xh, yh, zh, 0) (xl, yl, zl, 0) (rho, sigma, Vx, Vy)_h (..)_l
+ * (Vz, Bx, By, Bz)_h (..)_l, with h = v rounded to FP32 and l = (v - h)
+ * rounded to FP32), for tests that check them.  Host only.  Returns 0, or 1
+ * for an invalid plan or NULL output. */
+int phb_record_region(const phb_plan* plan, size_t* offset, size_t* bytes);
+
 /* Copy diagnostic counters of the last operations on a workspace to the host
  * (synchronising on `stream`): out[0] = fits routed to FP64 by the last fused
  * fit, out[1] = tiles of the last neighbour build that read neighbours from

@@ -28,7 +28,7 @@ EXPORTS = ["phb_plan_init", "phb_workspace_size", "phb_status_string", "phb_chec
            "phb_rhs_adjoint_stored", "phb_mhd_rhs_active", "phb_timestep_levels",
            "phb_struct_sizes", "phb_reorder", "phb_adapt_scan", "phb_adapt_apply",
            "phb_workspace_part", "phb_kh_mode_amplitude", "phb_block_begin",
-           "phb_block_substep", "phb_fit_tc_experiment", "phb_pc_step_host"]
+           "phb_block_substep", "phb_fit_tc_experiment", "phb_pc_step_host", "phb_record_region"]
 
 
 class Box(C.Structure):
@@ -118,6 +118,8 @@ def lib(path: str | None = None) -> C.CDLL:
     L.phb_trace_read.argtypes = [_vp, _vp, C.c_int32]
     L.phb_trace_read.restype = C.c_int
     L.phb_workspace_stats.argtypes = [P(Plan), _vp, _vp, C.c_int32, _vp]
+    L.phb_record_region.argtypes = [P(Plan), P(C.c_size_t), P(C.c_size_t)]
+    L.phb_record_region.restype = C.c_int
     L.phb_workspace_stats.restype = C.c_int
     L.phb_mhd_rhs_noalloc.argtypes = [P(Plan), P(Params), _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.phb_mhd_rhs_noalloc.restype = C.c_int

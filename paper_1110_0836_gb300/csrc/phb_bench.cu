@@ -130,6 +130,13 @@ extern "C" int phb_fma_peak(int32_t precision, int32_t blocks, int32_t iters, vo
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
+extern "C" int phb_record_region(const phb_plan* plan, size_t* offset, size_t* bytes) {
+  if (!plan || !offset || !bytes || plan->ws_bytes == 0 || plan->n <= 0) return 1;
+  *offset = plan->ws_off[phb::R_REC];
+  *bytes = static_cast<size_t>(plan->n) * 24 * sizeof(float);
+  return 0;
+}
+
 extern "C" int phb_workspace_stats(const phb_plan* plan, const void* ws, int32_t* out, int32_t count,
                                    phb_stream_t stream) {
   if (!plan || !ws || !out || count < 0 || count > 5 || plan->ws_bytes == 0) return 1;

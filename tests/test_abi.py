@@ -179,3 +179,31 @@ def test_new_entry_points_reject_bad_arguments_on_host(L):
     prm.precision = _lib.PHB_FP32_MIXED
     assert tc(C.byref(p), C.byref(prm), arr, arr, arr, ws, big, arr, 214 * 4 * p.n - 4, arr, None,
               None) == bad
+
+
+def test_host_step_and_record_region_check_arguments_on_host(L):
+    """phb_pc_step_host rejects missing outputs and a non-finite step before any
+    CUDA call; phb_record_region reports the records' place in the workspace
+    from the plan alone."""
+    from paper_1110_0836_gb300 import _lib
+    p = _plan()
+    assert L.phb_plan_init(C.byref(p)) == 0
+    prm = _lib.Params()
+    prm.gamma, prm.precision = 5.0 / 3.0, _lib.PHB_FP32_MIXED
+    ws, big = C.c_void_p(0x1000), p.ws_bytes
+    arr = C.c_void_p(0x2000)
+    bad = _lib.PHB_ERR_INVALID_ARG
+    step = L.phb_pc_step_host
+    assert step(C.byref(p), C.byref(prm), arr, arr, arr, None, arr, 0.1, ws, big, None, None) == bad
+    assert step(C.byref(p), C.byref(prm), arr, arr, arr, arr, None, 0.1, ws, big, None, None) == bad
+    assert step(C.byref(p), C.byref(prm), arr, arr, arr, arr, arr, float("inf"), ws, big, None,
+                None) == bad
+    assert step(C.byref(p), C.byref(prm), None, arr, arr, arr, arr, 0.1, ws, big, None, None) == bad
+    assert step(C.byref(p), C.byref(prm), arr, arr, arr, arr, arr, 0.1, ws, 16, None, None) == \
+        _lib.PHB_ERR_WORKSPACE
+    off, nbytes = C.c_size_t(), C.c_size_t()
+    assert L.phb_record_region(C.byref(p), C.byref(off), C.byref(nbytes)) == 0
+    assert nbytes.value == p.n * 24 * 4 and 0 < off.value and off.value + nbytes.value <= p.ws_bytes
+    assert off.value % 256 == 0
+    assert L.phb_record_region(None, C.byref(off), C.byref(nbytes)) == 1
+    assert L.phb_record_region(C.byref(p), None, C.byref(nbytes)) == 1

@@ -239,3 +239,53 @@ def test_host_buffer_step_matches_device_step():
     assert torch.equal(hpos, pos_d.cpu()) and torch.equal(hU, U_d.cpu())
     with pytest.raises(ValueError):
         phb.pc_step_host(plan, prm, pos_d, lam_d, U_d, dt)
+
+
+def _split_fp64(v):
+    """FP32 hi/lo split by its definition: h = fl32(v), l = fl32(v - h)."""
+    h = v.astype(np.float32)
+    return h, (v - h.astype(np.float64)).astype(np.float32)
+
+
+def test_records_are_the_fp64_hilo_split_bit_for_bit():
+    """The FP32 hi/lo records the fits read (split on the integer pipe) equal
+    h = fl32(v), l = fl32(v - h) bit for bit, for ordinary values and for
+    zeros, tiny, huge, exactly representable and tie-rounding ones."""
+    phb = need_gpu()
+    from paper_1110_0836_gb300 import _lib
+    import ctypes as C
+    w = workloads.random_modes(16, seed=41)
+    rng = np.random.default_rng(3)
+    n = w.n
+    U = w.U.copy()
+    special = np.array([0.0, -0.0, 1e-30, -3e-25, 7.5e-23, 2.0**-74, 2.0**-75, 1e30, -2.5e37,
+                        2.0**126 * 1.9, 1.0, -2.0, (2.0**24 + 1.0) * 2.0**-24,
+                        (2.0**23 + 0.5) * 2.0**-20, (2.0**23 + 1.5) * 2.0**-20,
+                        1.0 + 2.0**-24, 1.0 + 3 * 2.0**-25])
+    idx = rng.choice(n, size=(4, special.size), replace=False)
+    for f, row in zip((4, 5, 6, 7), idx):
+        U[f, row] = special
+    plan = phb.Plan.for_workload(w)
+    pos, lam, Ud = phb.tensors_of(w)
+    Ud.copy_(torch.as_tensor(U))
+    phb.build_neighbors(plan, pos, lam)
+    perm = phb.reorder(plan, pos, lam, Ud).cpu().numpy()   # arrays now in slot order
+    phb.build_neighbors(plan, pos, lam)
+    phb.mhd_rhs(plan, phb.Params(gamma=w.gamma, precision="fp64"), pos, lam, Ud)
+    torch.cuda.synchronize()
+    off, nbytes = C.c_size_t(), C.c_size_t()
+    assert _lib.lib().phb_record_region(C.byref(plan.c), C.byref(off), C.byref(nbytes)) == 0
+    assert nbytes.value == n * 24 * 4
+    rec = plan.ws[off.value:off.value + nbytes.value].view(torch.float32).cpu().numpy()
+    rec = rec.reshape(n, 24)
+    P, Us = pos.cpu().numpy(), Ud.cpu().numpy()
+    assert np.array_equal(Us, U[:, perm])
+    xh, xl = _split_fp64(P)
+    uh, ul = _split_fp64(Us)
+    layout = {0: xh[0], 1: xh[1], 2: xh[2], 4: xl[0], 5: xl[1], 6: xl[2],
+              8: uh[0], 9: uh[7], 10: uh[1], 11: uh[2], 12: ul[0], 13: ul[7], 14: ul[1],
+              15: ul[2], 16: uh[3], 17: uh[4], 18: uh[5], 19: uh[6], 20: ul[3], 21: ul[4],
+              22: ul[5], 23: ul[6]}
+    for col, want in layout.items():
+        got = rec[:, col]
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), col
