@@ -220,3 +220,21 @@ def test_reorder_into_storage_order():
     cells = np.floor(w.pos[:, p] / np.array(plan.c.cell)[:, None]).astype(np.int64)
     same = np.all(cells[:, 1:] == cells[:, :-1], axis=0).mean()
     assert same > 0.5
+
+
+def test_positions_outside_the_periodic_box():
+    """Positions shifted by whole box lengths on periodic axes (the cell wrap's
+    integer division below and above the box, and its FP64 form far outside)
+    give the brute-force sets of the same (shifted) positions."""
+    phb = need_gpu()
+    w = workloads.random_modes(12, seed=43)
+    rng = np.random.default_rng(9)
+    shifted = w.pos.copy()
+    k = rng.choice([-3, -2, -1, 1, 2, 5], size=shifted.shape)
+    pick = rng.random(shifted.shape) < 0.3
+    shifted[pick] += k[pick] * w.box_len[np.nonzero(pick)[0]]
+    shifted[0, 7] += 2.0**31 * w.box_len[0]   # far outside: the FP64 form of the wrap
+    w.pos = shifted
+    got, plan = gpu_sets(phb, w)
+    assert_equal_sets(got, oracle_sets(w))
+    assert plan.read_status() == 0
