@@ -354,3 +354,26 @@ def test_corrected_step_schedules_agree():
         assert np.array_equal(a, b)
     with pytest.raises(ValueError):
         phb.Params(gamma=w.gamma, refine_schedule="later").c()
+
+
+@pytest.mark.parametrize("tile", [64, 128])
+def test_corrected_step_under_both_tile_schedules(tile):
+    """The corrected step (every tile refined, in both of its schedules) under
+    the persistent tile schedule gives the time derivatives of one CTA per
+    tile bit for bit (the same tiles, staged relative to the same particles),
+    and both tile sizes meet 1e-5 against the oracle."""
+    phb = need_gpu()
+    w = workloads.shear_layer(60_000, seed=33)
+    q = sample(w.n, 400, seed=10)
+    exp, _ = oracle_run(w, query=q)
+    (go, ho), _ = oracle_run(w, "derivs", query=q)
+    sc = rhs_term_scales(w.U[:, q], go, ho, w.gamma)
+    ref_plan = phb.Plan.for_workload(w, tile=tile, schedule=0)
+    plan = phb.Plan.for_workload(w, tile=tile, schedule=1)
+    for sched in ("queue", "tile"):
+        prm = phb.Params(gamma=w.gamma, refine="on", refine_schedule=sched)
+        ref, _, _ = gpu_run(phb, w, prm, plan=ref_plan)
+        out, _, _ = gpu_run(phb, w, prm, plan=plan)
+        assert np.array_equal(out, ref), sched
+        assert plan.stats()["refined_tiles"] == plan.stats()["tiles"]
+        assert rhs_err(out[:, q], exp, sc).max() < 1e-5
