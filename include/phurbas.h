@@ -345,8 +345,10 @@ phb_status phb_pc_step(const phb_plan* plan, const phb_params* params, double* p
  * stream while the second right-hand side runs.  All of it is ordered on
  * `stream`: the outputs are valid once the stream has reached this point (a
  * synchronisation, an event).  Capturable in a CUDA graph after one eager
- * call.  Same results and status as phb_pc_step; PHB_ERR_INVALID_ARG also for
- * a NULL output. */
+ * call.  The side stream and its events are shared by all calls on a device:
+ * calls issued concurrently from several host threads must be serialised by
+ * the caller.  Same results and status as phb_pc_step; PHB_ERR_INVALID_ARG
+ * also for a NULL output. */
 phb_status phb_pc_step_host(const phb_plan* plan, const phb_params* params, const double* pos_in,
                             const double* lambda_in, const double* U_in, double* pos_out,
                             double* U_out, double dt, void* ws, size_t ws_bytes,
