@@ -64,17 +64,24 @@ def split(alpha):
 
 # Packed moment accumulation.  The 80 moments are held as 40 float2
 # accumulator pairs.  With the weighted basis pairs wp[k] = w qg2[k] (k < 8),
-# degree 2 and 3 are wp[5..7] and wp[0..4] themselves (packed adds), and a
-# packed FMA wp[k] * qg2[j] adds the two monomials (w q^(a_k + a_j),
-# w q^(b_k + b_j)) of pairs k = (a_k, b_k), j = (a_j, b_j).  PAIRED lists the
-# (k, j) products used for degrees 4, 5 and 6: a maximum matching of each
-# degree's moments under such products (5 of 15, 7 of 21 and 9 of 28 pairs;
-# no product pairs xxxy with another moment).  The remaining 22 moments take
-# one scalar FMA each, two to an accumulator pair: 40 packed and 22 scalar
-# instructions instead of 80 scalar ones.
-PAIRED = [(0, 8), (1, 8), (2, 8), (6, 6), (7, 7),
-          (0, 5), (0, 6), (0, 7), (1, 6), (2, 7), (3, 6), (4, 6),
-          (0, 0), (0, 1), (0, 2), (1, 1), (1, 3), (1, 4), (2, 2), (3, 3), (4, 4)]
+# degree 2 and 3 are wp[5..7] and wp[0..4] themselves (packed adds).  A packed
+# FMA adds two moments of degree 4..6 at once, either as wp[k] * qg2[j]
+# ("pair": (w q^(a_k + a_j), w q^(b_k + b_j)) for pairs k = (a_k, b_k),
+# j = (a_j, b_j)) or as one half of wp[k] broadcast over qg2[j] ("splat":
+# (w q^(h_k + a_j), w q^(h_k + b_j)); a broadcast operand costs no
+# instruction).  PRODUCTS lists the ones used for degrees 4, 5 and 6: a
+# maximum matching of each degree's moments under such products (7 of 15, 10
+# of 21 and 13 of 28 pairs).  The remaining 4 moments take one scalar FMA
+# each, two to an accumulator pair: 38 packed and 4 scalar instructions
+# instead of 80 scalar ones.
+PRODUCTS = [("pair", 0, 8), ("pair", 1, 8), ("pair", 2, 8), ("pair", 6, 6), ("pair", 7, 7),
+            ("splat", 3, 1, 8), ("splat", 4, 1, 8),
+            ("pair", 0, 5), ("pair", 0, 6), ("pair", 0, 7), ("pair", 1, 6), ("pair", 2, 7),
+            ("splat", 3, 1, 5), ("splat", 3, 1, 7), ("splat", 4, 1, 5), ("splat", 4, 1, 7),
+            ("splat", 6, 1, 3),
+            ("pair", 0, 0), ("pair", 0, 1), ("pair", 0, 2), ("pair", 1, 1), ("pair", 2, 2),
+            ("pair", 4, 4), ("splat", 1, 1, 3), ("splat", 1, 1, 4), ("splat", 2, 1, 4),
+            ("splat", 3, 0, 3), ("splat", 3, 0, 4), ("splat", 3, 1, 0), ("splat", 4, 1, 0)]
 NWP = 8  # weighted pairs formed (w q for basis pairs 0..7: cubic and quadratic)
 
 
@@ -82,15 +89,20 @@ def packed_moment_layout():
     """[(kind, operands, (alpha_x, alpha_y))] per accumulator pair, and alpha -> (pair, half)."""
     bp = [(BASIS[2 * j], BASIS[2 * j + 1] if 2 * j + 1 < NB else None) for j in range(10)]
     pairs = [("add", k, bp[k]) for k in (5, 6, 7, 0, 1, 2, 3, 4)]
-    for k, j in PAIRED:
-        h = (add(bp[k][0], bp[j][0]), add(bp[k][1], bp[j][1]))
+    for prod in PRODUCTS:
+        if prod[0] == "pair":
+            _, k, j = prod
+            h = (add(bp[k][0], bp[j][0]), add(bp[k][1], bp[j][1]))
+        else:
+            _, k, hk, j = prod
+            h = (add(bp[k][hk], bp[j][0]), add(bp[k][hk], bp[j][1]))
         assert h[0] != h[1] and sum(h[0]) == sum(h[1]) >= 4
-        pairs.append(("ffma2", (k, j), h))
+        pairs.append((prod[0], prod[1:], h))
     done = [a for p in pairs for a in p[2]]
-    assert len(done) == len(set(done)) == 58
+    assert len(done) == len(set(done)) == 76
     singles = [a for a in MOMENTS if a not in set(done)]
-    assert len(singles) == 22
-    for i in range(0, 22, 2):
+    assert len(singles) == 4
+    for i in range(0, 4, 2):
         pairs.append(("single", None, (singles[i], singles[i + 1])))
     assert len(pairs) == 40
     pos = {}
@@ -114,13 +126,17 @@ def gen_packed_moments(w):
     w("}")
     w("")
     w("// m2 += w q^alpha for the 80 moments in the packed layout: 8 packed adds,")
-    w("// 21 packed FMAs and 22 scalar FMAs.")
+    w("// 30 packed FMAs (a broadcast half of wp in 13 of them) and 4 scalar FMAs.")
     w("__device__ __forceinline__ void mls_accum_moments_p2(const float2 (&qg2)[kNB2], const float2 (&wp)[kNWP], float2 (&m2)[kNM2]) {")
     for p, (kind, op, h) in enumerate(pairs):
         if kind == "add":
             w(f"  m2[{p}] = __fadd2_rn(m2[{p}], wp[{op}]);  // {name(h[0])}, {name(h[1])}")
-        elif kind == "ffma2":
+        elif kind == "pair":
             w(f"  m2[{p}] = __ffma2_rn(wp[{op[0]}], qg2[{op[1]}], m2[{p}]);  // {name(h[0])}, {name(h[1])}")
+        elif kind == "splat":
+            k, hk, j = op
+            c = f"wp[{k}].{'xy'[hk]}"
+            w(f"  m2[{p}] = __ffma2_rn(make_float2({c}, {c}), qg2[{j}], m2[{p}]);  // {name(h[0])}, {name(h[1])}")
         else:
             for half, a in zip("xy", h):
                 b, g = split(a)
@@ -380,6 +396,31 @@ def gen():
         w(f"    y[{i}] = v * inv_diag[{i}]; }}")
     w("}")
     w("")
+    # ---- the same triangular solves for two right-hand sides at once (FP32
+    # pairs: b2[i] = (first field's b[i], second field's b[i])), packed FMAs
+    # with the factor's entries broadcast; each half rounds exactly as the
+    # scalar form
+    w("// mls_forward for two right-hand sides in the halves of b2.")
+    w("template <typename MT, typename DT>")
+    w("__device__ __forceinline__ void mls_forward2(const MT& L, const DT& inv_diag, float2 (&b)[kNB]) {")
+    for i in range(NB):
+        w(f"  {{ float2 v = b[{i}];")
+        for k in range(i):
+            w(f"    v = __ffma2_rn(make_float2(-L[{tri(i, k)}], -L[{tri(i, k)}]), b[{k}], v);")
+        w(f"    b[{i}] = __fmul2_rn(v, make_float2(inv_diag[{i}], inv_diag[{i}])); }}")
+    w("}")
+    w("")
+    for nm_, lo in (("mls_back9_2", 10), ("mls_back19_2", 0)):
+        w(f"// {nm_[:-2]} for two right-hand sides in the halves of y2.")
+        w("template <typename MT, typename DT>")
+        w(f"__device__ __forceinline__ void {nm_}(const MT& L, const DT& inv_diag, float2 (&y)[kNB]) {{")
+        for i in range(NB - 1, lo - 1, -1):
+            w(f"  {{ float2 v = y[{i}];")
+            for k in range(i + 1, NB):
+                w(f"    v = __ffma2_rn(make_float2(-L[{tri(k, i)}], -L[{tri(k, i)}]), y[{k}], v);")
+            w(f"    y[{i}] = __fmul2_rn(v, make_float2(inv_diag[{i}], inv_diag[{i}])); }}")
+        w("}")
+        w("")
     # ---- adjoint helpers: all monomials of degree 0..6 and polynomial gradients
     MONO = sorted({(a, b, c) for a in range(7) for b in range(7) for c in range(7) if a + b + c <= 6},
                   key=lambda e: (sum(e), [-x for x in e]))

@@ -569,8 +569,26 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   const bool solve = !singular && !routed;
   const float il = inv_l, il2 = inv_l * inv_l;
   if (solve && !refine) {
+    // two fields per solve: packed FMAs with the factor's entries broadcast
 #pragma unroll 1
-    for (int k = 0; k < G::NF; ++k) {
+    for (int k = 0; k + 1 < G::NF; k += 2) {
+      float2 b2[kNB];
+#pragma unroll
+      for (int j = 0; j < kNB; ++j)
+        b2[j] = make_float2(park[(k * kNB + j) * T + tid], park[((k + 1) * kNB + j) * T + tid]);
+      mls_forward2(M, invd, b2);
+      mls_back9_2(M, invd, b2);
+      float b0[kNB], b1[kNB];
+#pragma unroll
+      for (int j = kQuad0; j < kNB; ++j) {
+        b0[j] = b2[j].x;
+        b1[j] = b2[j].y;
+      }
+      park_derivs<T>(park + (k * kNB) * T + tid, b0, il, il2);
+      park_derivs<T>(park + ((k + 1) * kNB) * T + tid, b1, il, il2);
+    }
+    if (G::NF & 1) {
+      constexpr int k = G::NF - 1;
       float b[kNB];
 #pragma unroll
       for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
