@@ -332,6 +332,51 @@ __device__ __forceinline__ void park_derivs(float* d, const float (&b)[kNB], flo
   d[8 * T] = 2.f * b[kQuad0 + 5] * il2;
 }
 
+// Solves of NF fields with one factor: with Pair two fields at a time (packed
+// FMAs with the factor's entries broadcast; the last one alone when NF is
+// odd), else one at a time.  load(k, j) gives row j of field k's right-hand
+// side; use(k, b) takes its solution, all 19 coefficients (Full) or the
+// linear and quadratic ones.  (The full solves stay one field at a time: a
+// pair keeps the whole factor and 38 right-hand sides live and spills.)
+template <int NF, bool Full, bool Pair, class Load, class Use>
+__device__ __forceinline__ void solve_fields(const float (&M)[kNT], const float (&invd)[kNB], Load load,
+                                             Use use) {
+  constexpr int NP = Pair ? NF / 2 : 0;
+#pragma unroll 1
+  for (int k = 0; k < 2 * NP; k += 2) {
+    float2 b2[kNB];
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) b2[j] = make_float2(load(k, j), load(k + 1, j));
+    mls_forward2(M, invd, b2);
+    if constexpr (Full) {
+      mls_back19_2(M, invd, b2);
+    } else {
+      mls_back9_2(M, invd, b2);
+    }
+    float b0[kNB], b1[kNB];
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) {
+      b0[j] = b2[j].x;
+      b1[j] = b2[j].y;
+    }
+    use(k, b0);
+    use(k + 1, b1);
+  }
+#pragma unroll 1
+  for (int k = 2 * NP; k < NF; ++k) {
+    float b[kNB];
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) b[j] = load(k, j);
+    mls_forward(M, invd, b);
+    if constexpr (Full) {
+      mls_back19(M, invd, b);
+    } else {
+      mls_back9(M, invd, b);
+    }
+    use(k, b);
+  }
+}
+
 // Outputs of one fitted slot from its parked derivative rows: fit status
 // and gradients / Hessians (derivative mode) or the MHD time derivatives.
 // Singular fits (too few neighbours) report zero derivatives.  No barrier.
@@ -569,33 +614,9 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
   const bool solve = !singular && !routed;
   const float il = inv_l, il2 = inv_l * inv_l;
   if (solve && !refine) {
-    // two fields per solve: packed FMAs with the factor's entries broadcast
-#pragma unroll 1
-    for (int k = 0; k + 1 < G::NF; k += 2) {
-      float2 b2[kNB];
-#pragma unroll
-      for (int j = 0; j < kNB; ++j)
-        b2[j] = make_float2(park[(k * kNB + j) * T + tid], park[((k + 1) * kNB + j) * T + tid]);
-      mls_forward2(M, invd, b2);
-      mls_back9_2(M, invd, b2);
-      float b0[kNB], b1[kNB];
-#pragma unroll
-      for (int j = kQuad0; j < kNB; ++j) {
-        b0[j] = b2[j].x;
-        b1[j] = b2[j].y;
-      }
-      park_derivs<T>(park + (k * kNB) * T + tid, b0, il, il2);
-      park_derivs<T>(park + ((k + 1) * kNB) * T + tid, b1, il, il2);
-    }
-    if (G::NF & 1) {
-      constexpr int k = G::NF - 1;
-      float b[kNB];
-#pragma unroll
-      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
-      mls_forward(M, invd, b);
-      mls_back9(M, invd, b);
-      park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
-    }
+    solve_fields<G::NF, false, true>(
+        M, invd, [&](int k, int j) { return park[(k * kNB + j) * T + tid]; },
+        [&](int k, const float(&b)[kNB]) { park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2); });
   }
   // A refined tile of a set whose records fit in L2 hands its solved fits to
   // k_fit_refine: one queue position per fit (one atomic per warp), its
@@ -616,16 +637,12 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
       float* st = a.rstash + q;
 #pragma unroll 4
       for (int k = 0; k < kNM; ++k) st[k * static_cast<int64_t>(n)] = mstash[k * T + tid];
-#pragma unroll 1
-      for (int k = 0; k < G::NF; ++k) {
-        float b[kNB];
+      solve_fields<G::NF, true, false>(
+          M, invd, [&](int k, int j) { return park[(k * kNB + j) * T + tid]; },
+          [&](int k, const float(&b)[kNB]) {
 #pragma unroll
-        for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
-        mls_forward(M, invd, b);
-        mls_back19(M, invd, b);
-#pragma unroll
-        for (int j = 0; j < kNB; ++j) st[(kNM + k * kNB + j) * static_cast<int64_t>(n)] = b[j];
-      }
+            for (int j = 0; j < kNB; ++j) st[(kNM + k * kNB + j) * static_cast<int64_t>(n)] = b[j];
+          });
     }
   }
   if (solve && refine && !a.refine_queued) {
@@ -635,18 +652,14 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     // and quadratic ones (which the correction is added to) in the slot's
     // column of the stash
     float* cq = a.rstash + s;
-#pragma unroll 1
-    for (int k = 0; k < G::NF; ++k) {
-      float b[kNB];
+    solve_fields<G::NF, true, false>(
+        M, invd, [&](int k, int j) { return park[(k * kNB + j) * T + tid]; },
+        [&](int k, const float(&b)[kNB]) {
 #pragma unroll
-      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
-      mls_forward(M, invd, b);
-      mls_back19(M, invd, b);
+          for (int j = 0; j < kNB; ++j) park[(k * kNB + j) * T + tid] = b[j];
 #pragma unroll
-      for (int j = 0; j < kNB; ++j) park[(k * kNB + j) * T + tid] = b[j];
-#pragma unroll
-      for (int j = kQuad0; j < kNB; ++j) cq[(kNM + k * kNB + j) * static_cast<int64_t>(n)] = b[j];
-    }
+          for (int j = kQuad0; j < kNB; ++j) cq[(kNM + k * kNB + j) * static_cast<int64_t>(n)] = b[j];
+        });
     // residual passes over the neighbours from the global records (see
     // k_fit_refine)
     GlobalSrc src;
@@ -680,17 +693,15 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     float M2[kNT], invd2[kNB];
     mls_assemble_p2(mm, M2);
     mls_cholesky<float>(M2, invd2);
-#pragma unroll 1
-    for (int k = 0; k < G::NF; ++k) {
-      float b[kNB];
+    // one field at a time, as k_fit_refine solves it: the two schedules then
+    // round alike (the last scaling contracts with the added c0 into one FMA)
+    solve_fields<G::NF, false, false>(
+        M2, invd2, [&](int k, int j) { return park[(k * kNB + j) * T + tid]; },
+        [&](int k, float(&b)[kNB]) {
 #pragma unroll
-      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
-      mls_forward(M2, invd2, b);
-      mls_back9(M2, invd2, b);
-#pragma unroll
-      for (int j = kQuad0; j < kNB; ++j) b[j] += cq[(kNM + k * kNB + j) * static_cast<int64_t>(n)];
-      park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
-    }
+          for (int j = kQuad0; j < kNB; ++j) b[j] += cq[(kNM + k * kNB + j) * static_cast<int64_t>(n)];
+          park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
+        });
   }
   if (active && !routed && !deferred) write_outputs<MODE, T>(a, s, singular, park, tid);
   __syncthreads();  // the park region is reused by the next tile (persistent schedule)
@@ -795,17 +806,13 @@ __global__ void __launch_bounds__(T, 256 / T) k_fit_refine(const FitArgs a, cons
     mls_assemble_p2(mm, M);
     mls_cholesky<float>(M, invd);
     const float il = inv_l, il2 = inv_l * inv_l;
-#pragma unroll 1
-    for (int k = 0; k < G::NF; ++k) {
-      float b[kNB];
+    solve_fields<G::NF, false, false>(
+        M, invd, [&](int k, int j) { return park[(k * kNB + j) * T + tid]; },
+        [&](int k, float(&b)[kNB]) {
 #pragma unroll
-      for (int j = 0; j < kNB; ++j) b[j] = park[(k * kNB + j) * T + tid];
-      mls_forward(M, invd, b);
-      mls_back9(M, invd, b);
-#pragma unroll
-      for (int j = kQuad0; j < kNB; ++j) b[j] += st[(kNM + k * kNB + j) * n];
-      park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
-    }
+          for (int j = kQuad0; j < kNB; ++j) b[j] += st[(kNM + k * kNB + j) * n];
+          park_derivs<T>(park + (k * kNB) * T + tid, b, il, il2);
+        });
     write_outputs<MODE, T>(a, s, false, park, tid);
   }
 }

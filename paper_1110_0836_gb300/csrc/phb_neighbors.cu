@@ -131,8 +131,7 @@ struct Reach {
   bool wrap, open;
 };
 
-__device__ __forceinline__ Reach axis_reach(const Grid& g, int a, int c, double r) {
-  int R = static_cast<int>(ceil(r * g.inv_cell[a] * (1.0 + 1e-6)));
+__device__ __forceinline__ Reach axis_reach_cells(const Grid& g, int a, int c, int R) {
   Reach q;
   q.open = !g.periodic[a];
   if (g.periodic[a] && 2 * R + 1 >= g.ncell[a]) {
@@ -145,6 +144,10 @@ __device__ __forceinline__ Reach axis_reach(const Grid& g, int a, int c, double 
     q.wrap = g.periodic[a] != 0;
   }
   return q;
+}
+
+__device__ __forceinline__ Reach axis_reach(const Grid& g, int a, int c, double r) {
+  return axis_reach_cells(g, a, c, reach_cells(g, a, r));
 }
 
 __device__ __forceinline__ int axis_cell(const Grid& g, int a, const Reach& q, int k, bool& ok) {
@@ -453,18 +456,274 @@ __device__ __noinline__ void search_overflow(const Grid& g, const int2* __restri
   search_particle<kFillCsr>(g, clin, lin, cellc, scr, spos, r, s, base, end, out);
 }
 
+constexpr int kRunCap = 128;  // candidate runs a warp records (a reach of 3 cells: at most 98)
+
+// Per warp: the cell's particles being searched ("homes", 32 at a time, padded
+// to a multiple of four with homes that hit nothing) and the runs of their
+// common reach box.
+struct __align__(16) SearchWarp {
+  float nx[32], ny[32], nz[32];  // negated wrapped FP32 positions
+  float in2[32], out2[32];       // inner / outer screen radius^2
+  int slot[32];
+  double r2[32];                 // list radius^2 (exact test)
+  int run_t0[kRunCap];           // first linear-order record of each run
+  int run_pre[kRunCap + 1];      // candidates before each run (the last: the total)
+};
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane) {
+  int x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  return x - v;
+}
+
+// Squared FP32 screen distances of candidate o to two homes (a, b): packed
+// FP32x2, each half rounded as screen_d2 rounds it.
+template <bool kWrap>
+__device__ __forceinline__ float2 screen_d2_pair(const Grid& g, float4 o, float2 nx, float2 ny, float2 nz) {
+  float2 dx = __fadd2_rn(make_float2(o.x, o.x), nx);
+  float2 dy = __fadd2_rn(make_float2(o.y, o.y), ny);
+  float2 dz = __fadd2_rn(make_float2(o.z, o.z), nz);
+  if (kWrap) {
+    const float2 kx = __fmul2_rn(dx, make_float2(g.inv_lenf[0], g.inv_lenf[0]));
+    const float2 ky = __fmul2_rn(dy, make_float2(g.inv_lenf[1], g.inv_lenf[1]));
+    const float2 kz = __fmul2_rn(dz, make_float2(g.inv_lenf[2], g.inv_lenf[2]));
+    dx = __ffma2_rn(make_float2(-g.lenf[0], -g.lenf[0]), make_float2(rintf(kx.x), rintf(kx.y)), dx);
+    dy = __ffma2_rn(make_float2(-g.lenf[1], -g.lenf[1]), make_float2(rintf(ky.x), rintf(ky.y)), dy);
+    dz = __ffma2_rn(make_float2(-g.lenf[2], -g.lenf[2]), make_float2(rintf(kz.x), rintf(kz.y)), dz);
+  }
+  return __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+}
+
+// The candidates of one chunk (one per lane) against every home of the warp,
+// four homes per round (their loads and screens independent): a ballot per
+// home gives its hits, appended to its scratch row in lane order.
+template <bool kWrap>
+__device__ __forceinline__ void screen_chunk(const Grid& g, const double* __restrict__ spos,
+                                             const SearchWarp& S, int mh4, float4 o, int lane,
+                                             int& cnt, int32_t* __restrict__ ell) {
+  const int t = __float_as_int(o.w);
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll 1
+  for (int i = 0; i < mh4; i += 4) {
+    const float4 X = *reinterpret_cast<const float4*>(S.nx + i);
+    const float4 Y = *reinterpret_cast<const float4*>(S.ny + i);
+    const float4 Z = *reinterpret_cast<const float4*>(S.nz + i);
+    const float4 I2 = *reinterpret_cast<const float4*>(S.in2 + i);
+    const float4 O2 = *reinterpret_cast<const float4*>(S.out2 + i);
+    const int4 SL = *reinterpret_cast<const int4*>(S.slot + i);
+    const float2 d01 = screen_d2_pair<kWrap>(g, o, make_float2(X.x, X.y), make_float2(Y.x, Y.y),
+                                             make_float2(Z.x, Z.y));
+    const float2 d23 = screen_d2_pair<kWrap>(g, o, make_float2(X.z, X.w), make_float2(Y.z, Y.w),
+                                             make_float2(Z.z, Z.w));
+    const float d[4] = {d01.x, d01.y, d23.x, d23.y};
+    const float in2[4] = {I2.x, I2.y, I2.z, I2.w};
+    const float out2[4] = {O2.x, O2.y, O2.z, O2.w};
+    const int sl[4] = {SL.x, SL.y, SL.z, SL.w};
+    unsigned hit[4];
+    unsigned band = 0u;  // bit u: inside home u's band (the exact test decides)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool other = t != sl[u];
+      hit[u] = __ballot_sync(0xffffffffu, other && d[u] < in2[u]);
+      band |= (other && !(d[u] < in2[u]) && d[u] <= out2[u]) ? 1u << u : 0u;
+    }
+    if (__any_sync(0xffffffffu, band != 0u)) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        hit[u] |= __ballot_sync(0xffffffffu, ((band >> u) & 1u) &&
+                                                 dist2_exact(g, spos, g.n, sl[u], t) < S.r2[i + u]);
+    }
+    if ((hit[0] | hit[1] | hit[2] | hit[3]) != 0u) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (hit[u] == 0u) continue;
+        const int c = __shfl_sync(0xffffffffu, cnt, i + u);
+        if ((hit[u] >> lane) & 1u) {
+          const int e = c + __popc(hit[u] & lt);
+          if (e < g.ell) ell[static_cast<int64_t>(sl[u]) * g.ell + e] = t;
+        }
+        if (lane == i + u) cnt = c + __popc(hit[u]);
+      }
+    }
+  }
+}
+
+// Single pass, cell-major, for sets of one lambda: one warp per cell of the
+// linear order, its particles ("homes", 32 at a time) sharing one reach box.
+// The homes share one candidate sequence, the runs of their reach box in
+// the order of the particle-major search (rows in (x, y) offset order, the z
+// cells of a row as one or two runs of the linear-order records, slot order
+// inside a cell), taken 32 candidates per chunk, one per lane; each chunk is
+// screened against every home and a ballot per home appends its hits in lane
+// order, so every list equals the particle-major one.  Writes the exact list
+// lengths and the first g.ell entries of the lists it takes; a cell whose
+// homes differ in reach, or whose reach covers a whole periodic axis or has
+// more runs than a warp records, keeps the -1 of ncnt for k_search_ell.
+// (Where lambda varies the particle-major search alone is faster: sparse
+// cells leave most of a warp's homes empty, and cells of mixed reach would
+// send scattered particles to the second pass.)
+// One warp per block, so that the block scheduler hands out single cells
+// (32 resident per SM at 64 registers).
+__global__ void __launch_bounds__(32, 32) k_search_cells(Grid g, Lin lin,
+                                                     const double* __restrict__ spos,
+                                                     const double* __restrict__ slam,
+                                                     int32_t* __restrict__ ncnt,
+                                                     int32_t* __restrict__ ell) {
+  __shared__ SearchWarp S;
+  const int lane = threadIdx.x;
+  const int ncx = g.ncell[0], ncy = g.ncell[1], ncz = g.ncell[2];
+  const int64_t k = blockIdx.x;
+  if (k >= static_cast<int64_t>(ncx) * ncy * ncz) return;
+  const int h0 = lin.start[k], h1 = lin.start[k + 1];
+  const int cz = static_cast<int>(k % ncz);
+  const int cy = static_cast<int>((k / ncz) % ncy);
+  const int cx = static_cast<int>(k / (static_cast<int64_t>(ncz) * ncy));
+  for (int g0 = h0; g0 < h1; g0 += 32) {
+    const int mh = min(32, h1 - g0);
+    const bool mine = lane < mh;
+    float4 me = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    if (mine) me = lin.rec[g0 + lane];
+    const int s = __float_as_int(me.w);
+    double r = 0.0;
+    int R[3] = {0, 0, 0};
+    if (mine) {
+      r = list_radius(g, slam[s]);
+      for (int a = 0; a < 3; ++a) R[a] = reach_cells(g, a, r);
+    }
+    int U[3];
+    bool same = true;
+    for (int a = 0; a < 3; ++a) {
+      U[a] = __shfl_sync(0xffffffffu, R[a], 0);
+      same = same && (!mine || R[a] == U[a]);
+    }
+    if (!__all_sync(0xffffffffu, same) || U[0] < 0 || U[1] < 0 || U[2] < 0) continue;
+    const Reach qx = axis_reach_cells(g, 0, cx, U[0]);
+    const Reach qy = axis_reach_cells(g, 1, cy, U[1]);
+    const Reach qz = axis_reach_cells(g, 2, cz, U[2]);
+    const bool whole = (g.periodic[0] && !qx.wrap) || (g.periodic[1] && !qy.wrap) ||
+                       (g.periodic[2] && !qz.wrap);
+    const int64_t nrow = static_cast<int64_t>(qx.count) * qy.count;
+    if (whole || nrow > kRunCap) continue;
+    // the runs of the reach box, 32 rows at a time
+    int nrun = 0, total = 0;
+    for (int j0 = 0; j0 < nrow; j0 += 32) {
+      const int j = j0 + lane;
+      int nr = 0, ta = 0, la = 0, tb = 0, lb = 0;
+      if (j < nrow) {
+        const int kx = j / qy.count, ky = j - kx * qy.count;
+        bool okx, oky;
+        const int rx = axis_cell(g, 0, qx, kx, okx);
+        const int ry = axis_cell(g, 1, qy, ky, oky);
+        if (okx && oky) {
+          const int za = qz.start, zb = qz.start + qz.count - 1;
+          int a0 = za, b0 = zb, a1 = 0, b1 = -1;
+          if (!qz.wrap) {
+            a0 = max(za, 0);
+            b0 = min(zb, ncz - 1);
+          } else if (za < 0) {
+            a0 = za + ncz;
+            b0 = zb < 0 ? zb + ncz : ncz - 1;
+            b1 = zb < 0 ? -1 : zb;
+          } else if (zb >= ncz) {
+            a0 = za < ncz ? za : za - ncz;
+            b0 = za < ncz ? ncz - 1 : zb - ncz;
+            b1 = za < ncz ? zb - ncz : -1;
+          }
+          nr = (a0 <= b0 ? 1 : 0) + (a1 <= b1 ? 1 : 0);
+          if (a0 > b0) { a0 = a1; b0 = b1; }
+          const int64_t row = (static_cast<int64_t>(rx) * ncy + ry) * ncz;
+          if (nr >= 1) {
+            ta = lin.start[row + a0];
+            la = lin.start[row + b0 + 1] - ta;
+          }
+          if (nr == 2) {
+            tb = lin.start[row + a1];
+            lb = lin.start[row + b1 + 1] - tb;
+          }
+        }
+      }
+      const int rpos = nrun + warp_excl_scan(nr, lane);
+      const int cpos = total + warp_excl_scan(la + lb, lane);
+      if (rpos + nr <= kRunCap) {
+        if (nr >= 1) {
+          S.run_t0[rpos] = ta;
+          S.run_pre[rpos] = cpos;
+        }
+        if (nr == 2) {
+          S.run_t0[rpos + 1] = tb;
+          S.run_pre[rpos + 1] = cpos + la;
+        }
+      }
+      nrun = __shfl_sync(0xffffffffu, rpos + nr, 31);
+      total = __shfl_sync(0xffffffffu, cpos + la + lb, 31);
+    }
+    if (nrun > kRunCap) continue;
+    const int mh4 = (mh + 3) & ~3;
+    if (lane < mh4) {
+      Screen q = make_screen(g, r);
+      if (!mine) {  // padding: hits nothing
+        q.in2 = -1.f;
+        q.out2 = -1.f;
+      }
+      S.nx[lane] = -me.x;
+      S.ny[lane] = -me.y;
+      S.nz[lane] = -me.z;
+      S.in2[lane] = q.in2;
+      S.out2[lane] = q.out2;
+      S.slot[lane] = mine ? s : -2;
+      S.r2[lane] = q.r2;
+    }
+    if (lane == 0) S.run_pre[nrun] = total;
+    __syncwarp();
+    // the plain difference is the minimum image for the whole reach box
+    const bool plain = plain_axis(g, 0, cx, qx) && plain_axis(g, 1, cy, qy) && plain_axis(g, 2, cz, qz);
+    int run = 0;  // the run holding the next chunk's first candidate
+    // candidate v0 + lane (none past the end: a NaN record hits nothing)
+    auto fetch = [&](int v0) {
+      const int v = v0 + lane;
+      float4 o = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, __int_as_float(-1));
+      int rn = run;
+      if (v < total) {
+        while (S.run_pre[rn + 1] <= v) ++rn;
+        o = lin.rec[S.run_t0[rn] + (v - S.run_pre[rn])];
+      }
+      run = __shfl_sync(0xffffffffu, rn, 31);
+      return o;
+    };
+    int cnt = 0;  // lane i: the list length of home i so far
+    float4 next = fetch(0);
+    for (int v0 = 0; v0 < total; v0 += 32) {
+      const float4 o = next;
+      if (v0 + 32 < total) next = fetch(v0 + 32);  // one chunk ahead
+      if (plain) {
+        screen_chunk<false>(g, spos, S, mh4, o, lane, cnt, ell);
+      } else {
+        screen_chunk<true>(g, spos, S, mh4, o, lane, cnt, ell);
+      }
+    }
+    if (mine) ncnt[s] = cnt;
+    __syncwarp();  // the next group of homes rewrites the warp's records
+  }
+}
+
 // Single pass, thread per particle (slot order): exact list lengths and the
-// first g.ell entries of every list.
+// first g.ell entries of every list (after the cell-major search, left_only:
+// of the lists it left, ncnt still -1).
 __global__ void __launch_bounds__(kThreads, 4) k_search_ell(Grid g, const int2* __restrict__ clin,
                                                          Lin lin, const int32_t* __restrict__ cellc,
                                                          const float4* __restrict__ scr,
                                                          const double* __restrict__ spos,
                                                          const double* __restrict__ slam,
                                                          int32_t* __restrict__ ncnt,
-                                                         int32_t* __restrict__ ell) {
+                                                         int32_t* __restrict__ ell, bool left_only) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.n) return;
   if (s == g.n - 1) ncnt[g.n] = 0;  // the offsets scan's sentinel
+  if (left_only && ncnt[s] >= 0) return;
   const double r = list_radius(g, slam[s]);
   ncnt[s] = search_particle<kFillEll>(g, clin, lin, cellc, scr, spos, r, s, 0, 0,
                                       ell + static_cast<int64_t>(s) * g.ell);
@@ -1023,8 +1282,18 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   note_launch();
   const Lin lin{lscr, lstart};
   int32_t* ell = region<int32_t>(p, ws, R_ELL);
+  // one lambda: cell-major, then particle-major for the lists it left;
+  // lambda varying: particle-major
+  const bool cell_major = p->lambda_max <= 1.01 * p->lambda_min;
+  if (cell_major && (e = cudaMemsetAsync(ncnt, 0xff, static_cast<size_t>(n) * sizeof(int32_t), st)))
+    return e;
   int tr = trace_begin(4, st);
-  k_search_ell<<<blocks_for(n), kThreads, 0, st>>>(g, clin, lin, cellc, scr, spos, slam, ncnt, ell);
+  if (cell_major) {
+    k_search_cells<<<static_cast<unsigned>(ncells), 32, 0, st>>>(g, lin, spos, slam, ncnt, ell);
+    note_launch();
+  }
+  k_search_ell<<<blocks_for(n), kThreads, 0, st>>>(g, clin, lin, cellc, scr, spos, slam, ncnt, ell,
+                                                   cell_major);
   trace_end(tr, st);
   note_launch();
   if ((e = scan_exclusive_i32_to_i64(ncnt, off, n + 1, bsum, st))) return e;

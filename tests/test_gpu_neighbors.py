@@ -238,3 +238,89 @@ def test_positions_outside_the_periodic_box():
     got, plan = gpu_sets(phb, w)
     assert_equal_sets(got, oracle_sets(w))
     assert plan.read_status() == 0
+
+
+def _with_particles(w, extra_pos, extra_lam):
+    """w with particles appended (their states copied from the first ones)."""
+    k = extra_pos.shape[1]
+    w.pos = np.ascontiguousarray(np.concatenate([w.pos, extra_pos], axis=1))
+    w.lam = np.concatenate([w.lam, extra_lam])
+    w.U = np.ascontiguousarray(np.concatenate([w.U, w.U[:, :k]], axis=1))
+    return w
+
+
+def test_dense_cluster_in_one_cell():
+    """100 particles within a tenth of a lattice spacing of one point of a
+    12^3 lattice: one cell holds more particles than a warp searches at once
+    (the cell-major search takes them 32 at a time against the same
+    candidates); every set equals the brute force."""
+    phb = need_gpu()
+    w = workloads.random_modes(12, seed=21)
+    rng = np.random.default_rng(4)
+    h = w.box_len[0] / 12
+    c = (w.box_lo + 0.37 * w.box_len)[:, None]
+    w = _with_particles(w, c + 0.1 * h * (rng.random((3, 100)) - 0.5), np.full(100, w.lam.min()))
+    got, plan = gpu_sets(phb, w)
+    assert_equal_sets(got, oracle_sets(w))
+    assert plan.read_status() == 0
+
+
+def test_lambda_spread_within_cells():
+    """lambda spread 3x at random over a jittered 24^3 periodic lattice
+    (particles of 1 to 3 cells of reach side by side; the particle-major
+    search): sampled sets equal the brute force."""
+    phb = need_gpu()
+    w = workloads.random_modes(24, seed=31)
+    rng = np.random.default_rng(8)
+    w.lam = w.lam.min() * (1.0 + 2.0 * rng.random(w.n))
+    got, plan = gpu_sets(phb, w, nbr_capacity=w.n * 1600)
+    q = sample(w.n, 1200, seed=5)
+    assert_equal_sets(got, oracle_sets(w, q), q)
+    assert plan.read_status() == 0
+
+
+@pytest.mark.parametrize("cell_frac", [0.5, 0.4])
+def test_reach_of_two_cells(cell_frac):
+    """lambda twice the spacing of a jittered 20^3 lattice (~400 neighbours,
+    scratch rows that hold them) and cells of half or 0.4 of the list radius:
+    the cell-major search over a reach of two or three cells per axis (up to
+    98 runs per warp), cells of ~16 or ~8 particles; sampled sets equal the
+    brute force."""
+    phb = need_gpu()
+    w = workloads.random_modes(20, seed=37)
+    w.lam = 2.0 * w.lam
+    got, plan = gpu_sets(phb, w, cell_frac=cell_frac, ell_width=512, nbr_capacity=w.n * 480)
+    q = sample(w.n, 1000, seed=9)
+    assert_equal_sets(got, oracle_sets(w, q), q)
+    assert plan.read_status() == 0
+
+
+@pytest.mark.parametrize("big_factor", [1.0, 7.0])
+def test_open_box(big_factor):
+    """Open (non-periodic) 20^3 box, one lambda (the cell-major search, reach
+    rows outside the box skipped) or 40 particles of 7x the common lambda
+    (the particle-major search); sampled sets, with every large one and its
+    cell mates, equal the brute force."""
+    phb = need_gpu()
+    w = workloads.random_modes(20, seed=33)
+    w.periodic = np.zeros(3, np.int32)
+    rng = np.random.default_rng(6)
+    big = rng.choice(w.n, 40, replace=False)
+    w.lam = w.lam.copy()
+    w.lam[big] *= big_factor
+    got, plan = gpu_sets(phb, w, nbr_capacity=w.n * 400)
+    h = w.box_len[0] / 20
+    near = np.nonzero(np.min(np.abs(w.pos[:, :, None] - w.pos[:, None, big]).max(axis=0), axis=1) < 3 * h)[0]
+    q = np.unique(np.concatenate([sample(w.n, 800, seed=7), big, near]))
+    assert_equal_sets(got, oracle_sets(w, q), q)
+    assert plan.read_status() == 0
+
+
+def test_tiny_periodic_box_whole_axis_reach():
+    """A 6^3 periodic lattice: the reach of every cell covers each periodic
+    axis whole, so the cell-major search leaves every list to the
+    particle-major, cell-by-cell path; every set equals the brute force."""
+    phb = need_gpu()
+    w = workloads.random_modes(6, seed=35)
+    got, _ = gpu_sets(phb, w)
+    assert_equal_sets(got, oracle_sets(w))
