@@ -469,6 +469,11 @@ struct __align__(16) SearchWarp {
   int run_t0[kRunCap];           // first linear-order record of each run
   int run_pre[kRunCap + 1];      // candidates before each run (the last: the total)
 };
+// the home arrays are read four at a time as 16-byte vectors
+static_assert(offsetof(SearchWarp, nx) % 16 == 0 && offsetof(SearchWarp, ny) % 16 == 0 &&
+                  offsetof(SearchWarp, nz) % 16 == 0 && offsetof(SearchWarp, in2) % 16 == 0 &&
+                  offsetof(SearchWarp, out2) % 16 == 0 && offsetof(SearchWarp, slot) % 16 == 0,
+              "vector-read arrays of SearchWarp must be 16-byte aligned");
 
 __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
   int x = v;
