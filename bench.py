@@ -56,9 +56,9 @@ KERNEL_FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
 # scaled by the particles processed.  Absent = null.
 FIT_TRAFFIC = {
     "random_modes_64^3": (68647168 + 2780416, "ncu, this workload, one launch"),
-    "shock_tube_1048576": (287756800 + 836543488 + 1261519616 + 78016512,
+    "shock_tube_1048576": (287487744 + 836574208 + 1261656320 + 78807040,
                            "ncu, this workload, one launch of each of the two fit kernels"),
-    "shear_layer_8000000": (8 * (473725696 + 285469184),
+    "shear_layer_8000000": (8 * (474379264 + 285629440),
                             "ncu on the 1,000,000-particle set of the same recipe with the "
                             "corrected step in the tiles (the 8M set's schedule), x 8 "
                             "(particles processed)"),
