@@ -720,9 +720,10 @@ def run_ours(args):
            "d2h_bytes_per_step": int(opos.numel() + oU.numel()) * 8,
            "path": "phb_pc_step_host on pinned host arrays: pos and lambda uploaded, U uploaded "
                    "on a side stream during the neighbour build, the predictor-corrector step, "
-                   "the new pos and U downloaded (HostStepGraph replay, or the eager call with "
-                   "--no-graph); host wall clock around each step with a synchronize on both "
-                   "sides"}
+                   "the new pos downloaded beside the second right-hand side and the new U "
+                   "written to the host by the corrector's fit (the rest after the step) "
+                   "(HostStepGraph replay, or the eager call with --no-graph); host wall clock "
+                   "around each step with a synchronize on both sides"}
 
     # ---------------- measured FMA peaks (project probe) and the FP64 path's roofline
     p32 = fma_peak_tflops(L, dev, 1, sm_count)

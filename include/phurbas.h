@@ -342,7 +342,14 @@ phb_status phb_pc_step(const phb_plan* plan, const phb_params* params, double* p
  * per device, made on first use and kept) while the neighbour lists are built,
  * and the stream waits for it before U is read; x^{n+1}, which needs only V^n
  * and V^p, is corrected right after the predictor and downloaded on the side
- * stream while the second right-hand side runs.  All of it is ordered on
+ * stream while the second right-hand side runs.  When U_out is page-locked
+ * and mapped (cudaHostAlloc / cudaHostRegister memory under unified
+ * addressing) in the FP32-mixed precision, the corrector's fused fit writes
+ * U^{n+1} of its final fits straight to U_out wherever the 32 particles of a
+ * warp have caller indices within 64 of each other (storage order,
+ * phb_reorder), and the rest (fits routed to FP64 or queued for the corrected
+ * step, frozen particles, scattered warps) follows by a kernel after the
+ * step; otherwise U^{n+1} is copied back once at the end.  All of it is ordered on
  * `stream`: the outputs are valid once the stream has reached this point (a
  * synchronisation, an event).  Capturable in a CUDA graph after one eager
  * call.  The side stream and its events are shared by all calls on a device:

@@ -454,6 +454,7 @@ template <int T>
 struct FitShared {
   int tile;         // persistent schedule: tile taken from the queue
   int wfar[T / 32];  // per warp: staged an offset at or beyond a quarter box length
+  uint8_t fin[T];   // host-buffer corrector: the tile particle's fit is final here
 };
 
 // Stage a tile's neighbourhood (count records, slots from the plan) in shared
@@ -501,6 +502,35 @@ __device__ __forceinline__ bool stage_tile(const FitArgs& a, const Per32& P, con
     }
   }
   return far;
+}
+
+// Host-buffer step, corrector evaluation: thread t takes the tile's slot
+// s0 + t (slot order) and, where its fit is final (not routed to FP64, not
+// queued for the corrected step, not frozen) and the caller indices of its
+// warp's slots lie within 64 of each other (so that the warp's host writes
+// stay on a few lines), writes U^{n+1} = Y^n + h (F(Y^n) + F(Y^p)) - the
+// corrector's arithmetic, with F(Y^p) read back from this tile's dudt - to
+// the caller's row of the mapped host array; pc_done marks the slots
+// written.  Called by all T threads after a barrier that follows the
+// tile's output writes.
+template <int T>
+__device__ __forceinline__ void host_u_tile(const FitArgs& a, int s0, int cnt, const FitShared<T>& sh,
+                                            int tid) {
+  const int64_t n = a.n;
+  const bool ok = tid < cnt;
+  const int s = s0 + tid;
+  const int i = ok ? a.pc_perm[s] : 0;
+  const int lo = __reduce_min_sync(0xffffffffu, ok ? i : 0x7fffffff);
+  const int hi = __reduce_max_sync(0xffffffffu, ok ? i : -1);
+  const bool near = hi >= lo && hi - lo < 64;
+  const bool w = ok && near && sh.fin[tid] != 0 && !(a.pc_frozen && a.pc_frozen[i]);
+  if (w) {
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+      a.u_host[f * n + i] =
+          __fma_rn(a.pc_h, __dadd_rn(a.pc_f0[f * n + s], a.dudt[f * n + s]), a.pc_y0[(3 + f) * n + s]);
+  }
+  if (ok) a.pc_done[s] = w ? 1 : 0;
 }
 
 // One tile: stage its neighbourhood, accumulate, solve, write outputs.  All
@@ -704,6 +734,11 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
         });
   }
   if (active && !routed && !deferred) write_outputs<MODE, T>(a, s, singular, park, tid);
+  if (MODE == FitMode::kRHS && a.u_host != nullptr && !listed) {
+    if (active) sh.fin[mine] = (!routed && !deferred) ? 1 : 0;
+    __syncthreads();  // the tile's outputs and marks are written
+    host_u_tile<T>(a, s0, cnt_tile, sh, tid);
+  }
   __syncthreads();  // the park region is reused by the next tile (persistent schedule)
 }
 

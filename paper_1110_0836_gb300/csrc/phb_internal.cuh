@@ -57,6 +57,7 @@ enum Region {
   R_PC_F1,       // double [8][n] F(Y^p) (slot order)        -- PC step
   R_PC_Y0,       // double [11][n] saved x^n, U^n (slot order) -- PC step
   R_PC_IO,       // double [12][n] pos, lambda, U (caller order) of phb_pc_step_host -- PC step
+  R_PC_DONE,     // uint8 [n] slots whose U^{n+1} the corrector's fit wrote to the host -- PC step
   R_ADJ_ROFF,    // int64 [n+1] reverse-list offsets                     -- adjoint
   R_ADJ_RSRC,    // int32 [capacity] reverse lists: the particles naming each particle -- adjoint
   R_ADJ_RCNT,    // int32 [n+1] reverse-list counts / cursors            -- adjoint
@@ -408,6 +409,29 @@ struct FitArgs {
   int32_t* rq_len;             // their count (zeroed before the launch)
   float* rstash;               // [kNM + 8*19][n] moments and first solves, queue order
   int32_t* refined_tiles;      // count of refined tiles (zeroed before the launch)
+  // host-buffer step, corrector evaluation (u_host null: off): each tile
+  // writes U^{n+1} = Y^n + h (F(Y^n) + F(Y^p)) of its final fits straight to
+  // the caller's page-locked U_out, where a warp's slots map to nearby caller
+  // indices, and marks those slots in pc_done
+  double* u_host;              // mapped host [8][n], caller order
+  const double* pc_y0;         // [11][n] slot order: x^n, U^n
+  const double* pc_f0;         // [8][n] slot order: F(Y^n)
+  const int32_t* pc_perm;      // slot -> caller index
+  const uint8_t* pc_frozen;    // caller order, or null
+  uint8_t* pc_done;            // [n] slot order
+  double pc_h;                 // dt / 2
+};
+
+// What the corrector's fit of the host-buffer step needs for its direct
+// write of U^{n+1} (FitArgs.u_host and the pc_ fields).
+struct HostU {
+  double* u_host;
+  const double* y0;
+  const double* f0;
+  const int32_t* perm;
+  const uint8_t* frozen;
+  uint8_t* done;
+  double h;
 };
 
 // Fused FP32-mixed fit over all slots (list == null, staged tiles) or over
@@ -454,6 +478,6 @@ cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMo
                     const int32_t* perm_out, double* dudt, double* grad, double* hess,
                     int32_t* fit_status, int32_t* status_word, cudaStream_t st,
                     const int32_t* list = nullptr, const int32_t* list_len = nullptr,
-                    int64_t list_cap = 0);
+                    int64_t list_cap = 0, const HostU* hu = nullptr);
 
 }  // namespace phb

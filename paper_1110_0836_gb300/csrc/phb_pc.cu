@@ -52,19 +52,32 @@ __global__ void k_correct(int n, double dt, const int32_t* __restrict__ perm,
                           const uint8_t* __restrict__ frozen, const double* __restrict__ y0,
                           const double* __restrict__ sU_p, const double* __restrict__ f0,
                           const double* __restrict__ f1, double* __restrict__ pos,
-                          double* __restrict__ U, int parts) {
+                          double* __restrict__ U, int parts, const uint8_t* __restrict__ done) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int64_t N = n;
   const int i = perm[s];
   if (frozen && frozen[i]) return;
   const double h = 0.5 * dt;
+  // x^n + h (V^n + V^p), U^n + h (F(Y^n) + F(Y^p)): one rounding of the sum,
+  // one fused multiply-add (the corrector's fit writes U^{n+1} the same way)
   if (parts & 1)
     for (int a = 0; a < 3; ++a)
-      pos[a * N + i] = y0[a * N + s] + h * (y0[(3 + 1 + a) * N + s] + sU_p[(1 + a) * N + s]);
-  if (parts & 2)
+      pos[a * N + i] = __fma_rn(h, __dadd_rn(y0[(3 + 1 + a) * N + s], sU_p[(1 + a) * N + s]), y0[a * N + s]);
+  if ((parts & 2) && !(done && done[s]))  // (done: already on the host)
     for (int f = 0; f < 8; ++f)
-      U[f * N + i] = y0[(3 + f) * N + s] + h * (f0[f * N + s] + f1[f * N + s]);
+      U[f * N + i] = __fma_rn(h, __dadd_rn(f0[f * N + s], f1[f * N + s]), y0[(3 + f) * N + s]);
+}
+
+// Host-buffer step: U^{n+1} of the particles the corrector's fit did not
+// write to the host (routed or queued fits, frozen particles, warps of
+// scattered caller indices), in caller order, to the mapped host array.
+__global__ void k_download_rest(int n, const int32_t* __restrict__ inv, const uint8_t* __restrict__ done,
+                                const double* __restrict__ U, double* __restrict__ U_host) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || done[inv[i]]) return;
+  const int64_t N = n;
+  for (int f = 0; f < 8; ++f) U_host[f * N + i] = U[f * N + i];
 }
 
 // Side work of the host-buffer step: the upload of U to wait for before U is
@@ -75,6 +88,7 @@ struct PcOverlap {
   cudaStream_t side = nullptr;
   cudaEvent_t pos_ready = nullptr, pos_copied = nullptr;
   double* pos_out = nullptr;
+  double* U_host = nullptr;  // mapped U_out: U^{n+1} written by the corrector (else copied after)
 };
 
 // The step on device arrays, with the overlaps of `ov` if given.
@@ -103,7 +117,8 @@ phb_status pc_step_impl(const phb_plan* plan, const phb_params* prm, double* pos
   note_launch();
   if (ov) {
     // x^{n+1} now, and its download beside the second fit
-    k_correct<<<blocks, kThreads, 0, st>>>(n, dt, perm, prm->frozen, y0, sU, f0, nullptr, pos, U, 1);
+    k_correct<<<blocks, kThreads, 0, st>>>(n, dt, perm, prm->frozen, y0, sU, f0, nullptr, pos, U, 1,
+                                           nullptr);
     note_launch();
     if ((e = cudaEventRecord(ov->pos_ready, st)) ||
         (e = cudaStreamWaitEvent(ov->side, ov->pos_ready, 0)) ||
@@ -112,12 +127,22 @@ phb_status pc_step_impl(const phb_plan* plan, const phb_params* prm, double* pos
         (e = cudaEventRecord(ov->pos_copied, ov->side)))
       return launch_status(e);
   }
+  // the corrector; on the host-buffer step with a mapped U_out its fit writes
+  // U^{n+1} of most particles straight to the host, the rest follows
+  const bool direct = ov && ov->U_host && prm->precision == PHB_FP32_MIXED;
+  uint8_t* done = direct ? region<uint8_t>(plan, ws, R_PC_DONE) : nullptr;
+  HostU hu{ov ? ov->U_host : nullptr, y0, f0, perm, prm->frozen, done, 0.5 * dt};
   if ((e = run_fit(plan, prm, ws, FitMode::kRHS, nullptr, f1, nullptr, nullptr, nullptr,
-                   status_word, st)))
+                   status_word, st, nullptr, nullptr, 0, direct ? &hu : nullptr)))
     return launch_status(e);
   k_correct<<<blocks, kThreads, 0, st>>>(n, dt, perm, prm->frozen, y0, sU, f0, f1, pos, U,
-                                         ov ? 2 : 3);
+                                         ov ? 2 : 3, done);
   note_launch();
+  if (direct) {
+    k_download_rest<<<blocks, kThreads, 0, st>>>(n, region<int32_t>(plan, ws, R_INV), done, U,
+                                                 ov->U_host);
+    note_launch();
+  }
   if (ov && (e = cudaStreamWaitEvent(st, ov->pos_copied, 0))) return launch_status(e);
   return launch_status(cudaSuccess);
 }
@@ -202,9 +227,19 @@ extern "C" phb_status phb_pc_step_host(const phb_plan* plan, const phb_params* p
   ov.pos_ready = ss->pos_ready;
   ov.pos_copied = ss->pos_copied;
   ov.pos_out = pos_out;
+  // a page-locked, mapped U_out takes U^{n+1} from the kernels themselves
+  // (the corrector's fit for most particles); otherwise one copy after the step
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, U_out) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr)
+      ov.U_host = static_cast<double*>(pa.devicePointer);
+  } else {
+    cudaGetLastError();  // an unregistered pointer: clear the error, copy instead
+  }
   if ((s = pc_step_impl(plan, prm, dpos, dlam, dU, dt, ws, status_word, st, &ov)) != PHB_OK)
     return s;
-  if ((e = cudaMemcpyAsync(U_out, dU, 8 * n * sizeof(double), cudaMemcpyDeviceToHost, st)))
+  if (!(ov.U_host && prm->precision == PHB_FP32_MIXED) &&
+      (e = cudaMemcpyAsync(U_out, dU, 8 * n * sizeof(double), cudaMemcpyDeviceToHost, st)))
     return launch_status(e);
   return PHB_OK;
 }

@@ -355,6 +355,8 @@ extern "C" phb_status phb_plan_init(phb_plan* p) {
   pc += align256(size_t(11) * n * 8);
   p->ws_off[R_PC_IO] = pc;
   pc += align256(size_t(12) * n * 8);
+  p->ws_off[R_PC_DONE] = pc;
+  pc += align256(size_t(n));
   // adjoint regions overlay the PC ones
   size_t ad = off;
   p->ws_off[R_ADJ_ROFF] = ad;

@@ -132,14 +132,31 @@ FitArgs fit_args(const phb_plan* plan, const phb_params* prm, void* ws, const in
   a.rq_len = a.queue_len + 6;
   a.rstash = region<float>(plan, ws, R_RSTASH);
   a.refined_tiles = a.queue_len + 5;
+  a.u_host = nullptr;
+  a.pc_y0 = nullptr;
+  a.pc_f0 = nullptr;
+  a.pc_perm = nullptr;
+  a.pc_frozen = nullptr;
+  a.pc_done = nullptr;
+  a.pc_h = 0.0;
   return a;
 }
 
 cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMode mode,
                     const int32_t* perm_out, double* dudt, double* grad, double* hess,
                     int32_t* fit_status, int32_t* status_word, cudaStream_t st,
-                    const int32_t* list, const int32_t* list_len, int64_t list_cap) {
+                    const int32_t* list, const int32_t* list_len, int64_t list_cap,
+                    const HostU* hu) {
   FitArgs a = fit_args(plan, prm, ws, perm_out, dudt, grad, hess, fit_status, status_word);
+  if (hu && mode == FitMode::kRHS && !list && !perm_out && prm->precision != PHB_FP64) {
+    a.u_host = hu->u_host;
+    a.pc_y0 = hu->y0;
+    a.pc_f0 = hu->f0;
+    a.pc_perm = hu->perm;
+    a.pc_frozen = hu->frozen;
+    a.pc_done = hu->done;
+    a.pc_h = hu->h;
+  }
   cudaError_t e;
   if (prm->precision == PHB_FP64) return launch_fit_fp64(a, mode, list, list_len, st);
   if ((e = cudaMemsetAsync(a.queue_len, 0, sizeof(int32_t), st))) return e;

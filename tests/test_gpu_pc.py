@@ -241,6 +241,102 @@ def test_host_buffer_step_matches_device_step():
         phb.pc_step_host(plan, prm, pos_d, lam_d, U_d, dt)
 
 
+def _corrector_marks(phb, plan):
+    """Per slot: 1 where the corrector's fit of the last host-buffer step wrote
+    U^{n+1} to the host itself (the step part of the workspace ends with these
+    n bytes, 256-byte aligned)."""
+    from paper_1110_0836_gb300 import _lib
+    _, end = _lib.workspace_part(plan.c, _lib.PART_STEP)
+    n = plan.n
+    b = end - ((n + 255) // 256) * 256
+    return plan.ws[b:b + n].cpu().numpy()
+
+
+@pytest.mark.parametrize("order", ["storage", "generator"])
+def test_host_step_direct_write_matches_device_step(order):
+    """phb_pc_step_host with page-locked outputs: the corrector's fit writes
+    U^{n+1} straight to the host wherever a warp's slots have nearby caller
+    indices (most particles in the library's storage order, few in the
+    generator's) and the step copies the rest; with frozen particles, fits
+    routed to FP64 and fits queued for the corrected step, the outputs equal
+    phb_pc_step's bit for bit, and so do pageable outputs (one copy)."""
+    phb = need_gpu()
+    w = workloads.shear_layer(20_000, seed=12)
+    vmax = float(np.sqrt((w.U[1:4] ** 2).sum(0)).max())
+    dt = 0.05 * float(w.lam.min()) / max(vmax, 1.0)
+    skin = max(4.0 * dt * vmax, 0.02 * 2.3 * float(w.lam.min()))
+    plan = phb.Plan.for_workload(w, skin=skin)
+    pos_d, lam_d, U_d = phb.tensors_of(w)
+    frozen = np.random.default_rng(3).random(w.n) < 0.1
+    if order == "storage":
+        phb.build_neighbors(plan, pos_d, lam_d)
+        perm = phb.reorder(plan, pos_d, lam_d, U_d)
+        frozen = frozen[perm.cpu().numpy()]
+    prm = phb.Params(gamma=w.gamma, refine="on", cond_threshold=300.0,
+                     frozen=torch.from_numpy(frozen).cuda())
+    hpos, hlam, hU = (t.cpu().pin_memory() for t in (pos_d, lam_d, U_d))
+    opos, oU = torch.empty_like(hpos).pin_memory(), torch.empty_like(hU).pin_memory()
+    phb.pc_step_host(plan, prm, hpos, hlam, hU, dt, opos, oU)
+    torch.cuda.synchronize()
+    host_status = plan.read_status()
+    marks = _corrector_marks(phb, plan)
+    st = plan.stats()
+    assert st["routed_to_fp64"] > 0 and st["refined_tiles"] == st["tiles"]
+    plan.reset_status()
+    phb.pc_step(plan, prm, pos_d, lam_d, U_d, dt)
+    torch.cuda.synchronize()
+    assert plan.read_status() == host_status
+    assert torch.equal(opos, pos_d.cpu()) and torch.equal(oU, U_d.cpu())
+    assert np.array_equal(oU.numpy()[:, frozen], hU.numpy()[:, frozen])
+    # every solved fit is queued for the corrected step here (refine "on",
+    # lambda varies, the records fit in L2): tiles write only the few fits
+    # they finish themselves (too few neighbours to solve)
+    assert marks.mean() < 0.05
+    # pageable outputs: the copy after the step
+    ppos, pU = torch.empty_like(hpos), torch.empty_like(hU)
+    assert not pU.is_pinned()
+    phb.pc_step_host(plan, prm, hpos, hlam, hU, dt, ppos, pU)
+    torch.cuda.synchronize()
+    assert torch.equal(ppos, pos_d.cpu()) and torch.equal(pU, U_d.cpu())
+
+
+@pytest.mark.parametrize("order", ["storage", "generator"])
+def test_host_step_direct_write_plain_fits(order):
+    """The same on a lattice (no refined tile, no fit routed to FP64: the
+    lattice's fits are all about equally well conditioned) with some
+    particles frozen: in storage order the corrector's tiles write every
+    other particle's U^{n+1} to the host, in the generator's order few; the
+    outputs equal phb_pc_step's bit for bit either way."""
+    phb = need_gpu()
+    w = workloads.random_modes(24, seed=26, amp=0.05)
+    dt, skin = 0.002, 0.02
+    plan = phb.Plan.for_workload(w, skin=skin)
+    pos_d, lam_d, U_d = phb.tensors_of(w)
+    frozen = np.random.default_rng(4).random(w.n) < 0.05
+    if order == "storage":
+        phb.build_neighbors(plan, pos_d, lam_d)
+        perm = phb.reorder(plan, pos_d, lam_d, U_d)
+        frozen = frozen[perm.cpu().numpy()]
+    hpos, hlam, hU = (t.cpu().pin_memory() for t in (pos_d, lam_d, U_d))
+    opos, oU = torch.empty_like(hpos).pin_memory(), torch.empty_like(hU).pin_memory()
+    prm = phb.Params(gamma=w.gamma, refine="off", frozen=torch.from_numpy(frozen).cuda())
+    phb.pc_step_host(plan, prm, hpos, hlam, hU, dt, opos, oU)
+    torch.cuda.synchronize()
+    assert plan.stats()["routed_to_fp64"] == 0
+    host_status = plan.read_status()
+    marks = _corrector_marks(phb, plan)
+    plan.reset_status()
+    phb.pc_step(plan, prm, pos_d, lam_d, U_d, dt)
+    torch.cuda.synchronize()
+    assert plan.read_status() == host_status
+    assert torch.equal(opos, pos_d.cpu()) and torch.equal(oU, U_d.cpu())
+    if order == "storage":
+        assert marks.sum() == w.n - frozen.sum()
+    else:
+        assert marks.mean() < 0.5
+        assert marks.sum() <= w.n - frozen.sum()
+
+
 def _split_fp64(v):
     """FP32 hi/lo split by its definition: h = fl32(v), l = fl32(v - h)."""
     h = v.astype(np.float32)
