@@ -84,7 +84,7 @@ def parse():
                          "set of the same recipe for captures that must stay small; 0 = as named)")
     ap.add_argument("--tile", type=int, default=0, help="fit tile (64 or 128; 0 = library default)")
     ap.add_argument("--schedule", type=int, default=0,
-                    help="0 = one CTA per tile, 1 = persistent CTAs over a cost-ordered tile queue")
+                    help="0 = one CTA per tile in cell order, 1 = one CTA per tile in descending-cost order")
     ap.add_argument("--cell-frac", type=float, default=0.0, help="cell edge / min radius (0 = default)")
     ap.add_argument("--particle-order", choices=["storage", "generator"], default="storage",
                     help="storage: arrays put once into the library's storage order (phb_reorder) "
@@ -527,8 +527,9 @@ def run_ours(args):
     kflops = KERNEL_FLOP_PER_NEIGHBOUR * nbr_inside + KERNEL_FLOP_PER_PARTICLE * n
     peak = sm_count * FP32_LANES * 2 * mhz * 1e6 / 1e12
     achieved = flops / (fit_avg * 1e-3) / 1e12
-    kname = "k_fit_mixed_persistent" if plan.c.schedule == 1 else "k_fit_mixed"
-    tr = FIT_TRAFFIC.get(w.name) if (kname == "k_fit_mixed" and int(plan.c.tile) == 128) else None
+    kname = "k_fit_mixed"
+    # the captured traffic is of the default shape: 128-particle tiles in cell order
+    tr = FIT_TRAFFIC.get(w.name) if (int(plan.c.schedule) == 0 and int(plan.c.tile) == 128) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None if tr is None else tr[0],
                 "traffic_unit": "DRAM bytes read + written per launch (ncu, profiles/)",

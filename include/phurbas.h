@@ -67,8 +67,7 @@ typedef enum {
 #define PHB_FLAG_SKIN 0x02
 #define PHB_FLAG_FIT_SINGULAR 0x04
 #define PHB_FLAG_NONFINITE 0x08
-#define PHB_FLAG_TIMEOUT 0x10 /* reserved: no kernel waits on another - the persistent
-                                 tile queue is a wait-free counter - so none sets it */
+#define PHB_FLAG_TIMEOUT 0x10 /* reserved: no kernel waits on another, so none sets it */
 #define PHB_FLAG_LAMBDA_RANGE 0x20 /* a lambda outside the plan's [lambda_min, lambda_max] */
 #define PHB_FLAG_BAD_INDEX 0x40    /* an active-subset index outside [0, n) (it was skipped) */
 
@@ -153,8 +152,8 @@ typedef struct {
   double cell_frac;      /* cell edge / (rf_factor*lambda_min + skin); 0 = default 1 */
   int32_t tile;          /* particles per fused-fit tile (64 or 128; 0 = default 128) */
   int32_t stage_cap;     /* neighbourhood records staged per tile (0 = default) */
-  int32_t schedule;      /* fused fit: 0 = one CTA per tile in cell order; 1 = persistent CTAs
-                            taking tiles from a queue in descending-cost order */
+  int32_t schedule;      /* fused fit: 0 = one CTA per tile in cell order; 1 = one CTA per
+                            tile in descending-cost order (longest lists first) */
   int32_t ell_width;     /* neighbour search: list entries kept per particle in the
                             single-pass scratch (0 = default: 128, or 256 when
                             lambda_max > 1.26 lambda_min; longer lists are

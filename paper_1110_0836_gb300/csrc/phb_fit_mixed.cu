@@ -442,8 +442,7 @@ struct TileArgs {
   const uint8_t* tmap;    // per tile: thread -> tile particle (longest list first)
   const uint16_t* lidx;
   int32_t* fallback_count;
-  const int32_t* order;   // tile order (persistent schedule)
-  int32_t* queue_head;    // persistent tile-queue counter (zeroed before the launch)
+  const int32_t* order;   // tile of each CTA in descending cost (schedule 1), or null
   int32_t ntiles;
   const int32_t* list;      // active subset: slots (ascending), or null for all particles
   const int32_t* list_len;  // device count of the active subset
@@ -452,7 +451,6 @@ struct TileArgs {
 // Shared memory of one CTA besides the dynamic park/staging region.
 template <int T>
 struct FitShared {
-  int tile;         // persistent schedule: tile taken from the queue
   int wfar[T / 32];  // per warp: staged an offset at or beyond a quarter box length
   uint8_t fin[T];   // host-buffer corrector: the tile particle's fit is final here
 };
@@ -739,7 +737,6 @@ __device__ __forceinline__ void fit_tile(const FitArgs& a, const Per32& P, const
     __syncthreads();  // the tile's outputs and marks are written
     host_u_tile<T>(a, s0, cnt_tile, sh, tid);
   }
-  __syncthreads();  // the park region is reused by the next tile (persistent schedule)
 }
 
 template <FitMode MODE, int T>
@@ -751,27 +748,10 @@ __global__ void __launch_bounds__(T, 256 / T) k_fit_mixed(const FitArgs a, const
   __shared__ FitShared<T> sh;
   float* park = reinterpret_cast<float*>(smem4);
   float4* stage = smem4 + (G::NA * kNB * T) / 4;
-  fit_tile<MODE, T>(a, P, ta, blockIdx.x, park, stage, sh);
-}
-
-// Persistent CTAs: take tiles from the cost-ordered queue until it is empty
-// (a wait-free atomic counter; no CTA ever waits on another).
-template <FitMode MODE, int T>
-__global__ void __launch_bounds__(T, 256 / T) k_fit_mixed_persistent(const FitArgs a, const Per32 P,
-                                                                     const TileArgs ta) {
-  using G = Groups<MODE>;
-  extern __shared__ float4 smem4[];
-  __shared__ FitShared<T> sh;
-  float* park = reinterpret_cast<float*>(smem4);
-  float4* stage = smem4 + (G::NA * kNB * T) / 4;
-  for (;;) {
-    if (threadIdx.x == 0) sh.tile = atomicAdd(ta.queue_head, 1);
-    __syncthreads();
-    const int q = sh.tile;
-    __syncthreads();
-    if (q >= ta.ntiles) break;
-    fit_tile<MODE, T>(a, P, ta, ta.order[q], park, stage, sh);
-  }
+  // schedule 1: the block scheduler's dispatch order runs the tiles in
+  // descending cost (longest first), without a loop over tiles in the kernel
+  fit_tile<MODE, T>(a, P, ta, ta.order ? ta.order[blockIdx.x] : static_cast<int>(blockIdx.x), park,
+                    stage, sh);
 }
 
 // The corrected step of the fits of refined tiles (queued by k_fit_mixed with
@@ -1122,20 +1102,7 @@ cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, int64
   const unsigned tiles = static_cast<unsigned>((units + T - 1) / T);
   cudaError_t e;
   if (units == 0) return cudaGetLastError();
-  if (a.g.schedule == 1 && !ta.list) {
-    cudaFuncSetAttribute(k_fit_mixed_persistent<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit_mixed_persistent<MODE, T>, T, smem);
-    if (per_sm < 1) per_sm = 1;
-    unsigned grid = static_cast<unsigned>(num_sms() * per_sm);
-    if (grid > tiles) grid = tiles;
-    if ((e = cudaMemsetAsync(ta.queue_head, 0, sizeof(int32_t), st))) return e;
-    const int tr = trace_begin(1, st);
-    k_fit_mixed_persistent<MODE, T><<<grid, T, smem, st>>>(a, P, ta);
-    note_launch();
-    trace_end(tr, st);
-  } else {
+  {
     cudaFuncSetAttribute(k_fit_mixed<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     const int tr = trace_begin(1, st);
@@ -1179,11 +1146,12 @@ cudaError_t launch_t(const FitArgs& a, const Per32& P, const TileArgs& ta, int64
 
 cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int2* tplan, const int32_t* tslot,
                              const uint16_t* lself, const uint8_t* tmap, const uint16_t* lidx,
-                             int32_t* fallback_count, const int32_t* order, int32_t* queue_head,
+                             int32_t* fallback_count, const int32_t* order,
                              const int32_t* list, const int32_t* list_len, int64_t list_cap,
                              cudaStream_t st) {
   const Per32 P = make_per32(a.g);
-  const TileArgs ta{tplan, tslot, lself, tmap, lidx, fallback_count, order, queue_head,
+  const TileArgs ta{tplan, tslot, lself, tmap, lidx, fallback_count,
+                    (a.g.schedule == 1 && !list) ? order : nullptr,
                     static_cast<int32_t>((a.n + a.g.tile - 1) / a.g.tile), list, list_len};
   if (mode == FitMode::kDerivs)
     return a.g.tile == 64 ? launch_t<FitMode::kDerivs, 64>(a, P, ta, list_cap, st)
@@ -1197,7 +1165,7 @@ cudaError_t launch_fit_tc(const FitArgs& a, const int2* tplan, const int32_t* ts
                           float* gram, cudaStream_t st) {
   if (a.g.tile != 128) return cudaErrorInvalidValue;
   const Per32 P = make_per32(a.g);
-  const TileArgs ta{tplan, tslot, lself, tmap, lidx, nullptr, nullptr, nullptr,
+  const TileArgs ta{tplan, tslot, lself, tmap, lidx, nullptr, nullptr,
                     static_cast<int32_t>((a.n + 127) / 128), nullptr, nullptr};
   const size_t smem = size_t(a.g.stage_cap) * 3 * sizeof(float4) + 4 * kTcWarpFloats * sizeof(float);
   cudaFuncSetAttribute(k_gram_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,

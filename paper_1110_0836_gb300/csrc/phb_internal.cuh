@@ -18,7 +18,7 @@ constexpr int kDiagBlocks = 1024;  // fixed grid of the diagnostic reductions (d
 enum Region {
   R_MISC = 0,    // int32 [64]: 0 = FP64 route-queue length, 1 = tiles that fell back to
                  //   global gathers in the last neighbour build, 2 = same in the last
-                 //   fused fit, 3 = persistent tile-queue counter, 4 = active-subset
+                 //   fused fit, 3 = (unused), 4 = active-subset
                  //   length, 5 = tiles refined by the last FP32-mixed fit, 6 = fits
                  //   queued for its corrected step
   R_KEYS,        // int32 [n]   cell key of each caller particle
@@ -40,7 +40,7 @@ enum Region {
   R_CLIN,        // int2 [cells] (first slot, count) per linear cell index (x-major)
   R_LSTART,      // int32 [cells+1] first record of each cell in linear cell order
   R_LSCR,        // float4 [n+4] screen records in linear cell order, slot in w (+ padding)
-  R_TORDER,      // int32 [ntiles] tiles in descending cost class (persistent schedule)
+  R_TORDER,      // int32 [ntiles] tiles in descending cost class (schedule 1)
   R_ELL,         // int32 [n][ell_width] first list entries of each slot (single-pass search)
   R_TPLAN,       // int2 [ntiles] (staged particles, 1 = not staged) of each tile's neighbourhood
   R_TSLOT,       // int32 [ntiles][stage_cap] slot of every staged index of each tile
@@ -88,7 +88,7 @@ struct Grid {
   int32_t hbits;      // Hilbert order of the brick curve
   int32_t tile;       // particles per tile
   int32_t stage_cap;  // staged records per tile
-  int32_t schedule;   // 0: grid of tiles, 1: persistent queue
+  int32_t schedule;   // 0: tiles in cell order, 1: tiles in descending cost
   int32_t ell;        // list entries kept per slot by the single-pass search
   int32_t n;
   double rf_factor, skin;
@@ -438,7 +438,7 @@ struct HostU {
 // the slots list[0 .. *list_len) (at most list_cap; unstaged path).
 cudaError_t launch_fit_mixed(const FitArgs& a, FitMode mode, const int2* tplan, const int32_t* tslot,
                              const uint16_t* lself, const uint8_t* tmap, const uint16_t* lidx,
-                             int32_t* fallback_count, const int32_t* order, int32_t* queue_head,
+                             int32_t* fallback_count, const int32_t* order,
                              const int32_t* list, const int32_t* list_len, int64_t list_cap,
                              cudaStream_t st);
 // Tensor-core experiment: Gram matrices on mma.sync (3xTF32) into gram

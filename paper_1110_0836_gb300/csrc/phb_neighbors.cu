@@ -858,7 +858,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_compact(Grid g, const int2* __r
   }
 }
 
-// Tile order for the persistent fused fit: tiles grouped by cost class
+// Tile order for the fused fit's schedule 1: tiles grouped by cost class
 // floor(log2(list entries + 1)), most expensive class first (longest
 // processing time first keeps the tail of the launch short).  One CTA.
 __global__ void __launch_bounds__(1024) k_tile_order(int n, int T, int ntiles, int64_t cap,
@@ -1316,7 +1316,7 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
                                         tplan, tslot, lself, tmap, misc + 1, status_word);
   trace_end(tr, st);
   note_launch();
-  if (p->schedule == 1) {  // only the persistent fit reads the tile order
+  if (p->schedule == 1) {  // only schedule 1 of the fit reads the tile order
     k_tile_order<<<1, 1024, 0, st>>>(n, p->tile, p->ntiles, p->nbr_capacity, off,
                                      region<int32_t>(p, ws, R_TORDER));
     note_launch();

@@ -166,8 +166,7 @@ cudaError_t run_fit(const phb_plan* plan, const phb_params* prm, void* ws, FitMo
                             region<uint16_t>(plan, ws, R_LSELF), region<uint8_t>(plan, ws, R_TMAP),
                             region<uint16_t>(plan, ws, R_LIDX),
                             a.queue_len + 2,
-                            region<int32_t>(plan, ws, R_TORDER), a.queue_len + 3, list, list_len,
-                            list_cap, st)))
+                            region<int32_t>(plan, ws, R_TORDER), list, list_len, list_cap, st)))
     return e;
   return launch_fit_fp64(a, mode, a.queue, a.queue_len, st, true);
 }

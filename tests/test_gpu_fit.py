@@ -249,8 +249,8 @@ def test_nonfinite_input_is_flagged():
                                                      (64, 64, 0), (128, 0, 1), (64, 0, 1),
                                                      (128, 64, 1)])
 def test_tile_shapes_and_global_fallback(tile, stage_cap, schedule):
-    """Both tile sizes, both tile schedules (one CTA per tile, or persistent CTAs
-    popping tiles in descending cost order), and a staging capacity so small that
+    """Both tile sizes, both tile schedules (tiles in cell order, or in
+    descending cost order), and a staging capacity so small that
     every tile reads its neighbours from global memory, give the same answers
     within the bars."""
     phb = need_gpu()
@@ -358,9 +358,9 @@ def test_corrected_step_schedules_agree():
 
 @pytest.mark.parametrize("tile", [64, 128])
 def test_corrected_step_under_both_tile_schedules(tile):
-    """The corrected step (every tile refined, in both of its schedules) under
-    the persistent tile schedule gives the time derivatives of one CTA per
-    tile bit for bit (the same tiles, staged relative to the same particles),
+    """The corrected step (every tile refined, in both of its schedules) with
+    the tiles run in descending cost order gives the time derivatives of the
+    cell order bit for bit (the same tiles, staged relative to the same particles),
     and both tile sizes meet 1e-5 against the oracle."""
     phb = need_gpu()
     w = workloads.shear_layer(60_000, seed=33)
