@@ -55,10 +55,10 @@ KERNEL_FLOP_PER_PARTICLE = 2 * (1140 + 7 * 171 + 7 * 36) + 100
 # under the size rule are captured on a smaller set of the same recipe and
 # scaled by the particles processed.  Absent = null.
 FIT_TRAFFIC = {
-    "random_modes_64^3": (68647168 + 2780416, "ncu, this workload, one launch"),
-    "shock_tube_1048576": (287487744 + 836574208 + 1261656320 + 78807040,
+    "random_modes_64^3": (68648704 + 2796288, "ncu, this workload, one launch"),
+    "shock_tube_1048576": (287636736 + 836296448 + 1261650432 + 78091264,
                            "ncu, this workload, one launch of each of the two fit kernels"),
-    "shear_layer_8000000": (8 * (474379264 + 285629440),
+    "shear_layer_8000000": (8 * (473713408 + 285548288),
                             "ncu on the 1,000,000-particle set of the same recipe with the "
                             "corrected step in the tiles (the 8M set's schedule), x 8 "
                             "(particles processed)"),
