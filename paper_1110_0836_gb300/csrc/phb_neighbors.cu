@@ -466,6 +466,7 @@ struct __align__(16) SearchWarp {
   float in2[32], out2[32];       // inner / outer screen radius^2
   int slot[32];
   double r2[32];                 // list radius^2 (exact test)
+  int32_t* row[32];              // the home's scratch row
   int run_t0[kRunCap];           // first linear-order record of each run
   int run_pre[kRunCap + 1];      // candidates before each run (the last: the total)
 };
@@ -505,13 +506,13 @@ __device__ __forceinline__ float2 screen_d2_pair(const Grid& g, float4 o, float2
 
 // The candidates of one chunk (one per lane) against every home of the warp,
 // four homes per round (their loads and screens independent): a ballot per
-// home gives its hits, appended to its scratch row in lane order.
+// home gives its hits, appended to its scratch row (S.row) in lane order.
 template <bool kWrap>
 __device__ __forceinline__ void screen_chunk(const Grid& g, const double* __restrict__ spos,
                                              const SearchWarp& S, int mh4, float4 o, int lane,
-                                             int& cnt, int32_t* __restrict__ ell) {
+                                             int& cnt) {
   const int t = __float_as_int(o.w);
-  const unsigned lt = (1u << lane) - 1u;
+  const unsigned bit = 1u << lane, lt = bit - 1u;
 #pragma unroll 1
   for (int i = 0; i < mh4; i += 4) {
     const float4 X = *reinterpret_cast<const float4*>(S.nx + i);
@@ -547,9 +548,9 @@ __device__ __forceinline__ void screen_chunk(const Grid& g, const double* __rest
       for (int u = 0; u < 4; ++u) {
         if (hit[u] == 0u) continue;
         const int c = __shfl_sync(0xffffffffu, cnt, i + u);
-        if ((hit[u] >> lane) & 1u) {
+        if (hit[u] & bit) {
           const int e = c + __popc(hit[u] & lt);
-          if (e < g.ell) ell[static_cast<int64_t>(sl[u]) * g.ell + e] = t;
+          if (e < g.ell) S.row[i + u][e] = t;
         }
         if (lane == i + u) cnt = c + __popc(hit[u]);
       }
@@ -681,6 +682,7 @@ __global__ void __launch_bounds__(32, 32) k_search_cells(Grid g, Lin lin,
       S.out2[lane] = q.out2;
       S.slot[lane] = mine ? s : -2;
       S.r2[lane] = q.r2;
+      S.row[lane] = ell + static_cast<int64_t>(mine ? s : 0) * g.ell;
     }
     if (lane == 0) S.run_pre[nrun] = total;
     __syncwarp();
@@ -705,9 +707,9 @@ __global__ void __launch_bounds__(32, 32) k_search_cells(Grid g, Lin lin,
       const float4 o = next;
       if (v0 + 32 < total) next = fetch(v0 + 32);  // one chunk ahead
       if (plain) {
-        screen_chunk<false>(g, spos, S, mh4, o, lane, cnt, ell);
+        screen_chunk<false>(g, spos, S, mh4, o, lane, cnt);
       } else {
-        screen_chunk<true>(g, spos, S, mh4, o, lane, cnt, ell);
+        screen_chunk<true>(g, spos, S, mh4, o, lane, cnt);
       }
     }
     if (mine) ncnt[s] = cnt;
