@@ -743,7 +743,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_search_ell(Grid g, const int2* 
 // index, each tile particle's own staged index - and map every list entry to
 // its staged index.
 template <int T>
-__global__ void __launch_bounds__(T, 1024 / T) k_compact(Grid g, const int2* __restrict__ clin, Lin lin,
+__global__ void __launch_bounds__(T, 1152 / T) k_compact(Grid g, const int2* __restrict__ clin, Lin lin,
                                                const int32_t* __restrict__ cellc,
                                                const float4* __restrict__ scr,
                                                const double* __restrict__ spos,
@@ -1310,6 +1310,13 @@ cudaError_t build_neighbors_impl(const phb_plan* p, const double* pos, const dou
   uint16_t* lself = region<uint16_t>(p, ws, R_LSELF);
   uint8_t* tmap = region<uint8_t>(p, ws, R_TMAP);
   tr = trace_begin(5, st);
+  // nine 128-thread blocks per SM at 56 registers: 2048 tiles in 1.5 waves
+  // of 1368 instead of 1.7 of 1216 (the shared memory of nine needs the
+  // largest carve-out)
+  cudaFuncSetAttribute(k_compact<128>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_compact<64>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
   if (p->tile == 128)
     k_compact<128><<<tiles, 128, 0, st>>>(g, clin, lin, cellc, scr, spos, slam, ncnt, ell, off, idx, lidx,
                                           tplan, tslot, lself, tmap, misc + 1, status_word);
